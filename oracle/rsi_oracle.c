@@ -1,0 +1,456 @@
+/*
+ * rsi_oracle.c -- plain, slow FP64 CPU oracle for the quasi-Monte Carlo
+ * Rayleigh-Sommerfeld-integral (RSI) beam model of Lello de Almeida, Png and
+ * Lan, "Efficient numerical frameworks for modelling ultrasonic beams
+ * propagating across interfaces" (arXiv 2408.06765).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load this library.  It shares no code with
+ * the CUDA path: its Sobol generator, scrambler, geometry and sums are written
+ * here from the paper and from the published constructions named below.
+ *
+ * Every sum is a direct loop over sources in index order, in double
+ * precision, with Neumaier compensation (Neumaier 1974).  Targets are
+ * independent, so they are split across POSIX threads; this changes no
+ * arithmetic.
+ *
+ * What each function follows:
+ *   orc_sobol          QMC points (Sec. 2.3, Eq. monte_carlo).  The paper
+ *                      draws Halton points; this build draws the first two
+ *                      Sobol dimensions (Bratley & Fox 1988; Joe & Kuo 2008
+ *                      construction), optionally with a nested (Owen 1995)
+ *                      bit scramble keyed by a SplitMix64 stream (Steele, Lea
+ *                      & Flood 2014; output mixer = Stafford 2011 "Mix13").
+ *   orc_map_disk       piston face sampling, Eq. circle_sampling (Sec. 2.3).
+ *   orc_map_rect       square interface sampling, Eq. square_sampling, with
+ *                      the side length given explicitly.
+ *   orc_map_cyl        cylindrical interface (projected-area sampling with the
+ *                      surface Jacobian); the paper has no curved interface,
+ *                      this is the multilayer workload's curved variant.
+ *   orc_piston_field   incident field of a piston, Eq. incident_field (Sec. 2.1).
+ *   orc_transmit       T12 of Eq. transmission_coefficient with Snell's
+ *                      invariant of Eq. root_searching; the source density of
+ *                      Eq. approximated_transmitted_field is T12 * phi_i since
+ *                      (rho1/rho2)(1+R12) = T12 (Eq. reflection_coefficient).
+ *   orc_rsi_field      first Rayleigh-Sommerfeld solution, Eq. rayleigh_sommerfeld
+ *                      (Sec. 2.1), over weighted source points; the sign of
+ *                      its bracket is read as explained at rsi_range().
+ *   orc_grid_points    cell-centred field-image grid (Sec. 3 uses a 2-D slice).
+ */
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based hash: the SplitMix64 generator.  Its n-th output for initial
+ * state s is mix64(s + n * GOLDEN).                                          */
+/* ------------------------------------------------------------------------ */
+#define ORC_GOLDEN 0x9E3779B97F4A7C15ULL
+
+uint64_t orc_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* key of one (seed, point set, dimension) triple */
+uint64_t orc_scramble_key(uint64_t seed, uint32_t set_id, uint32_t dim)
+{
+    uint64_t base = orc_mix64(seed + ORC_GOLDEN);
+    return orc_mix64(base ^ (((uint64_t)set_id << 1) | (uint64_t)(dim & 1u)));
+}
+
+/* Nested bit scramble: output bit b (counted from the most significant bit)
+ * is input bit b XOR the top bit of the hash of the tree node formed by the
+ * b leading input bits.  Node id = 2^b + (leading b bits). */
+uint32_t orc_owen(uint32_t x, uint64_t key)
+{
+    uint32_t y = x;
+    for (int b = 0; b < 32; ++b) {
+        uint64_t prefix = (b == 0) ? 0u : (uint64_t)(x >> (32 - b));
+        uint64_t node = ((uint64_t)1 << b) | prefix;
+        uint64_t h = orc_mix64(key + node * ORC_GOLDEN);
+        y ^= (uint32_t)(h >> 63) << (31 - b);
+    }
+    return y;
+}
+
+/* Direction numbers v_j = m_j 2^(32-j), j = 1..32.
+ * dim 0: m_j = 1 (van der Corput in base 2).
+ * dim 1: primitive polynomial x + 1 (degree 1), m_1 = 1, and the Sobol
+ *        recurrence for degree 1: m_j = 2 m_{j-1} XOR m_{j-1}.            */
+static void sobol_directions(uint32_t v[2][32])
+{
+    uint32_t m = 1u;
+    for (int j = 1; j <= 32; ++j) {
+        v[0][j - 1] = 1u << (32 - j);
+        if (j > 1)
+            m = (m << 1) ^ m;
+        v[1][j - 1] = m << (32 - j);
+    }
+}
+
+/* Points first .. first+n-1 of the 2-D Sobol sequence in natural index
+ * order: x = XOR of v_j over the set bits j of the index (bit j-1 of i). */
+void orc_sobol(uint64_t seed, uint32_t set_id, int64_t first, int64_t n,
+               int scrambled, uint32_t *su, uint32_t *sv)
+{
+    uint32_t v[2][32];
+    sobol_directions(v);
+    uint64_t k0 = orc_scramble_key(seed, set_id, 0);
+    uint64_t k1 = orc_scramble_key(seed, set_id, 1);
+    for (int64_t q = 0; q < n; ++q) {
+        uint64_t i = (uint64_t)(first + q);
+        uint32_t x = 0, y = 0;
+        for (int j = 1; j <= 32; ++j) {
+            if ((i >> (j - 1)) & 1u) {
+                x ^= v[0][j - 1];
+                y ^= v[1][j - 1];
+            }
+        }
+        if (scrambled) {
+            x = orc_owen(x, k0);
+            y = orc_owen(y, k1);
+        }
+        su[q] = x;
+        sv[q] = y;
+    }
+}
+
+/* unit value of a 32-bit QMC coordinate: (x + 1/2) 2^-32, exact in FP64 */
+static double unit(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+/* Piston face, Eq. circle_sampling: r = a sqrt(H), theta = 2 pi H (first
+ * dimension radial, second angular).  The face is centred at c and tilted by
+ * `tilt` radians about +y: in-plane axes e1 = (cos t, 0, -sin t), e2 = +y,
+ * normal (sin t, 0, cos t).  Weight = face area / n (Eq. monte_carlo).    */
+void orc_map_disk(int64_t n, const uint32_t *su, const uint32_t *sv,
+                  double cx, double cy, double cz, double tilt, double a,
+                  double *x, double *y, double *z,
+                  double *nx, double *ny, double *nz, double *w)
+{
+    double ct = cos(tilt), st = sin(tilt);
+    for (int64_t i = 0; i < n; ++i) {
+        double r = a * sqrt(unit(su[i]));
+        double th = 2.0 * M_PI * unit(sv[i]);
+        double l1 = r * cos(th), l2 = r * sin(th);
+        x[i] = cx + l1 * ct;
+        y[i] = cy + l2;
+        z[i] = cz - l1 * st;
+        nx[i] = st;
+        ny[i] = 0.0;
+        nz[i] = ct;
+        w[i] = M_PI * a * a / (double)n;
+    }
+}
+
+/* Flat interface patch, Eq. square_sampling with sides wx, wy centred on c;
+ * the interface normal is +z, toward the observation side (Sec. 2.1).    */
+void orc_map_rect(int64_t n, const uint32_t *su, const uint32_t *sv,
+                  double cx, double cy, double cz, double wx, double wy,
+                  double *x, double *y, double *z,
+                  double *nx, double *ny, double *nz, double *w)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        x[i] = cx + wx * (unit(su[i]) - 0.5);
+        y[i] = cy + wy * (unit(sv[i]) - 0.5);
+        z[i] = cz;
+        nx[i] = 0.0;
+        ny[i] = 0.0;
+        nz[i] = 1.0;
+        w[i] = wx * wy / (double)n;
+    }
+}
+
+/* Cylindrical interface with axis parallel to y through (cx, ., cz + R):
+ * z = cz + R - sqrt(R^2 - xi^2), xi = x - cx.  Points are uniform in the
+ * projected (x, y) rectangle; the weight carries the surface Jacobian
+ * R / sqrt(R^2 - xi^2).  The normal points toward the axis (+z side).     */
+void orc_map_cyl(int64_t n, const uint32_t *su, const uint32_t *sv,
+                 double cx, double cy, double cz, double wx, double wy, double R,
+                 double *x, double *y, double *z,
+                 double *nx, double *ny, double *nz, double *w)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double xi = wx * (unit(su[i]) - 0.5);
+        double s = sqrt(R * R - xi * xi);
+        x[i] = cx + xi;
+        y[i] = cy + wy * (unit(sv[i]) - 0.5);
+        z[i] = cz + R - s;
+        nx[i] = -xi / R;
+        ny[i] = 0.0;
+        nz[i] = s / R;
+        w[i] = wx * wy / (double)n * (R / s);
+    }
+}
+
+/* Cell-centred grid in the plane y = y0: x_i = x0 + (i + 1/2)(x1 - x0)/nx,
+ * z_j = z0 + (j + 1/2)(z1 - z0)/nz, stored row-major [nz][nx].           */
+void orc_grid_points(double x0, double x1, int64_t nxp, double z0, double z1,
+                     int64_t nzp, double y0, double *x, double *y, double *z)
+{
+    double dx = (x1 - x0) / (double)nxp, dz = (z1 - z0) / (double)nzp;
+    for (int64_t j = 0; j < nzp; ++j)
+        for (int64_t i = 0; i < nxp; ++i) {
+            int64_t q = j * nxp + i;
+            x[q] = x0 + ((double)i + 0.5) * dx;
+            y[q] = y0;
+            z[q] = z0 + ((double)j + 0.5) * dz;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neumaier-compensated complex accumulator                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct { double s, c; } nsum;
+
+static void nsum_add(nsum *a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v))
+        a->c += (a->s - t) + v;
+    else
+        a->c += (v - t) + a->s;
+    a->s = t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Thread fan-out over targets                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int kind; /* 0 piston, 1 rsi */
+    int64_t ns;
+    const double *sx, *sy, *sz, *snx, *sny, *snz, *sw, *sre, *sim;
+    double v0, k;
+    const double *tx, *ty, *tz;
+    double *ore, *oim;
+    int64_t t0, t1;
+} field_job;
+
+/* Eq. incident_field:  phi_i(P1) = -(v0 / 2 pi) sum_i w_i e^{i k r} / r      */
+static void piston_range(const field_job *J)
+{
+    for (int64_t j = J->t0; j < J->t1; ++j) {
+        nsum re = {0, 0}, im = {0, 0};
+        for (int64_t i = 0; i < J->ns; ++i) {
+            double dx = J->tx[j] - J->sx[i];
+            double dy = J->ty[j] - J->sy[i];
+            double dz = J->tz[j] - J->sz[i];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r < 1e-12)
+                continue; /* coincident source and target: no contribution */
+            double complex term = -(J->v0 / (2.0 * M_PI)) * J->sw[i] * cexp(I * J->k * r) / r;
+            nsum_add(&re, creal(term));
+            nsum_add(&im, cimag(term));
+        }
+        J->ore[j] = re.s + re.c;
+        J->oim[j] = im.s + im.c;
+    }
+}
+
+/* Eq. rayleigh_sommerfeld with the source density sigma = phi (or T12 phi_i
+ * across an interface, Eq. approximated_transmitted_field):
+ *   phi(Po) = -(i/lambda) sum_i w_i sigma_i e^{ikr}/r (1 - 1/(ikr)) cos(theta),
+ * r from the source point P_i to Po, cos(theta) = n_i . (Po - P_i) / r with
+ * n_i toward the observation side, lambda = 2 pi / k of the medium the field
+ * propagates in.  The printed equation has the bracket as (1/(ikr) - 1); with
+ * the paper's stated normal and r conventions that sign returns -phi for an
+ * outgoing field, while the equation is named (and used in Sec. 3.1-3.2) as
+ * the first Rayleigh-Sommerfeld solution, which must return +phi.  The
+ * bracket is therefore read as (1 - 1/(ikr)), the standard solution.         */
+static void rsi_range(const field_job *J)
+{
+    double lambda = 2.0 * M_PI / J->k;
+    for (int64_t j = J->t0; j < J->t1; ++j) {
+        nsum re = {0, 0}, im = {0, 0};
+        for (int64_t i = 0; i < J->ns; ++i) {
+            double dx = J->tx[j] - J->sx[i];
+            double dy = J->ty[j] - J->sy[i];
+            double dz = J->tz[j] - J->sz[i];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (r < 1e-12)
+                continue; /* coincident source and target: no contribution */
+            double cos_theta = (J->snx[i] * dx + J->sny[i] * dy + J->snz[i] * dz) / r;
+            double complex sigma = J->sre[i] + I * J->sim[i];
+            double complex term = (-I / lambda) * J->sw[i] * sigma * cexp(I * J->k * r) / r
+                                  * (1.0 - 1.0 / (I * J->k * r)) * cos_theta;
+            nsum_add(&re, creal(term));
+            nsum_add(&im, cimag(term));
+        }
+        J->ore[j] = re.s + re.c;
+        J->oim[j] = im.s + im.c;
+    }
+}
+
+static void *field_worker(void *arg)
+{
+    field_job *J = (field_job *)arg;
+    if (J->kind == 0)
+        piston_range(J);
+    else
+        rsi_range(J);
+    return NULL;
+}
+
+static void run_field(field_job proto, int64_t nt, int nthreads)
+{
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > 256)
+        nthreads = 256;
+    if ((int64_t)nthreads > nt)
+        nthreads = (int)(nt > 0 ? nt : 1);
+    pthread_t th[256];
+    int started[256];
+    field_job jobs[256];
+    int64_t chunk = (nt + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t] = proto;
+        jobs[t].t0 = (int64_t)t * chunk;
+        jobs[t].t1 = jobs[t].t0 + chunk < nt ? jobs[t].t0 + chunk : nt;
+        started[t] = 0;
+        if (jobs[t].t0 >= jobs[t].t1)
+            continue;
+        if (nthreads > 1 && pthread_create(&th[t], NULL, field_worker, &jobs[t]) == 0)
+            started[t] = 1;
+        else
+            field_worker(&jobs[t]); /* single thread, or no thread available */
+    }
+    for (int t = 0; t < nthreads; ++t)
+        if (started[t])
+            pthread_join(th[t], NULL);
+}
+
+void orc_piston_field(int64_t ns, const double *sx, const double *sy, const double *sz,
+                      const double *sw, double v0, double k,
+                      int64_t nt, const double *tx, const double *ty, const double *tz,
+                      double *out_re, double *out_im, int nthreads)
+{
+    field_job J;
+    memset(&J, 0, sizeof J);
+    J.kind = 0;
+    J.ns = ns;
+    J.sx = sx; J.sy = sy; J.sz = sz; J.sw = sw;
+    J.v0 = v0; J.k = k;
+    J.tx = tx; J.ty = ty; J.tz = tz;
+    J.ore = out_re; J.oim = out_im;
+    run_field(J, nt, nthreads);
+}
+
+void orc_rsi_field(int64_t ns, const double *sx, const double *sy, const double *sz,
+                   const double *snx, const double *sny, const double *snz,
+                   const double *sw, const double *sig_re, const double *sig_im, double k,
+                   int64_t nt, const double *tx, const double *ty, const double *tz,
+                   double *out_re, double *out_im, int nthreads)
+{
+    field_job J;
+    memset(&J, 0, sizeof J);
+    J.kind = 1;
+    J.ns = ns;
+    J.sx = sx; J.sy = sy; J.sz = sz;
+    J.snx = snx; J.sny = sny; J.snz = snz;
+    J.sw = sw; J.sre = sig_re; J.sim = sig_im;
+    J.k = k;
+    J.tx = tx; J.ty = ty; J.tz = tz;
+    J.ore = out_re; J.oim = out_im;
+    run_field(J, nt, nthreads);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interface transmission                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* cos of an angle whose sine is s (real): sqrt(1 - s^2) when |s| <= 1, else
+ * the branch i sqrt(s^2 - 1) (Im >= 0: evanescent decay for e^{-i w t}).   */
+static double complex cos_from_sin(double s)
+{
+    double q = 1.0 - s * s;
+    if (q >= 0.0)
+        return sqrt(q);
+    return I * sqrt(-q);
+}
+
+/* Eq. transmission_coefficient:
+ *   T12 = 2 rho1 c2 cos a1 / (rho2 c2 cos a1 + rho1 c1 cos a2).           */
+double complex orc_T12(double rho1, double c1, double rho2, double c2,
+                       double complex cos1, double complex cos2)
+{
+    return 2.0 * rho1 * c2 * cos1 / (rho2 * c2 * cos1 + rho1 * c1 * cos2);
+}
+
+/* Eq. reflection_coefficient, for the identity test (rho1/rho2)(1+R12) = T12. */
+double complex orc_R12(double rho1, double c1, double rho2, double c2,
+                       double complex cos1, double complex cos2)
+{
+    return (rho2 * c2 * cos1 - rho1 * c1 * cos2) / (rho2 * c2 * cos1 + rho1 * c1 * cos2);
+}
+
+/* ctypes-friendly wrappers (complex split into re/im) */
+void orc_T12_ri(double rho1, double c1, double rho2, double c2,
+                double cos1_re, double cos1_im, double cos2_re, double cos2_im,
+                double *out)
+{
+    double complex t = orc_T12(rho1, c1, rho2, c2, cos1_re + I * cos1_im, cos2_re + I * cos2_im);
+    out[0] = creal(t);
+    out[1] = cimag(t);
+}
+
+void orc_R12_ri(double rho1, double c1, double rho2, double c2,
+                double cos1_re, double cos1_im, double cos2_re, double cos2_im,
+                double *out)
+{
+    double complex t = orc_R12(rho1, c1, rho2, c2, cos1_re + I * cos1_im, cos2_re + I * cos2_im);
+    out[0] = creal(t);
+    out[1] = cimag(t);
+}
+
+/* Source density on an interface, sigma_i = T12(alpha1_i) phi_i(P_i).
+ * mode 0 (global): one incidence angle for the whole interface, fixed by
+ *   Snell's invariant C = sin a / c (Eq. root_searching) of the beam axis:
+ *   sin a1 = c1 C, sin a2 = c2 C.
+ * mode 1 (local): the incidence angle at each point is the angle between
+ *   the beam direction in medium 1, d = (c1 C, 0, sqrt(1 - (c1 C)^2)), and
+ *   the local normal n_i: cos a1 = d . n_i (clamped at 0 from below),
+ *   sin a2 = (c2 / c1) sin a1.
+ * Writes T (re, im) when T_re/T_im are non-NULL.                            */
+void orc_transmit(int64_t n, int mode, double rho1, double c1, double rho2, double c2,
+                  double snell_C, const double *nx, const double *ny, const double *nz,
+                  const double *phi_re, const double *phi_im,
+                  double *sig_re, double *sig_im, double *T_re, double *T_im)
+{
+    double s1g = c1 * snell_C;
+    double dxv = s1g, dyv = 0.0, dzv = sqrt(fmax(0.0, 1.0 - s1g * s1g));
+    for (int64_t i = 0; i < n; ++i) {
+        double complex cos1, cos2;
+        if (mode == 0) {
+            cos1 = cos_from_sin(c1 * snell_C);
+            cos2 = cos_from_sin(c2 * snell_C);
+        } else {
+            double c = dxv * nx[i] + dyv * ny[i] + dzv * nz[i];
+            if (c < 0.0)
+                c = 0.0;
+            if (c > 1.0)
+                c = 1.0;
+            double s = sqrt(1.0 - c * c);
+            cos1 = c;
+            cos2 = cos_from_sin(c2 / c1 * s);
+        }
+        double complex T = orc_T12(rho1, c1, rho2, c2, cos1, cos2);
+        double complex phi = phi_re[i] + I * phi_im[i];
+        double complex sig = T * phi;
+        sig_re[i] = creal(sig);
+        sig_im[i] = cimag(sig);
+        if (T_re)
+            T_re[i] = creal(T);
+        if (T_im)
+            T_im[i] = cimag(T);
+    }
+}
