@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the RSI hot path on GB300: one step = the full-image chain of
+the 2^16-point piston / 2^18-point 80 x 80 mm interface / 512 x 512 image
+workload at 2.25, 5 and 10 MHz (points, piston stage, transmission, RSI
+stage, image), i.e. 2.58e11 source x target pair terms.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is pair terms per second over the K timed
+steps (CUDA events on the launching stream, L2 flushed before every step);
+`e2e` repeats the measurement through the public API with the image read
+back into pinned host memory each step; `roofline` relates the dominant
+kernel's pair rate to the FP32-issue / MUFU limits measured by the
+library's own throughput probes; `cpu_baseline` times the FP64 oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Per-pair work of the FP32C kernels as formulated (counted from the source of
+# csrc/stage_fp32.cu, reciprocal variant): FP32-pipe instructions, MUFU
+# operations, shared-memory loads per pair at 4 targets per thread.
+OPS = {
+    "rsi": {"fp32": 27, "mufu": 4, "lds": 0.5},
+    "piston": {"fp32": 20, "mufu": 4, "lds": 0.5},
+}
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "rsi_pair_terms_per_s"
+UNIT = "pair-terms/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target duration of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", choices=["chain", "stage"], default="chain",
+                    help="stage: only the RSI interface -> image kernel of the 10 MHz c2 chain "
+                         "on a 256 x 256 image (small case for profiler captures)")
+    ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--tpt", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2408_06765_gb300 import workloads as W
+    cfgs = W.c2_all()
+    pairs = sum(W.pairs_of(c) for c in cfgs)
+    pixels = sum(int(c["grid"]["nx"]) * int(c["grid"]["nz"]) for c in cfgs)
+    return cfgs, pairs, pixels
+
+
+def config_block(cfgs, n_gpus):
+    return {"workload": "c2 full-image RSI: 2^16 piston x 2^18 interface (80 mm) x 512^2 image, "
+                        "f = 2.25/5/10 MHz, water -> steel at 50 mm",
+            "frequencies_mhz": [c["freq"] / 1e6 for c in cfgs],
+            "n_piston": cfgs[0]["piston"]["n"], "n_interface": cfgs[0]["interfaces"][0]["n"],
+            "image": [cfgs[0]["grid"]["nz"], cfgs[0]["grid"]["nx"]],
+            "precision": "fp32 pairs, double-float phase, compensated sums",
+            "l2": "flushed (256 MiB write) before every timed step",
+            "parallelism": f"replica per GPU x{n_gpus}" if n_gpus > 1 else "1 GPU"}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# throughput probes -> ALU roofline
+# ---------------------------------------------------------------------------
+def measure_unit_rates(rsi, torch):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, iters = sms * 8, 4096
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    rates = {}
+    for kind in ("ffma", "rsqrt", "sin"):
+        rsi.ubench(kind, blocks, 64, sink)  # warm-up
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rsi.ubench(kind, blocks, iters, sink)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        rates[kind] = blocks * 256 * iters * 8 / best  # lane operations per second
+    return rates
+
+
+def alu_roofline(kind: str, rates: dict):
+    """Peak pairs/s of a stage kernel: the tighter of the issue limit (one warp
+    instruction per scheduler per clock, measured as the FFMA rate) and the
+    MUFU limit (measured rsqrt rate)."""
+    o = OPS[kind]
+    issue = (o["fp32"] + o["mufu"] + o["lds"]) / rates["ffma"]
+    mufu = o["mufu"] / rates["rsqrt"]
+    return 1.0 / max(issue, mufu), ("mufu" if mufu >= issue else "issue")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, seconds: float, seed: int = 0):
+    """Time the FP64 oracle on a bounded sample of one chain: all piston
+    points onto m1 interface points, and all interface points onto m2 image
+    pixels; m1, m2 sized for about `seconds` of work."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    pc = cfg["piston"]
+    it = cfg["interfaces"][0]
+    piston = oracle.make_points(dict(pc, kind="disk"), cfg["seed"], pc["set_id"], pc["n"])
+    iface = oracle.make_points(it, cfg["seed"], it["set_id"], it["n"])
+    grid = oracle.grid_points(cfg["grid"])
+    k1 = oracle.wavenumber(cfg["freq"], cfg["media"][0]["c"])
+    k2 = oracle.wavenumber(cfg["freq"], cfg["media"][1]["c"])
+    rng = np.random.default_rng(seed)
+    sig = np.ones(it["n"], np.complex128)
+
+    def run(m1, m2):
+        s1 = rng.choice(it["n"], m1, replace=False)
+        s2 = rng.choice(grid["x"].shape[0], m2, replace=False)
+        t0 = time.perf_counter()
+        phi1 = oracle.piston_field(piston, {k: iface[k][s1] for k in ("x", "y", "z")}, k1)
+        oracle.rsi_field(iface, sig, {k: grid[k][s2] for k in ("x", "y", "z")}, k2)
+        dt = time.perf_counter() - t0
+        return dt, pc["n"] * m1 + it["n"] * m2, s1, phi1
+
+    dt, pairs, _, _ = run(32, 8)
+    rate = pairs / dt
+    m = max(16, int(seconds * rate / (pc["n"] + it["n"]) / 2))
+    dt, pairs, s1, phi1 = run(m, m)
+    return {"seconds": dt, "pairs": pairs, "rate": pairs / dt, "m": m,
+            "iface_slots_natural": s1, "phi1": phi1, "threads": oracle.default_threads()}
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def reduce_max(v: float, world: int):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_ours(args):
+    import torch
+    from paper_2408_06765_gb300 import build, rsi
+    world, rank, local = dist_setup()
+    build.build()
+    rsi.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfgs, pairs_step, pixels_step = workload()
+    ws = rsi.Workspace(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        return [rsi.run_chain(c, fmt="c64", workspace=ws, device=dev).image for c in cfgs]
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    rsi.sync_status()
+
+    rates = measure_unit_rates(rsi, torch)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    rsi.timing_enable(True)
+    n0 = rsi.launch_count()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = rsi.launch_count() - n0
+    barrier(world)
+    clk = clocks.stop()
+    rsi_ms, rsi_n, rsi_pairs = rsi.timing_read(rsi.STAGE_RSI)
+    pis_ms, pis_n, pis_pairs = rsi.timing_read(rsi.STAGE_PISTON)
+    rsi.timing_enable(False)
+    rsi.sync_status()
+    total_s = reduce_max(sum(step_ms) * 1e-3, world)
+    value = world * pairs_step * args.steps / total_s
+
+    # dominant kernel: the RSI stage kernel (interface -> image dominates)
+    avg_s = rsi_ms * 1e-3 / max(1, rsi_n)
+    achieved = (rsi_pairs / max(1, rsi_n)) / avg_s
+    peak, limiter = alu_roofline("rsi", rates)
+    pis_avg = pis_ms * 1e-3 / max(1, pis_n)
+    pis_peak, _ = alu_roofline("piston", rates)
+    roof = {"bound": "alu", "kernel": "stage_fp32_kernel<RSI>", "achieved": achieved / 1e9,
+            "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+            "limiter": limiter,
+            "ops_per_pair": OPS["rsi"],
+            "peak_source": "measured in this run: FFMA issue rate and MUFU rsqrt rate "
+                           "(rsi_ubench), same clocks as the timed region",
+            "unit_rates_tops": {k: v / 1e12 for k, v in rates.items()},
+            "avg_launch_ms": avg_s * 1e3, "launches": rsi_n,
+            "piston_kernel": {"achieved": (pis_pairs / max(1, pis_n)) / max(pis_avg, 1e-12) / 1e9,
+                              "peak": pis_peak / 1e9, "avg_launch_ms": pis_avg * 1e3,
+                              "launches": pis_n}}
+    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_file):
+        try:
+            roof["traffic"] = json.load(open(traffic_file)).get("stage_fp32_kernel_rsi_bytes_per_launch")
+        except (OSError, ValueError):
+            pass
+
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.empty((c["grid"]["nz"], c["grid"]["nx"]), dtype=torch.complex64,
+                            pin_memory=True) for c in cfgs]
+        d2h = sum(h.numel() * h.element_size() for h in host)
+        e2e_s = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            imgs = step()
+            for h, im in zip(host, imgs):
+                h.copy_(im, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_s.append(time.perf_counter() - t0)
+        tot = reduce_max(sum(e2e_s), world)
+        e2e = {"value": world * pairs_step * args.steps / tot, "unit": UNIT,
+               "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+               "note": "inputs are scalar workload parameters passed by value through the "
+                       "C ABI (no array inputs); the three c64 images are read back each step"}
+
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import numpy as np
+        cfg = cfgs[1]
+        smp = oracle_sample(cfg, args.cpu_seconds)
+        cpu = {"value": smp["rate"], "unit": UNIT, "cores": smp["threads"], "kind": "oracle",
+               "sample": f"c2 at {cfg['freq'] / 1e6:g} MHz: all {cfg['piston']['n']} piston points "
+                         f"onto {smp['m']} random interface points + all "
+                         f"{cfg['interfaces'][0]['n']} interface points onto {smp['m']} random "
+                         f"pixels ({smp['pairs']:.3g} pairs, {smp['seconds']:.1f} s), FP64"}
+        res = rsi.run_chain(cfg, keep=True, workspace=ws, device=dev)
+        (gif, gphi), = res.ifaces
+        idx = gif.field("IDX").cpu().numpy().view(np.uint32)
+        slot_of = np.empty_like(idx)
+        slot_of[idx] = np.arange(idx.size, dtype=np.uint32)
+        g = gphi.cpu().numpy()[slot_of[smp["iface_slots_natural"]]]
+        err = float(np.linalg.norm(g - smp["phi1"]) / np.linalg.norm(smp["phi1"]))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup),
+                "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded scrambled-Sobol points; workload parameters only)",
+                "config": config_block(cfgs, world),
+                "field_pts_per_s": world * pixels_step * args.steps / total_s,
+                "rel_l2_err": {"piston_stage_sampled_vs_fp64_oracle": err, "tolerance": 1e-4},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm, on the host cores (rank 0)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfgs, _, _ = workload()
+    cfg = cfgs[1]
+    per_step = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
+    for _ in range(max(1, args.warmup)):
+        oracle_sample(cfg, 1.0, seed=99)
+    rates, secs, pairs = [], 0.0, 0
+    for s in range(args.steps):
+        smp = oracle_sample(cfg, per_step, seed=s)
+        rates.append(smp["rate"])
+        secs += smp["seconds"]
+        pairs += smp["pairs"]
+    value = pairs / secs
+    cpu = {"value": value, "unit": UNIT, "cores": smp["threads"], "kind": "oracle",
+           "sample": f"per step: all piston points onto {smp['m']} interface points + all "
+                     f"interface points onto {smp['m']} pixels of c2 at 5 MHz, FP64"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(1, args.warmup),
+            "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(cfgs, 1), "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_stage_case(args):
+    """One RSI stage (2^18 interface points -> 65 536 pixels), `steps` times."""
+    import torch
+    from paper_2408_06765_gb300 import build, rsi
+    from paper_2408_06765_gb300 import workloads as W
+    build.build()
+    cfg = W.c2_full_image(10e6)
+    cfg["grid"] = dict(cfg["grid"], nx=256, nz=256)
+    it = cfg["interfaces"][0]
+    pts = rsi.make_qmc_points(it, 0, it["set_id"], it["n"])
+    grid = rsi.grid_points(cfg["grid"])
+    sigma = torch.ones(it["n"], dtype=torch.complex128, device="cuda")
+    st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", rsi.wavenumber(cfg["freq"], 5900.0),
+                          normals=rsi.NORMALS_Z, tile=args.tile, tpt=args.tpt, variant=args.variant)
+    ws = rsi.Workspace()
+    out = None
+    times = []
+    for _ in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = rsi.propagate_stage(st, pts, sigma, grid, workspace=ws)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    rsi.sync_status()
+    ms = min(times[args.warmup:])
+    pairs = it["n"] * grid.n
+    print(json.dumps({"case": "stage", "ms": ms, "gpair_per_s": pairs / ms / 1e6,
+                      "variant": args.variant, "tile": args.tile, "tpt": args.tpt,
+                      "checksum": float(out.abs().sum().item())}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.case == "stage":
+        run_stage_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * rsi.h -- C ABI of the GB300 (sm_103a) hot path of the quasi-Monte Carlo
+ * Rayleigh-Sommerfeld-integral (RSI) beam model of Lello de Almeida, Png and
+ * Lan (arXiv 2408.06765).
+ *
+ * Conventions shared by every call
+ *   - Units are SI.  z is depth; the beam travels toward +z.  Complex values
+ *     are interleaved (re, im) doubles; the time factor is e^{-i w t}, so an
+ *     outgoing wave is e^{+ikr}/r (Sec. 2.1).
+ *   - Pointers named *points, *field, *sigma, *out and *workspace are DEVICE
+ *     pointers allocated and owned by the caller (for example torch tensors);
+ *     structs passed by const pointer are HOST memory, read during the call
+ *     only.  The library never frees caller memory and, apart from a small
+ *     per-device status word, allocates no device memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     only enqueues work on it and returns; results are ready once the stream
+ *     is synchronised.
+ *   - Return value: RSI_OK (0) or a negative RSI_E_* code; rsi_last_error()
+ *     then describes the failure (thread-local).  Invalid arguments are
+ *     rejected before anything is enqueued.
+ *   - Errors detected on the device (a bounded wait that expired, a
+ *     non-finite result) are written to a per-device status word that
+ *     rsi_sync_status() reads and clears.
+ */
+#ifndef RSI_H
+#define RSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RSI_OK 0
+#define RSI_E_INVAL (-1)       /* invalid argument (null pointer, size, kind)   */
+#define RSI_E_CUDA (-2)        /* a CUDA runtime call failed                    */
+#define RSI_E_TIMEOUT (-3)     /* a device-side bounded wait expired            */
+#define RSI_E_NONFINITE (-4)   /* a result was NaN or infinite                  */
+#define RSI_E_NOMEM (-5)       /* workspace or output buffer too small          */
+#define RSI_E_UNSUPPORTED (-6) /* no kernel for this combination / device       */
+
+int rsi_version(void);                 /* library ABI version (this header: 1) */
+const char *rsi_last_error(void);      /* message of the last failure on this thread */
+
+/* Wait for `stream`, then read and clear the device status word of the
+ * current device.  Returns RSI_OK, RSI_E_TIMEOUT, RSI_E_NONFINITE or
+ * RSI_E_CUDA (a CUDA error surfaced by the synchronisation). */
+int rsi_sync_status(void *stream);
+
+/* ---- point sets ---------------------------------------------------------- */
+/* A point set of n points is ONE caller-allocated device buffer holding
+ * structure-of-arrays fields, each starting on a 256-byte boundary at
+ * rsi_points_offset(field, n); its total size is rsi_points_bytes(n).
+ *   IDX, SU, SV    uint32  Sobol index of the point and its two 32-bit
+ *                          (scrambled) coordinates
+ *   X, Y, Z        double  position (m)
+ *   NX, NY, NZ     double  unit normal pointing toward the observation side
+ *   W              double  quadrature weight (area / n, times any Jacobian)
+ *   XH..ZL         float   position split as hi = fl32(x), lo = fl32(x - hi)
+ */
+enum rsi_points_field {
+    RSI_PF_IDX = 0, RSI_PF_SU, RSI_PF_SV,
+    RSI_PF_X, RSI_PF_Y, RSI_PF_Z,
+    RSI_PF_NX, RSI_PF_NY, RSI_PF_NZ,
+    RSI_PF_W,
+    RSI_PF_XH, RSI_PF_XL, RSI_PF_YH, RSI_PF_YL, RSI_PF_ZH, RSI_PF_ZL,
+    RSI_PF_COUNT
+};
+size_t rsi_points_bytes(int64_t n);
+int64_t rsi_points_offset(int32_t field, int64_t n); /* -1 for an unknown field */
+
+enum rsi_surface_kind {
+    RSI_SURF_DISK = 0, /* piston face: radius a, centre, tilt about +y          */
+    RSI_SURF_RECT = 1, /* flat interface patch wx x wy at z = centre[2], normal +z */
+    RSI_SURF_CYL = 2   /* cylinder, axis parallel to y through (cx, ., cz + R)  */
+};
+
+typedef struct rsi_surface {
+    int32_t kind;     /* enum rsi_surface_kind                                  */
+    int32_t scramble; /* 1: nested bit scramble of the Sobol digits; 0: plain   */
+    double centre[3]; /* DISK: face centre; RECT: patch centre; CYL: apex point */
+    double tilt;      /* DISK: rotation about +y (rad), normal (sin t, 0, cos t)*/
+    double a;         /* DISK: radius (m)                                       */
+    double wx, wy;    /* RECT, CYL: side lengths of the (projected) patch (m)   */
+    double R;         /* CYL: radius of curvature (m), R > wx / 2               */
+} rsi_surface;
+
+/* Steps a1-a2.  Sobol points 0..n-1 of the set (seed, set_id), dimensions 1
+ * and 2, optionally scrambled (digit b flipped by the top bit of SplitMix64's
+ * (2^b + leading b digits)-th output for the dimension's key), mapped onto
+ * the surface: DISK r = a sqrt(u), theta = 2 pi v (Eq. circle_sampling);
+ * RECT x = cx + wx (u - 1/2), y = cy + wy (v - 1/2) (Eq. square_sampling);
+ * CYL the same (x, y) with z = cz + R - sqrt(R^2 - (x - cx)^2) and Jacobian
+ * R / sqrt(R^2 - (x - cx)^2) in the weight; u = (su + 1/2) 2^-32.
+ * Layout: points are stored in CELL ORDER, not index order: n is split into
+ * aligned power-of-two blocks (its binary digits, largest first); within a
+ * block of 2^m points, point i goes to slot block_start + morton(cx, cy) with
+ * cx the top ceil(m/2) bits of su and cy the top floor(m/2) bits of sv (cx
+ * on even bits).  Each block is a (0,m,2)-net, so this is a permutation and
+ * consecutive slots are spatially compact.  IDX gives each slot's Sobol index.
+ * Requires 1 <= n <= 2^31, points_bytes >= rsi_points_bytes(n).             */
+int rsi_make_qmc_points(const rsi_surface *surf, uint64_t seed, uint32_t set_id, int64_t n,
+                        void *points, size_t points_bytes, void *stream);
+
+typedef struct rsi_grid {
+    double x0, x1; /* x extent (m); pixel i at x0 + (i + 1/2)(x1 - x0)/nx      */
+    double z0, z1; /* z extent (m); pixel j at z0 + (j + 1/2)(z1 - z0)/nz      */
+    double y;      /* plane of the slice                                        */
+    int32_t nx, nz;
+} rsi_grid;
+
+/* Step a7 (targets).  Writes the nx*nz cell-centred pixels of the grid as a
+ * point set in row-major [nz][nx] order (IDX = pixel index, normals +z,
+ * W = 0).  points_bytes >= rsi_points_bytes(nx * nz).                       */
+int rsi_grid_points(const rsi_grid *g, void *points, size_t points_bytes, void *stream);
+
+/* ---- stage sums (steps a3, a5, a6) ------------------------------------- */
+enum rsi_stage_kind {
+    RSI_STAGE_PISTON = 0, /* Eq. incident_field: phi(Q) = -(v0/2pi) sum w e^{ikr}/r */
+    RSI_STAGE_RSI = 1     /* Eq. rayleigh_sommerfeld: phi(Q) = -(i/lambda) sum w sigma
+                               e^{ikr}/r (1 - 1/(ikr)) cos(theta), cos(theta) =
+                               n.(Q - P)/r.  The printed bracket (1/(ikr) - 1)
+                               would return -phi for an outgoing field; this is
+                               the first Rayleigh-Sommerfeld solution itself.  */
+};
+enum rsi_precision {
+    RSI_PREC_FP64 = 0, /* double precision throughout                          */
+    RSI_PREC_FP32C = 1 /* FP32 pair arithmetic; per (target, source tile) a
+                          double-float reference distance and phase k R mod 2 pi;
+                          compensated accumulation across tiles              */
+};
+enum rsi_normals {
+    RSI_NORMALS_Z = 0,     /* every source normal is +z (flat interface)       */
+    RSI_NORMALS_POINTS = 1 /* use the per-point normals                         */
+};
+
+typedef struct rsi_stage {
+    int32_t kind;      /* enum rsi_stage_kind                                   */
+    int32_t precision; /* enum rsi_precision                                    */
+    double k;          /* wavenumber of the medium the field propagates in (rad/m) */
+    double v0;         /* PISTON: normal velocity amplitude (m/s)               */
+    int32_t normals;   /* RSI: enum rsi_normals                                  */
+    int32_t tile;      /* sources per shared-memory tile (64, 128, 256); 0 = auto */
+    int32_t tpt;       /* targets per thread (FP32C: 2 or 4; FP64: 1); 0 = auto   */
+    int32_t splits;    /* source splits (>= 1); 0 = auto                          */
+    int32_t variant;   /* FP32C distance update: 0 = auto, 1 = reciprocal, 2 = Newton */
+    int32_t reserved;
+} rsi_stage;
+
+/* Workspace needed by rsi_propagate_stage for this stage and these sizes
+ * (staged source tiles, plus split partial sums).  0 on invalid input.     */
+size_t rsi_stage_workspace_bytes(const rsi_stage *st, int64_t n_src, int64_t n_tgt);
+
+/* Steps a3/a5 (+a6).  For every target Q_j of `tgt_points`:
+ *   PISTON  field[j] = -(v0 / 2 pi) sum_i w_i e^{ikr_ij} / r_ij
+ *   RSI     field[j] = -(i / lambda) sum_i w_i sigma_i e^{ikr}/r (1 - 1/(ikr)) cos(theta_ij)
+ * with lambda = 2 pi / k.  Pairs closer than 1e-12 m contribute nothing.
+ * src_sigma: complex [n_src] in the source set's slot order (RSI only; NULL
+ * for PISTON).  tgt_field: complex [n_tgt] in the target set's slot order,
+ * overwritten.  workspace: >= rsi_stage_workspace_bytes(...), 256-byte
+ * aligned; its contents are scratch.  Calls that share a workspace must be
+ * ordered on one stream.                                                   */
+int rsi_propagate_stage(const rsi_stage *st,
+                        const void *src_points, int64_t n_src, const double *src_sigma,
+                        const void *tgt_points, int64_t n_tgt, double *tgt_field,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* ---- interface transmission (step a4) ------------------------------------ */
+enum rsi_tmode {
+    RSI_T_GLOBAL = 0, /* one incidence angle: sin a1 = c1 C, sin a2 = c2 C        */
+    RSI_T_LOCAL = 1   /* per point: cos a1 = d . n_i, d = (c1 C, 0, sqrt(1-(c1 C)^2)),
+                         sin a2 = (c2/c1) sin a1                                   */
+};
+typedef struct rsi_interface {
+    int32_t mode;       /* enum rsi_tmode                                          */
+    int32_t reserved;
+    double rho1, c1;    /* medium the field arrives from                           */
+    double rho2, c2;    /* medium the field is transmitted into                    */
+    double snell_C;     /* Snell invariant sin(a)/c of the beam axis (s/m), Eq. root_searching */
+} rsi_interface;
+
+/* Step a4: sigma[i] = T12(a1_i) phi[i] with Eq. transmission_coefficient,
+ *   T12 = 2 rho1 c2 cos a1 / (rho2 c2 cos a1 + rho1 c1 cos a2) = (rho1/rho2)(1 + R12),
+ * cos a = i sqrt(sin^2 a - 1) past the critical angle.  phi and sigma are
+ * complex [n] in slot order; sigma may alias phi.                           */
+int rsi_interface_transmit(const rsi_interface *it, const void *points, int64_t n,
+                           const double *phi, double *sigma, void *stream);
+
+/* ---- field image (step a7) ------------------------------------------------- */
+enum rsi_image_format {
+    RSI_IMG_C128 = 0, /* complex double [nz][nx]                                */
+    RSI_IMG_C64 = 1,  /* complex float  [nz][nx]                                */
+    RSI_IMG_ABS32 = 2 /* float |k phi / v0| [nz][nx]                            */
+};
+/* out[j] = (k / v0) field[j] for the grid's nx*nz pixels (normalised
+ * velocity amplitude k phi / v0 of Fig. oblique_incidence).                */
+int rsi_field_image(const rsi_grid *g, const double *field, double k, double v0,
+                    int32_t format, void *out, void *stream);
+
+/* ---- measurement hooks (no counterpart in the paper) --------------------- */
+/* Number of kernels this library has enqueued in this process.             */
+uint64_t rsi_launch_count(void);
+
+/* Per-kernel timing of the source x target kernels.  While enabled, every
+ * rsi_propagate_stage call brackets its main kernel with CUDA events recorded
+ * on the call's stream.  rsi_timing_enable(1) clears the record and starts;
+ * rsi_timing_enable(0) stops.  rsi_timing_read(kind, ...) synchronises with
+ * the recorded events and returns, for the stages of that kind
+ * (RSI_STAGE_PISTON or RSI_STAGE_RSI): the summed kernel time in ms, the
+ * number of launches and the summed source x target pair count.            */
+int rsi_timing_enable(int32_t on);
+int rsi_timing_read(int32_t kind, double *total_ms, int64_t *launches, double *pairs);
+
+/* Throughput probes for the ALU roofline: `iters` iterations of 8
+ * independent dependency chains per thread of one operation,
+ *   RSI_UB_FFMA  fused multiply-add (FP32 pipe)
+ *   RSI_UB_RSQRT rsqrt.approx.f32   (MUFU)
+ *   RSI_UB_SIN   sin.approx.f32     (MUFU, after its range scaling)
+ * over `blocks` CTAs of 256 threads; `sink` (device, >= blocks*256 floats)
+ * receives one value per thread.  Time it with events on `stream`.         */
+enum rsi_ubench_kind { RSI_UB_FFMA = 0, RSI_UB_RSQRT = 1, RSI_UB_SIN = 2 };
+int rsi_ubench(int32_t kind, int32_t blocks, int32_t iters, float *sink, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSI_H */

@@ -23,6 +23,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import platform
 import subprocess
 import threading
 
@@ -43,7 +44,9 @@ _I64 = ctypes.c_int64
 def build(force: bool = False) -> str:
     """Compile rsi_oracle.c into oracle/_build/liboracle.so (gcc, -O2, IEEE)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
+    stamp = os.path.join(_BUILD, "machine.txt")
+    same_host = os.path.exists(stamp) and open(stamp).read().strip() == platform.machine()
+    if (not force and same_host and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
@@ -51,6 +54,8 @@ def build(force: bool = False) -> str:
            "-ffp-contract=off", "-o", tmp, _SRC, "-lm", "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
+    with open(stamp, "w") as f:
+        f.write(platform.machine())
     return _LIB_PATH
 
 

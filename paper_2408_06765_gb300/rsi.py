@@ -1,0 +1,345 @@
+"""ctypes binding of include/rsi.h (argument marshalling only).
+
+Every numerical step runs in librsi.so's CUDA kernels; this module only
+allocates device buffers with PyTorch, passes pointers, sizes and the current
+stream, and raises on a non-zero status.  There is no fallback: if the
+library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librsi.so")
+_lock = threading.Lock()
+_lib = None
+
+# --- constants mirrored from include/rsi.h -----------------------------------
+RSI_OK = 0
+PF = dict(IDX=0, SU=1, SV=2, X=3, Y=4, Z=5, NX=6, NY=7, NZ=8, W=9,
+          XH=10, XL=11, YH=12, YL=13, ZH=14, ZL=15)
+PF_DTYPE = {**{k: torch.int32 for k in ("IDX", "SU", "SV")},
+            **{k: torch.float64 for k in ("X", "Y", "Z", "NX", "NY", "NZ", "W")},
+            **{k: torch.float32 for k in ("XH", "XL", "YH", "YL", "ZH", "ZL")}}
+SURF = {"disk": 0, "rect": 1, "cyl": 2}
+STAGE_PISTON, STAGE_RSI = 0, 1
+PREC = {"fp64": 0, "fp32c": 1}
+NORMALS_Z, NORMALS_POINTS = 0, 1
+TMODE = {"global": 0, "local": 1}
+IMG = {"c128": 0, "c64": 1, "abs32": 2}
+
+SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes",
+           "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points",
+           "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_interface_transmit",
+           "rsi_field_image", "rsi_launch_count", "rsi_timing_enable", "rsi_timing_read",
+           "rsi_ubench"]
+UB = {"ffma": 0, "rsqrt": 1, "sin": 2}
+
+
+class Surface(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("scramble", ctypes.c_int32),
+                ("centre", ctypes.c_double * 3), ("tilt", ctypes.c_double),
+                ("a", ctypes.c_double), ("wx", ctypes.c_double), ("wy", ctypes.c_double),
+                ("R", ctypes.c_double)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("x1", ctypes.c_double), ("z0", ctypes.c_double),
+                ("z1", ctypes.c_double), ("y", ctypes.c_double), ("nx", ctypes.c_int32),
+                ("nz", ctypes.c_int32)]
+
+
+class Stage(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("precision", ctypes.c_int32), ("k", ctypes.c_double),
+                ("v0", ctypes.c_double), ("normals", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("tpt", ctypes.c_int32), ("splits", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Interface(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rho1", ctypes.c_double),
+                ("c1", ctypes.c_double), ("rho2", ctypes.c_double), ("c2", ctypes.c_double),
+                ("snell_C", ctypes.c_double)]
+
+
+class RSIError(RuntimeError):
+    def __init__(self, what: str, code: int, msg: str):
+        super().__init__(f"{what} failed ({code}): {msg}")
+        self.code = code
+
+
+def load(path: str | None = None):
+    """Load librsi.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"librsi.so not built ({p}); run paper_2408_06765_gb300.build")
+        L = ctypes.CDLL(p)
+        vp, i32, i64, u32, u64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t)
+        L.rsi_version.restype = ctypes.c_int
+        L.rsi_last_error.restype = ctypes.c_char_p
+        L.rsi_sync_status.argtypes = [vp]
+        L.rsi_points_bytes.restype = sz
+        L.rsi_points_bytes.argtypes = [i64]
+        L.rsi_points_offset.restype = i64
+        L.rsi_points_offset.argtypes = [i32, i64]
+        L.rsi_make_qmc_points.argtypes = [ctypes.POINTER(Surface), u64, u32, i64, vp, sz, vp]
+        L.rsi_grid_points.argtypes = [ctypes.POINTER(Grid), vp, sz, vp]
+        L.rsi_stage_workspace_bytes.restype = sz
+        L.rsi_stage_workspace_bytes.argtypes = [ctypes.POINTER(Stage), i64, i64]
+        L.rsi_propagate_stage.argtypes = [ctypes.POINTER(Stage), vp, i64, vp, vp, i64, vp, vp, sz, vp]
+        L.rsi_interface_transmit.argtypes = [ctypes.POINTER(Interface), vp, i64, vp, vp, vp]
+        L.rsi_field_image.argtypes = [ctypes.POINTER(Grid), vp, ctypes.c_double, ctypes.c_double,
+                                      i32, vp, vp]
+        L.rsi_launch_count.restype = u64
+        L.rsi_timing_enable.argtypes = [i32]
+        L.rsi_timing_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        L.rsi_ubench.argtypes = [i32, i32, i32, vp, vp]
+        _lib = L
+        return L
+
+
+def _check(rc: int, what: str):
+    if rc != RSI_OK:
+        raise RSIError(what, rc, load().rsi_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+# ---------------------------------------------------------------------------
+# point sets
+# ---------------------------------------------------------------------------
+class Points:
+    """A point set: one device buffer in the layout of include/rsi.h."""
+
+    def __init__(self, n: int, device="cuda"):
+        L = load()
+        self.n = int(n)
+        self.nbytes = int(L.rsi_points_bytes(self.n))
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        if self.buf.data_ptr() % 256:
+            raise RuntimeError("point buffer is not 256-byte aligned")
+
+    def field(self, name: str) -> torch.Tensor:
+        """Typed view of one field (IDX/SU/SV are uint32 stored as int32)."""
+        off = int(load().rsi_points_offset(PF[name], self.n))
+        dt = PF_DTYPE[name]
+        nb = self.n * torch.empty(0, dtype=dt).element_size()
+        return self.buf[off:off + nb].view(dt)
+
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+
+def surface_struct(surf: dict, scramble: bool = True) -> Surface:
+    s = Surface()
+    s.kind = SURF[surf["kind"]]
+    s.scramble = 1 if scramble else 0
+    for i, v in enumerate(surf.get("centre", (0.0, 0.0, 0.0))):
+        s.centre[i] = float(v)
+    s.tilt = float(surf.get("tilt", 0.0))
+    s.a = float(surf.get("a", 0.0))
+    s.wx = float(surf.get("wx", 0.0))
+    s.wy = float(surf.get("wy", 0.0))
+    s.R = float(surf.get("R", 0.0))
+    return s
+
+
+def make_qmc_points(surf: dict, seed: int, set_id: int, n: int, scramble: bool = True,
+                    device="cuda", stream=None, out: Points | None = None) -> Points:
+    pts = out if out is not None else Points(n, device)
+    s = surface_struct(surf, scramble)
+    _check(load().rsi_make_qmc_points(ctypes.byref(s), int(seed) & (2**64 - 1), int(set_id), int(n),
+                                      pts.ptr(), pts.nbytes, _stream(stream)), "rsi_make_qmc_points")
+    return pts
+
+
+def grid_struct(g: dict) -> Grid:
+    G = Grid()
+    G.x0, G.x1, G.z0, G.z1 = (float(g[k]) for k in ("x0", "x1", "z0", "z1"))
+    G.y = float(g.get("y", 0.0))
+    G.nx, G.nz = int(g["nx"]), int(g["nz"])
+    return G
+
+
+def grid_points(g: dict, device="cuda", stream=None, out: Points | None = None) -> Points:
+    G = grid_struct(g)
+    pts = out if out is not None else Points(G.nx * G.nz, device)
+    _check(load().rsi_grid_points(ctypes.byref(G), pts.ptr(), pts.nbytes, _stream(stream)),
+           "rsi_grid_points")
+    return pts
+
+
+# ---------------------------------------------------------------------------
+# stages
+# ---------------------------------------------------------------------------
+def stage_struct(kind: int, precision: str, k: float, v0: float = 1.0, normals: int = NORMALS_Z,
+                 tile: int = 0, tpt: int = 0, splits: int = 0, variant: int = 0) -> Stage:
+    st = Stage()
+    st.kind, st.precision = int(kind), PREC[precision]
+    st.k, st.v0 = float(k), float(v0)
+    st.normals, st.tile, st.tpt, st.splits, st.variant = (int(normals), int(tile), int(tpt),
+                                                          int(splits), int(variant))
+    return st
+
+
+def workspace_bytes(st: Stage, n_src: int, n_tgt: int) -> int:
+    nb = int(load().rsi_stage_workspace_bytes(ctypes.byref(st), int(n_src), int(n_tgt)))
+    if nb == 0:
+        raise RSIError("rsi_stage_workspace_bytes", -1, load().rsi_last_error().decode())
+    return nb
+
+
+class Workspace:
+    """Grow-only device scratch buffer shared by successive stage calls."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+def propagate_stage(st: Stage, src: Points, sigma, tgt: Points, out=None,
+                    workspace: Workspace | None = None, stream=None) -> torch.Tensor:
+    """Field at `tgt` (complex128 [n_tgt], slot order) from sources `src`."""
+    if out is None:
+        out = torch.empty(tgt.n, dtype=torch.complex128, device=tgt.buf.device)
+    ws = (workspace or Workspace(tgt.buf.device)).get(workspace_bytes(st, src.n, tgt.n))
+    _check(load().rsi_propagate_stage(ctypes.byref(st), src.ptr(), src.n, _ptr(sigma), tgt.ptr(),
+                                      tgt.n, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+           "rsi_propagate_stage")
+    return out
+
+
+def interface_struct(m_in: dict, m_out: dict, snell_C: float, mode: str = "global") -> Interface:
+    it = Interface()
+    it.mode = TMODE[mode]
+    it.rho1, it.c1 = float(m_in["rho"]), float(m_in["c"])
+    it.rho2, it.c2 = float(m_out["rho"]), float(m_out["c"])
+    it.snell_C = float(snell_C)
+    return it
+
+
+def interface_transmit(pts: Points, phi, m_in: dict, m_out: dict, snell_C: float,
+                       mode: str = "global", out=None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty_like(phi)
+    it = interface_struct(m_in, m_out, snell_C, mode)
+    _check(load().rsi_interface_transmit(ctypes.byref(it), pts.ptr(), pts.n, _ptr(phi), _ptr(out),
+                                         _stream(stream)), "rsi_interface_transmit")
+    return out
+
+
+def field_image(g: dict, field, k: float, v0: float = 1.0, fmt: str = "c128", out=None,
+                stream=None) -> torch.Tensor:
+    G = grid_struct(g)
+    if out is None:
+        dt = {"c128": torch.complex128, "c64": torch.complex64, "abs32": torch.float32}[fmt]
+        out = torch.empty((G.nz, G.nx), dtype=dt, device=field.device)
+    _check(load().rsi_field_image(ctypes.byref(G), _ptr(field), float(k), float(v0), IMG[fmt],
+                                  _ptr(out), _stream(stream)), "rsi_field_image")
+    return out
+
+
+def sync_status(stream=None):
+    _check(load().rsi_sync_status(_stream(stream)), "rsi_sync_status")
+
+
+def launch_count() -> int:
+    """Kernels this library has enqueued in this process."""
+    return int(load().rsi_launch_count())
+
+
+def timing_enable(on: bool = True):
+    _check(load().rsi_timing_enable(1 if on else 0), "rsi_timing_enable")
+
+
+def timing_read(kind: int):
+    """(total ms, launches, pairs) of the main stage kernels of `kind` since enable."""
+    ms, n, pr = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(load().rsi_timing_read(int(kind), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pr)),
+           "rsi_timing_read")
+    return ms.value, n.value, pr.value
+
+
+def ubench(kind: str, blocks: int, iters: int, sink, stream=None):
+    _check(load().rsi_ubench(UB[kind], int(blocks), int(iters), _ptr(sink), _stream(stream)),
+           "rsi_ubench")
+
+
+# ---------------------------------------------------------------------------
+# the stage chain of a workload description (paper_2408_06765_gb300.workloads)
+# ---------------------------------------------------------------------------
+def wavenumber(freq: float, c: float) -> float:
+    return 2.0 * math.pi * float(freq) / float(c)
+
+
+def snell_invariant(cfg: dict) -> float:
+    return math.sin(float(cfg["piston"].get("tilt", 0.0))) / float(cfg["media"][0]["c"])
+
+
+class ChainResult:
+    def __init__(self, image, field, ifaces):
+        self.image = image    # complex [nz][nx], k phi / v0 (or None)
+        self.field = field    # complex128 field at the targets (slot order)
+        self.ifaces = ifaces  # [(Points, phi on the points)] when kept
+
+
+def run_chain(cfg: dict, precision: str | None = None, targets: Points | None = None,
+              keep: bool = False, fmt: str = "c128", workspace: Workspace | None = None,
+              stage_opts: dict | None = None, stream=None, device="cuda") -> ChainResult:
+    """piston -> interfaces -> targets (default: the image grid) on the GPU."""
+    prec = precision or cfg.get("precision", "fp32c")
+    opts = stage_opts or {}
+    ws = workspace or Workspace(device)
+    seed = int(cfg.get("seed", 0))
+    freq, v0 = float(cfg["freq"]), float(cfg.get("v0", 1.0))
+    media = cfg["media"]
+    C = snell_invariant(cfg)
+    mode = cfg.get("tmode", "global")
+    pc = cfg["piston"]
+    piston = make_qmc_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]),
+                             device=device, stream=stream)
+    ifaces = [make_qmc_points(it, seed, int(it["set_id"]), int(it["n"]), device=device, stream=stream)
+              for it in cfg["interfaces"]]
+    use_grid = targets is None
+    if use_grid:
+        targets = grid_points(cfg["grid"], device=device, stream=stream)
+    kept = []
+    first_tgt = ifaces[0] if ifaces else targets
+    st = stage_struct(STAGE_PISTON, prec, wavenumber(freq, media[0]["c"]), v0, **opts)
+    phi = propagate_stage(st, piston, None, first_tgt, workspace=ws, stream=stream)
+    for s, pts in enumerate(ifaces):
+        if keep:
+            kept.append((pts, phi))
+        sigma = interface_transmit(pts, phi, media[s], media[s + 1], C, mode, stream=stream)
+        nxt = ifaces[s + 1] if s + 1 < len(ifaces) else targets
+        normals = NORMALS_POINTS if cfg["interfaces"][s]["kind"] != "rect" else NORMALS_Z
+        st = stage_struct(STAGE_RSI, prec, wavenumber(freq, media[s + 1]["c"]), 1.0, normals, **opts)
+        phi = propagate_stage(st, pts, sigma, nxt, workspace=ws, stream=stream)
+    image = None
+    if use_grid:
+        k_last = wavenumber(freq, media[len(ifaces)]["c"])
+        image = field_image(cfg["grid"], phi, k_last, v0, fmt, stream=stream)
+    return ChainResult(image, phi, kept)
