@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
+    ap.add_argument("--sweep", action="store_true",
+                    help="with --case stage: time every tile / targets-per-thread / variant")
     return ap.parse_args()
 
 
@@ -403,24 +405,28 @@ def run_stage_case(args):
     pts = rsi.make_qmc_points(it, 0, it["set_id"], it["n"])
     grid = rsi.grid_points(cfg["grid"])
     sigma = torch.ones(it["n"], dtype=torch.complex128, device="cuda")
-    st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", rsi.wavenumber(cfg["freq"], 5900.0),
-                          normals=rsi.NORMALS_Z, tile=args.tile, tpt=args.tpt, variant=args.variant)
     ws = rsi.Workspace()
-    out = None
-    times = []
-    for _ in range(args.warmup + args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        out = rsi.propagate_stage(st, pts, sigma, grid, workspace=ws)
-        e1.record()
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-    rsi.sync_status()
-    ms = min(times[args.warmup:])
-    pairs = it["n"] * grid.n
-    print(json.dumps({"case": "stage", "ms": ms, "gpair_per_s": pairs / ms / 1e6,
-                      "variant": args.variant, "tile": args.tile, "tpt": args.tpt,
-                      "checksum": float(out.abs().sum().item())}), flush=True)
+    shapes = [(args.tile, args.tpt, args.variant)]
+    if args.sweep:
+        shapes = [(t, q, v) for t in (64, 128, 256, 512) for q in (2, 4) for v in (1, 2)]
+    for tile, tpt, variant in shapes:
+        st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", rsi.wavenumber(cfg["freq"], 5900.0),
+                              normals=rsi.NORMALS_Z, tile=tile, tpt=tpt, variant=variant)
+        out = None
+        times = []
+        for _ in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = rsi.propagate_stage(st, pts, sigma, grid, workspace=ws)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        rsi.sync_status()
+        ms = min(times[args.warmup:])
+        pairs = it["n"] * grid.n
+        print(json.dumps({"case": "stage", "ms": ms, "gpair_per_s": pairs / ms / 1e6,
+                          "variant": variant, "tile": tile, "tpt": tpt,
+                          "checksum": float(out.abs().sum().item())}), flush=True)
 
 
 def main():

@@ -129,7 +129,19 @@ int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p) {
         return rsi_fail(RSI_E_INVAL, "more than 2^31 sources or targets");
     if (!(st.k > 0) || !isfinite(st.k)) return rsi_fail(RSI_E_INVAL, "wavenumber must be finite and > 0");
     const bool fp32 = st.precision == RSI_PREC_FP32C;
-    p.S = st.tile ? st.tile : (fp32 ? 256 : 64);
+    if (st.tile) {
+        p.S = st.tile;
+    } else if (fp32) {
+        // The FP32 offset term k (r - R) carries ~2^-23 k (tile radius) of
+        // phase error.  Cell-ordered QMC tiles of S points cover S/n of the
+        // surface, so keep S <= n/64 for small sets (tiles of at most 1/64 of
+        // the surface), between 32 and 256 sources.
+        int64_t cap = n_src / 64;
+        p.S = 256;
+        while (p.S > 32 && p.S > cap) p.S >>= 1;
+    } else {
+        p.S = 64;
+    }
     if (!valid_tile(p.S)) return rsi_fail(RSI_E_INVAL, "tile must be 32, 64, 128, 256 or 512 (got %d)", st.tile);
     if (fp32) {
         p.tpt = st.tpt ? st.tpt : (n_tgt >= int64_t(4) * fp32_threads() * rsi_num_sms() ? 4 : 2);

@@ -1,0 +1,62 @@
+"""Write the stored expected values of the full-size parity tests.
+
+Calls only the FP64 oracle (oracle/) and the workload descriptions.  For each
+full-size workload it runs the whole oracle chain (piston -> every interface)
+and evaluates the final stage on a seeded sample of image pixels, then stores
+pixel indices and normalised values k phi / v0 as JSON text:
+
+    python tests/golden/make_golden.py [name ...]
+
+Workloads: c2 at 2.25, 5 and 10 MHz (2^16 x 2^18 points, 512^2 image) and the
+multilayer c3 workload, flat and curved (9 interfaces of 2^16 points).
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_2408_06765_gb300 import workloads as W  # noqa: E402
+
+N_PIXELS = 1024
+
+
+def cases():
+    out = {f"c2_{f / 1e6:g}MHz": W.c2_full_image(f) for f in W.C2_FREQS}
+    out["c3_flat"] = W.c3_multilayer(curved=False)
+    out["c3_curved"] = W.c3_multilayer(curved=True)
+    return out
+
+
+def make(name: str, cfg: dict):
+    g = cfg["grid"]
+    n_pix = int(g["nx"]) * int(g["nz"])
+    rng = np.random.default_rng(1234)
+    pix = np.sort(rng.choice(n_pix, N_PIXELS, replace=False))
+    grid = oracle.grid_points(g)
+    targets = {k: grid[k][pix] for k in ("x", "y", "z")}
+    t0 = time.time()
+    phi, _ = oracle.chain(cfg, targets)
+    k_last = oracle.wavenumber(cfg["freq"], cfg["media"][len(cfg["interfaces"])]["c"])
+    val = (k_last / float(cfg["v0"])) * phi
+    rec = {"workload": name, "source": "oracle.chain (FP64 CPU oracle), tests/golden/make_golden.py",
+           "pixels": pix.tolist(), "re": val.real.tolist(), "im": val.imag.tolist(),
+           "oracle_seconds": time.time() - t0}
+    with open(os.path.join(HERE, f"{name}.json"), "w") as f:
+        json.dump(rec, f)
+    print(f"{name}: {time.time() - t0:.1f} s", flush=True)
+
+
+if __name__ == "__main__":
+    want = sys.argv[1:]
+    for name, cfg in cases().items():
+        if not want or name in want:
+            make(name, cfg)

@@ -88,10 +88,12 @@ def test_qmc_points_bit_exact(surf, n, seed, set_id):
     assert np.array_equal(p["SU"], su_o[idx]) and np.array_equal(p["SV"], sv_o[idx])
     check_cell_order(idx, p["SU"], p["SV"], n)
     ref = oracle.map_points(surf, su_o, sv_o)
+    # FP64 geometry: a few ulps of the largest term entering each coordinate
+    extent = sum(abs(c) for c in surf["centre"]) + 2 * max(surf.get(k, 0.0) for k in ("a", "wx", "wy", "R"))
     for key in ("x", "y", "z", "nx", "ny", "nz", "w"):
         got, want = p[key.upper()], ref[key][idx]
-        scale = max(1e-300, float(np.max(np.abs(want))))
-        assert np.max(np.abs(got - want)) <= 4e-16 * scale + 1e-300, key
+        scale = extent if key in ("x", "y", "z") else float(np.max(np.abs(want)))
+        assert np.max(np.abs(got - want)) <= 8 * 2.0**-52 * scale + 1e-300, key
     for c in ("X", "Y", "Z"):
         assert np.array_equal(p[c + "H"], p[c].astype(np.float32))
         assert np.array_equal(p[c + "L"], (p[c] - p[c + "H"].astype(np.float64)).astype(np.float32))
@@ -176,26 +178,38 @@ def test_launch_shapes_agree(opts):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
 def test_coincident_targets_contribute_nothing(prec):
-    # an interface propagated onto its own points: every target coincides with
-    # one source, whose term is dropped (both sides)
-    surf = {"kind": "rect", "centre": (0.0, 0.0, 0.02), "wx": 0.02, "wy": 0.02}
-    pts = rsi.make_qmc_points(surf, 0, 1, 700)
-    hp = host_points(pts)
+    # a surface propagated onto its own points: every target coincides with one
+    # source, whose term is dropped (both sides)
     rng = np.random.default_rng(0)
-    sig = rng.normal(size=700) + 1j * rng.normal(size=700)
     k = 2 * math.pi * 2e6 / 1480.0
-    st = rsi.stage_struct(rsi.STAGE_RSI, prec, k, normals=rsi.NORMALS_Z)
-    out = rsi.propagate_stage(st, pts, torch.tensor(sig, device="cuda"), pts)
+    sig = rng.normal(size=700) + 1j * rng.normal(size=700)
+    sig_d = torch.tensor(sig, device="cuda")
+    # flat patch: every chord lies in the plane, cos(theta) = 0, the RSI field is 0
+    flat = rsi.make_qmc_points({"kind": "rect", "centre": (0.0, 0.0, 0.02), "wx": 0.02, "wy": 0.02},
+                               0, 1, 700)
+    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_RSI, prec, k, normals=rsi.NORMALS_Z),
+                              flat, sig_d, flat)
     rsi.sync_status()
+    hp = host_points(flat)
+    src = {"x": hp["X"], "y": hp["Y"], "z": hp["Z"], "nx": hp["NX"], "ny": hp["NY"], "nz": hp["NZ"],
+           "w": hp["W"]}
+    assert np.all(out.cpu().numpy() == 0) and np.all(oracle.rsi_field(src, sig, src, k) == 0)
+    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_PISTON, prec, k), flat, None, flat)
+    rsi.sync_status()
+    ref = oracle.piston_field(src, src, k)
+    assert np.all(np.isfinite(out.cpu().numpy()))
+    assert rel_l2(out.cpu().numpy(), ref) <= TOL[prec]
+    # curved surface: chords are not normal to the surface normals
+    cyl = rsi.make_qmc_points({"kind": "cyl", "centre": (0.0, 0.0, 0.02), "wx": 0.03, "wy": 0.03,
+                               "R": 0.02}, 0, 2, 700)
+    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_RSI, prec, k, normals=rsi.NORMALS_POINTS),
+                              cyl, sig_d, cyl)
+    rsi.sync_status()
+    hp = host_points(cyl)
     src = {"x": hp["X"], "y": hp["Y"], "z": hp["Z"], "nx": hp["NX"], "ny": hp["NY"], "nz": hp["NZ"],
            "w": hp["W"]}
     ref = oracle.rsi_field(src, sig, src, k)
     assert np.all(np.isfinite(out.cpu().numpy()))
-    assert rel_l2(out.cpu().numpy(), ref) <= TOL[prec]
-    # piston kind onto its own points as well
-    st = rsi.stage_struct(rsi.STAGE_PISTON, prec, k)
-    out = rsi.propagate_stage(st, pts, None, pts)
-    ref = oracle.piston_field(src, src, k)
     assert rel_l2(out.cpu().numpy(), ref) <= TOL[prec]
 
 
