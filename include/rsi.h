@@ -167,6 +167,30 @@ int rsi_propagate_stage(const rsi_stage *st,
                         const void *tgt_points, int64_t n_tgt, double *tgt_field,
                         void *workspace, size_t workspace_bytes, void *stream);
 
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot give the library device memory for scratch (a latency-bound
+ * acquisition loop that must not call cudaMalloc, a plug-in whose host owns
+ * every device allocation, a foreign-language host that only receives
+ * finished buffers).  Same sums, arguments and results as
+ * rsi_propagate_stage, but the scratch is a fixed area of
+ * RSI_NOALLOC_SCRATCH_BYTES compiled into the library (held by every GPU that
+ * loads it until the process exits); nothing is allocated.
+ *   - A stage whose scratch need exceeds the area (staged source tiles plus
+ *     partial sums; for FP32C about 2 million sources on few targets) is
+ *     rejected with RSI_E_NOMEM before anything is enqueued.  With splits = 0
+ *     the call first retries with fewer source splits to fit.
+ *   - The first call on a device looks up the area's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the area: calls whose GPU work overlaps
+ *     (other streams, other host threads) race; order them on one stream.
+ *     No part of the area has to start at zero.                            */
+#define RSI_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int rsi_propagate_stage_noalloc(const rsi_stage *st,
+                                const void *src_points, int64_t n_src, const double *src_sigma,
+                                const void *tgt_points, int64_t n_tgt, double *tgt_field,
+                                void *stream);
+
 /* ---- interface transmission (step a4) ------------------------------------ */
 enum rsi_tmode {
     RSI_T_GLOBAL = 0, /* one incidence angle: sin a1 = c1 C, sin a2 = c2 C        */
