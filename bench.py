@@ -30,12 +30,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# Per-pair work of the FP32C kernels as formulated (counted from the source of
-# csrc/stage_fp32.cu, reciprocal variant): FP32-pipe instructions, MUFU
-# operations, shared-memory loads per pair at 4 targets per thread.
+# Per-pair work of the FP32C kernels as formulated (far path, Newton update of
+# r, counted from csrc/stage_fp32_body.cuh): FP32-pipe instructions, MUFU
+# operations, and shared-memory loads per pair at 2 targets per thread (two
+# 16-byte records per source shared by the thread's 2 targets).
 OPS = {
-    "rsi": {"fp32": 27, "mufu": 4, "lds": 0.5},
-    "piston": {"fp32": 20, "mufu": 4, "lds": 0.5},
+    "rsi": {"fp32": 23, "mufu": 3, "lds": 1.0},
+    "piston": {"fp32": 13, "mufu": 3, "lds": 1.0},
 }
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "rsi_pair_terms_per_s"

@@ -36,7 +36,7 @@ def sources():
 
 
 def _deps():
-    inc = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    inc = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]  # any header
     inc.append(os.path.join(os.path.dirname(HERE), "include", "rsi.h"))
     return inc
 

@@ -9,7 +9,7 @@
 //                  target offsets are), |p|^2, then
 //                  PISTON  (A, 0, 0, 0)            A = -v0 w / (2 pi)
 //                  RSI     (B.re, B.im, C.re, C.im) B = -w sigma / (2 pi), C = i k B
-//                  [+ (nx, ny, nz, 0) for per-point normals]
+//                  [+ (nx, ny, nz, n.p) for per-point normals]
 //   FP64 record  : (x, y, z, B.re, B.im, nx, ny, nz)  (PISTON: B = (A, 0))
 // Padding records (past the last source) have zero amplitude and sit 4 m away.
 #pragma once
@@ -52,6 +52,7 @@ struct StageArgs {
 };
 
 size_t fp32_record_bytes(int kind, int normals);
+double stage_amp_scale(const rsi_stage& st);  // -v0/(2 pi) (piston) or -1/(2 pi) (RSI)
 size_t fp64_record_bytes();
 
 int launch_prep_fp32(const rsi_stage& st, const PointsView& src, int64_t n_src, const double2* sigma,

@@ -1,0 +1,393 @@
+// stage_fp32_body.cuh -- device code of the FP32C source x target sum (steps
+// a3, a5), shared by the single-stage kernel (stage_fp32.cu) and the
+// persistent multi-instance kernel (batch.cu).
+//
+// Every target keeps, per source tile, a reference built in double-float
+// arithmetic: D = Q - c (c = tile centre), R = |D| and the phase
+// tau = k R mod 2 pi.  A pair then needs only FP32 work on small offsets
+// p = P - c: t = |p|^2 - 2 D.p = r^2 - R^2, and r - R follows without
+// cancellation from a Newton step on r^2 = R^2 + t (or from t / (R + r)), so
+// the phase tau + k (r - R) is accurate to about 2^-23 k |r - R| <= 2^-23 k
+// (tile radius) instead of 2^-24 k r.
+//
+// Two pair paths, chosen per (warp, tile):
+//   far   every target of the warp is more than two tile radii from the tile
+//         centre, so r > R/2 > 0: r^2 = R^2 + t is accurate to a few ulps and
+//         r - R is exact to form; no coincidence test is needed.
+//   near  r^2 = |D - p|^2 from the FP32 offsets (accurate for r << R), and
+//         pairs closer than 1e-12 m are dropped.
+// Tiles arrive in shared memory by bulk copy (cp.async.bulk) on mbarriers,
+// RSI_PIPE_STAGES deep; each thread owns TPT targets and loops over the
+// tile; tile sums are FP32 and are added into a double-float accumulator.
+#pragma once
+
+#include <math.h>
+
+#include "stage.cuh"
+
+namespace rsi_fp32 {
+
+constexpr int kThreads = 256;
+
+struct TgtRef {
+    float Dx, Dy, Dz, mx, my, mz, R, R2, tau;
+};
+
+// double-float reference of one target against one tile centre
+__device__ __forceinline__ TgtRef target_reference(float qxh, float qxl, float qyh, float qyl, float qzh,
+                                                   float qzl, const float* c, float kh, float kl,
+                                                   const TwoPiSplit& tp) {
+    float dxh, dxl, dyh, dyl, dzh, dzl;
+    df_diff(qxh, qxl, c[0], c[1], dxh, dxl);
+    df_diff(qyh, qyl, c[2], c[3], dyh, dyl);
+    df_diff(qzh, qzl, c[4], c[5], dzh, dzl);
+    float ax, axl, ay, ayl, az, azl, sh, sl;
+    df_sqr(dxh, dxl, ax, axl);
+    df_sqr(dyh, dyl, ay, ayl);
+    df_sqr(dzh, dzl, az, azl);
+    df_add_pos(ax, axl, ay, ayl, sh, sl);
+    df_add_pos(sh, sl, az, azl, sh, sl);
+    float Rh = 0.0f, Rl = 0.0f;
+    if (sh > 0.0f) {
+        // one Newton step from the FP32 reciprocal square root: ~2^-44 relative
+        float y = rsqrtf(sh);
+        float r0 = __fmul_rn(sh, y);
+        float p, pe;
+        two_prod(r0, r0, p, pe);
+        float e = __fadd_rn(__fsub_rn(__fsub_rn(sh, p), pe), sl);
+        fast_two_sum(r0, __fmul_rn(e, __fmul_rn(0.5f, y)), Rh, Rl);
+    }
+    // k R as a double-float, reduced modulo 2 pi (Cody & Waite)
+    float ph, pl;
+    two_prod(kh, Rh, ph, pl);
+    pl = __fmaf_rn(kh, Rl, __fmaf_rn(kl, Rh, pl));
+    float n = rintf(__fmul_rn(ph, tp.inv));
+    float x = __fmaf_rn(-n, tp.p1, ph);
+    x = __fmaf_rn(-n, tp.p2, x);
+    x = __fmaf_rn(-n, tp.p3, x);
+    x = __fadd_rn(x, pl);
+    TgtRef t;
+    t.Dx = dxh;
+    t.Dy = dyh;
+    t.Dz = dzh;
+    t.mx = -2.0f * dxh;
+    t.my = -2.0f * dyh;
+    t.mz = -2.0f * dzh;
+    t.R = Rh;
+    t.R2 = Rh * Rh;
+    t.tau = x;
+    return t;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// the source term once the phase u and 1/r are known
+template <int KIND, int NORM>
+__device__ __forceinline__ void accumulate(float u, float ir, float nd, const float4& b, float& acc_r,
+                                           float& acc_i) {
+    float s, c;
+    __sincosf(u, &s, &c);
+    if (KIND == RSI_STAGE_PISTON) {
+        float amp = b.x * ir;
+        acc_r = fmaf(amp, c, acc_r);
+        acc_i = fmaf(amp, s, acc_i);
+    } else {
+        float h = nd * (ir * ir);        // cos(theta) / r
+        float vr = fmaf(-ir, b.x, b.z);  // B (ik - 1/r)
+        float vi = fmaf(-ir, b.y, b.w);
+        float wr = fmaf(vr, c, -vi * s);
+        float wi = fmaf(vr, s, vi * c);
+        acc_r = fmaf(h, wr, acc_r);
+        acc_i = fmaf(h, wi, acc_i);
+    }
+}
+
+// near path: one source (records a, b[, n]) onto one target reference
+template <int KIND, int NORM, int VAR>
+__device__ __forceinline__ void pair_near(const TgtRef& t, const float4& a, const float4& b, const float4& nr,
+                                          float k, float& acc_r, float& acc_i) {
+    float dx = t.Dx - a.x, dy = t.Dy - a.y, dz = t.Dz - a.z;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float tt = fmaf(t.mx, a.x, fmaf(t.my, a.y, fmaf(t.mz, a.z, a.w)));  // r^2 - R^2
+    float ir = rsqrt_approx(r2);
+    ir = r2 > 1e-24f ? ir : 0.0f;  // pairs closer than 1e-12 m contribute nothing
+    float dr;
+    if (VAR == 1) {
+        float r = r2 * ir;
+        dr = __fdividef(tt, fmaxf(t.R + r, 1e-30f));
+    } else {
+        float r0 = r2 * ir;
+        float am = t.R - r0;
+        float e = fmaf(am, t.R + r0, tt);  // r^2 - r0^2
+        dr = fmaf(e, 0.5f * ir, -am);
+    }
+    float nd = (NORM == RSI_NORMALS_Z) ? dz : fmaf(nr.x, dx, fmaf(nr.y, dy, nr.z * dz));
+    accumulate<KIND, NORM>(fmaf(k, dr, t.tau), ir, nd, b, acc_r, acc_i);
+}
+
+// far path: R > 2 (tile radius), so r / R lies in (1/2, 3/2)
+template <int KIND, int NORM, int VAR>
+__device__ __forceinline__ void pair_far(const TgtRef& t, const float4& a, const float4& b, const float4& nr,
+                                         float k, float& acc_r, float& acc_i) {
+    float tt = fmaf(t.mx, a.x, fmaf(t.my, a.y, fmaf(t.mz, a.z, a.w)));  // r^2 - R^2
+    float r2 = t.R2 + tt;
+    float ir = rsqrt_approx(r2);
+    float r0 = r2 * ir;
+    float dr;
+    if (VAR == 1) {
+        dr = __fdividef(tt, t.R + r0);
+    } else {
+        float am = r0 - t.R;                // exact: r0 and R within a factor 2
+        float e = fmaf(-am, t.R + r0, tt);  // r^2 - r0^2, accurate to 2^-24 |t|
+        dr = fmaf(e, 0.5f * ir, am);
+    }
+    float nd;
+    if (NORM == RSI_NORMALS_Z)
+        nd = t.Dz - a.z;
+    else
+        nd = fmaf(nr.x, t.Dx, fmaf(nr.y, t.Dy, fmaf(nr.z, t.Dz, -nr.w)));  // n.D - n.p
+    accumulate<KIND, NORM>(fmaf(k, dr, t.tau), ir, nd, b, acc_r, acc_i);
+}
+
+// One CTA's share of a stage: targets j0 .. j0 + TPT*kThreads - 1 against
+// the `ntile` staged tiles starting at `t_begin`.
+struct BlockWork {
+    const uint8_t* tiles;
+    uint32_t tile_bytes;
+    int S;
+    int t_begin, ntile;
+    TgtView tgt;
+    int64_t n_tgt, j0;
+    float kh, kl;
+    TwoPiSplit tp;
+    double2* out;  // out[j] for the targets of this block
+    int* status;
+};
+
+// Shared memory: RSI_PIPE_STAGES tile buffers, then one mbarrier per buffer
+// (initialised once per CTA).  `uses` counts buffer fills of this CTA so far
+// and keeps the mbarrier phases consistent across successive calls.
+// Returns false (after recording RSI_DEV_TIMEOUT) if a bounded wait expired.
+template <int KIND, int NORM, int TPT, int VAR>
+__device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uint64_t* bars, uint32_t& uses) {
+    const int tid = threadIdx.x;
+    const int rec_f4 = (KIND == RSI_STAGE_RSI && NORM == RSI_NORMALS_POINTS) ? 3 : 2;
+    int64_t jt[TPT];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+        int64_t j = w.j0 + int64_t(q) * kThreads + tid;
+        jt[q] = j < w.n_tgt ? j : w.n_tgt - 1;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < RSI_PIPE_STAGES && s < w.ntile; ++s) {
+            const uint32_t b = (uses + s) % RSI_PIPE_STAGES;
+            uint32_t bar = smem_u32(&bars[b]);
+            mbar_expect_tx(bar, w.tile_bytes);
+            bulk_g2s(smem_u32(smem + b * w.tile_bytes), w.tiles + size_t(w.t_begin + s) * w.tile_bytes,
+                     w.tile_bytes, bar);
+        }
+    }
+    float hr[TPT], lr[TPT], hi[TPT], li[TPT];
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) hr[q] = lr[q] = hi[q] = li[q] = 0.0f;
+    const float k = w.kh;
+    int failed_at = -1;
+
+    for (int it = 0; it < w.ntile; ++it) {
+        const uint32_t u = uses + it;
+        const uint32_t buf = u % RSI_PIPE_STAGES;
+        bool ok = mbar_wait_bounded(smem_u32(&bars[buf]), (u / RSI_PIPE_STAGES) & 1u);
+        if (__syncthreads_or(!ok)) {
+            failed_at = it;
+            break;
+        }
+        const uint8_t* tile = smem + buf * w.tile_bytes;
+        const float* hdr = reinterpret_cast<const float*>(tile);
+        const float4* rec = reinterpret_cast<const float4*>(tile + RSI_TILE_HDR_BYTES);
+        TgtRef ref[TPT];
+        float ar[TPT], ai[TPT];
+        const float far_min = 2.0f * hdr[6];  // twice the tile radius
+        bool far_lane = true;
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            const int64_t j = jt[q];
+            ref[q] = target_reference(__ldg(w.tgt.xh + j), __ldg(w.tgt.xl + j), __ldg(w.tgt.yh + j),
+                                      __ldg(w.tgt.yl + j), __ldg(w.tgt.zh + j), __ldg(w.tgt.zl + j), hdr, w.kh,
+                                      w.kl, w.tp);
+            far_lane = far_lane && ref[q].R > far_min && ref[q].R > 0.0f;
+            ar[q] = 0.0f;
+            ai[q] = 0.0f;
+        }
+        if (__all_sync(0xffffffffu, far_lane)) {
+#pragma unroll 2
+            for (int i = 0; i < w.S; ++i) {
+                const float4 ra = rec[i * rec_f4];
+                const float4 rb = rec[i * rec_f4 + 1];
+                const float4 rn = (rec_f4 == 3) ? rec[i * rec_f4 + 2] : make_float4(0.f, 0.f, 1.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) pair_far<KIND, NORM, VAR>(ref[q], ra, rb, rn, k, ar[q], ai[q]);
+            }
+        } else {
+#pragma unroll 2
+            for (int i = 0; i < w.S; ++i) {
+                const float4 ra = rec[i * rec_f4];
+                const float4 rb = rec[i * rec_f4 + 1];
+                const float4 rn = (rec_f4 == 3) ? rec[i * rec_f4 + 2] : make_float4(0.f, 0.f, 1.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) pair_near<KIND, NORM, VAR>(ref[q], ra, rb, rn, k, ar[q], ai[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < TPT; ++q) {
+            float s, e;
+            two_sum(hr[q], ar[q], s, e);
+            hr[q] = s;
+            lr[q] = __fadd_rn(lr[q], e);
+            two_sum(hi[q], ai[q], s, e);
+            hi[q] = s;
+            li[q] = __fadd_rn(li[q], e);
+        }
+        __syncthreads();  // every thread is done with this buffer
+        if (tid == 0 && it + RSI_PIPE_STAGES < w.ntile) {
+            uint32_t bar = smem_u32(&bars[buf]);
+            mbar_expect_tx(bar, w.tile_bytes);
+            bulk_g2s(smem_u32(smem + buf * w.tile_bytes),
+                     w.tiles + size_t(w.t_begin + it + RSI_PIPE_STAGES) * w.tile_bytes, w.tile_bytes, bar);
+        }
+    }
+
+    if (failed_at >= 0) {
+        if (tid == 0) {
+            atomicExch(w.status, RSI_DEV_TIMEOUT);
+            // let the copies still in flight land (bounded) before returning
+            for (int it = failed_at; it < w.ntile && it < failed_at + RSI_PIPE_STAGES; ++it) {
+                const uint32_t u = uses + it;
+                mbar_wait_bounded(smem_u32(&bars[u % RSI_PIPE_STAGES]), (u / RSI_PIPE_STAGES) & 1u);
+            }
+        }
+        return false;
+    }
+    uses += uint32_t(w.ntile);
+
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+        int64_t j = w.j0 + int64_t(q) * kThreads + tid;
+        if (j < w.n_tgt) {
+            double re = double(hr[q]) + double(lr[q]);
+            double im = double(hi[q]) + double(li[q]);
+            if (!isfinite(re) || !isfinite(im)) atomicExch(w.status, RSI_DEV_NONFINITE);
+            w.out[j] = make_double2(re, im);
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void init_barriers(uint64_t* bars) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RSI_PIPE_STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// tile preparation: one CTA per tile, one thread per record
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_reduce(double v, bool is_max, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        double w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmax(v, w) : fmin(v, w);
+    }
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    v = sh[0];
+    for (int q = 1; q < nw; ++q) v = is_max ? fmax(v, sh[q]) : fmin(v, sh[q]);
+    return v;
+}
+
+// Writes tile `tile` (header + blockDim.x records) of a source set; called by
+// every thread of a CTA of blockDim.x == S threads.
+__device__ __forceinline__ void prep_tile(int kind, int normals, int64_t n_src, const PointsView& src,
+                                          const double2* __restrict__ sigma, double amp_scale, double k,
+                                          uint8_t* tiles, size_t tile_bytes, int64_t tile, double* red) {
+    const int S = blockDim.x;
+    const int64_t i = tile * S + threadIdx.x;
+    const bool valid = i < n_src;
+    double c[3];
+    const double* coord[3] = {src.x, src.y, src.z};
+    for (int d = 0; d < 3; ++d) {
+        double v = valid ? coord[d][i] : 0.0;
+        double lo = block_reduce(valid ? v : INFINITY, false, red);
+        double hi = block_reduce(valid ? v : -INFINITY, true, red);
+        c[d] = 0.5 * (lo + hi);
+    }
+    float ch[3], cl[3];
+    for (int d = 0; d < 3; ++d) {
+        ch[d] = __double2float_rn(c[d]);
+        cl[d] = __double2float_rn(c[d] - double(ch[d]));
+    }
+    const int rec_f = (kind == RSI_STAGE_RSI && normals == RSI_NORMALS_POINTS) ? 12 : 8;
+    float* rec = reinterpret_cast<float*>(tiles + size_t(tile) * tile_bytes + RSI_TILE_HDR_BYTES) +
+                 size_t(threadIdx.x) * rec_f;
+    float px = 4.0f, py = 4.0f, pz = 4.0f, radius2 = 0.0f;
+    float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+    float nx = 0.f, ny = 0.f, nz = 1.f;
+    if (valid) {
+        float h, l;
+        df_diff(src.xh[i], src.xl[i], ch[0], cl[0], h, l);
+        px = h;
+        df_diff(src.yh[i], src.yl[i], ch[1], cl[1], h, l);
+        py = h;
+        df_diff(src.zh[i], src.zl[i], ch[2], cl[2], h, l);
+        pz = h;
+        radius2 = px * px + py * py + pz * pz;
+        if (kind == RSI_STAGE_PISTON) {
+            r0 = float(amp_scale * src.w[i]);
+        } else {
+            double2 sg = sigma[i];
+            double br = amp_scale * src.w[i] * sg.x, bi = amp_scale * src.w[i] * sg.y;
+            r0 = float(br);
+            r1 = float(bi);
+            r2 = float(-k * bi);
+            r3 = float(k * br);
+            nx = float(src.nx[i]);
+            ny = float(src.ny[i]);
+            nz = float(src.nz[i]);
+        }
+    }
+    rec[0] = px;
+    rec[1] = py;
+    rec[2] = pz;
+    rec[3] = fmaf(px, px, fmaf(py, py, pz * pz));
+    rec[4] = r0;
+    rec[5] = r1;
+    rec[6] = r2;
+    rec[7] = r3;
+    if (rec_f == 12) {
+        rec[8] = nx;
+        rec[9] = ny;
+        rec[10] = nz;
+        rec[11] = fmaf(nx, px, fmaf(ny, py, nz * pz));  // n . p
+    }
+    double rad = block_reduce(double(radius2), true, red);
+    if (threadIdx.x == 0) {
+        float* hdr = reinterpret_cast<float*>(tiles + size_t(tile) * tile_bytes);
+        hdr[0] = ch[0];
+        hdr[1] = cl[0];
+        hdr[2] = ch[1];
+        hdr[3] = cl[1];
+        hdr[4] = ch[2];
+        hdr[5] = cl[2];
+        hdr[6] = sqrtf(float(rad));
+        hdr[7] = 0.0f;
+    }
+}
+
+}  // namespace rsi_fp32
