@@ -223,6 +223,59 @@ enum rsi_image_format {
 int rsi_field_image(const rsi_grid *g, const double *field, double k, double v0,
                     int32_t format, void *out, void *stream);
 
+/* ---- autotuning of the launch shape --------------------------------------- */
+/* Times the FP32C launch shapes of one stage on the given data -- tile size
+ * (32 ... 512, capped by the accuracy rule of at most n_src/64 sources per
+ * tile) x targets per thread {2, 4} x distance update {reciprocal, Newton},
+ * each shape needing at most workspace_bytes -- and writes the fastest to
+ * *best (kind, precision, k, v0 and normals copied from *st, splits = 0).
+ * Each candidate runs once to warm up and twice timed (CUDA events on
+ * `stream`); the call synchronises `stream` and leaves the last candidate's
+ * field in tgt_field.  Shapes are cached for the process by (kind, normals,
+ * ceil(log2 n_src), ceil(log2 n_tgt)); a cached shape returns at once.
+ * FP64 stages have one shape and return it untimed.                        */
+int rsi_autotune_stage(const rsi_stage *st,
+                       const void *src_points, int64_t n_src, const double *src_sigma,
+                       const void *tgt_points, int64_t n_tgt, double *tgt_field,
+                       void *workspace, size_t workspace_bytes, void *stream, rsi_stage *best);
+
+/* ---- batched chains in one CUDA graph (step a8) ---------------------------- */
+/* One instance: piston -> one interface -> image grid (Eq. incident_field,
+ * Eq. transmission_coefficient, Eq. approximated_transmitted_field), e.g. one
+ * frequency of a broadband pulse (Sec. 4 superposes single-frequency fields)
+ * at one scan position.                                                     */
+typedef struct rsi_batch_instance {
+    rsi_surface piston;       /* RSI_SURF_DISK                                 */
+    rsi_surface iface;        /* RSI_SURF_RECT or RSI_SURF_CYL                 */
+    int64_t n_piston, n_iface;/* QMC points (1 .. 2^30)                        */
+    uint32_t piston_set, iface_set; /* Sobol point-set ids (with the batch seed) */
+    rsi_interface transmit;   /* media and Snell invariant of the interface    */
+    double k1, k2;            /* wavenumbers before / after the interface      */
+    double v0;                /* piston velocity amplitude                     */
+    rsi_grid grid;            /* image of this instance                        */
+} rsi_batch_instance;
+
+typedef struct rsi_batch_plan rsi_batch_plan; /* opaque, host memory */
+
+/* Plans a batch (host work only, nothing enqueued): per-instance tile sizes
+ * by the accuracy rule, work items of about 2^22 pairs sorted largest first,
+ * and the workspace layout.  shape: NULL or an FP32C rsi_stage whose tile
+ * (upper bound), tpt and variant fields override the defaults.  Returns the
+ * workspace size and the number of complex64 image elements (the instances'
+ * nx*nz, concatenated in instance order).                                  */
+int rsi_batch_create(const rsi_batch_instance *inst, int32_t n_inst, uint64_t seed,
+                     const rsi_stage *shape, rsi_batch_plan **plan,
+                     size_t *workspace_bytes, size_t *image_elems);
+/* Runs the whole batch on `stream`: points, piston stages, transmission, RSI
+ * stages and images, with the two stage sums as persistent kernels that take
+ * work items from a global counter.  The first run with a given workspace /
+ * images pair uploads the plan's tables into the workspace (synchronously),
+ * captures the work into a CUDA graph and instantiates it; every run then
+ * launches that graph.  images: complex64 [image_elems], device.           */
+int rsi_batch_run(rsi_batch_plan *plan, void *workspace, size_t workspace_bytes, void *images,
+                  void *stream);
+int rsi_batch_destroy(rsi_batch_plan *plan);
+
 /* ---- measurement hooks (no counterpart in the paper) --------------------- */
 /* Number of kernels this library has enqueued in this process.             */
 uint64_t rsi_launch_count(void);

@@ -4,7 +4,9 @@
 // (step a6).
 #include <math.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "stage.cuh"
@@ -277,5 +279,96 @@ extern "C" int rsi_propagate_stage(const rsi_stage* st, const void* src_points, 
         reduce_partials_kernel<<<blocks, threads, 0, s>>>(a.out, p.splits, n_tgt, field, status);
         RSI_CHECK_LAUNCH("reduce_partials_kernel");
     }
+    return RSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, rsi_stage> g_tune_cache;
+
+int ceil_log2(int64_t v) {
+    int b = 0;
+    while ((int64_t(1) << b) < v) ++b;
+    return b;
+}
+}  // namespace
+
+extern "C" int rsi_autotune_stage(const rsi_stage* st, const void* src_points, int64_t n_src,
+                                  const double* src_sigma, const void* tgt_points, int64_t n_tgt,
+                                  double* tgt_field, void* workspace, size_t workspace_bytes, void* stream,
+                                  rsi_stage* best) {
+    if (!st || !best) return rsi_fail(RSI_E_INVAL, "rsi_autotune_stage: null argument");
+    Plan p0;
+    int rc = make_plan(*st, n_src, n_tgt, p0);
+    if (rc != RSI_OK) return rc;
+    rsi_stage base = *st;
+    base.tile = base.tpt = base.splits = base.variant = 0;
+    if (st->precision != RSI_PREC_FP32C) {
+        *best = base;
+        return RSI_OK;
+    }
+    const auto key = std::make_tuple(st->kind, st->kind == RSI_STAGE_RSI ? st->normals : 0, ceil_log2(n_src),
+                                     ceil_log2(n_tgt));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto f = g_tune_cache.find(key);
+        if (f != g_tune_cache.end()) {
+            *best = base;
+            best->tile = f->second.tile;
+            best->tpt = f->second.tpt;
+            best->variant = f->second.variant;
+            return RSI_OK;
+        }
+    }
+    // largest tile the accuracy rule allows (the default plan's tile)
+    const int cap = p0.S;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RSI_CUDA_TRY(cudaEventCreate(&e0), "cudaEventCreate");
+    RSI_CUDA_TRY(cudaEventCreate(&e1), "cudaEventCreate");
+    float best_ms = 1e30f;
+    rsi_stage win = base;
+    for (int S = 32; S <= cap; S <<= 1)
+        for (int tpt : {2, 4})
+            for (int var : {1, 2}) {
+                rsi_stage c = base;
+                c.tile = S;
+                c.tpt = tpt;
+                c.variant = var;
+                if (rsi_stage_workspace_bytes(&c, n_src, n_tgt) > workspace_bytes) continue;
+                float t_best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    RSI_CUDA_TRY(cudaEventRecord(e0, s), "cudaEventRecord");
+                    rc = rsi_propagate_stage(&c, src_points, n_src, src_sigma, tgt_points, n_tgt, tgt_field,
+                                             workspace, workspace_bytes, stream);
+                    if (rc != RSI_OK) break;
+                    RSI_CUDA_TRY(cudaEventRecord(e1, s), "cudaEventRecord");
+                    RSI_CUDA_TRY(cudaEventSynchronize(e1), "cudaEventSynchronize");
+                    float ms = 0.0f;
+                    RSI_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+                    if (rep > 0) t_best = fminf(t_best, ms);
+                }
+                if (rc != RSI_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return rc;
+                }
+                if (t_best < best_ms) {
+                    best_ms = t_best;
+                    win = c;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms >= 1e30f) return rsi_fail(RSI_E_NOMEM, "rsi_autotune_stage: no shape fits the workspace");
+    win.splits = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = win;
+    }
+    *best = win;
     return RSI_OK;
 }

@@ -36,7 +36,8 @@ __global__ void prep_fp32_kernel(int kind, int normals, int64_t n_src, PointsVie
                                  const double2* __restrict__ sigma, double amp_scale, double k, uint8_t* tiles,
                                  size_t tile_bytes) {
     __shared__ double red[32];
-    prep_tile(kind, normals, n_src, src, sigma, amp_scale, k, tiles, tile_bytes, int64_t(blockIdx.x), red);
+    prep_tile(kind, normals, int(blockDim.x), n_src, src, sigma, amp_scale, k, tiles, tile_bytes,
+              int64_t(blockIdx.x), red);
 }
 
 template <int KIND, int NORM, int TPT, int VAR>

@@ -312,14 +312,15 @@ __device__ __forceinline__ double block_reduce(double v, bool is_max, double* sh
     return v;
 }
 
-// Writes tile `tile` (header + blockDim.x records) of a source set; called by
-// every thread of a CTA of blockDim.x == S threads.
-__device__ __forceinline__ void prep_tile(int kind, int normals, int64_t n_src, const PointsView& src,
+// Writes tile `tile` (header + S records) of a source set; called by every
+// thread of a CTA of blockDim.x >= S threads (threads past S only take part
+// in the block reductions).
+__device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t n_src, const PointsView& src,
                                           const double2* __restrict__ sigma, double amp_scale, double k,
                                           uint8_t* tiles, size_t tile_bytes, int64_t tile, double* red) {
-    const int S = blockDim.x;
+    const bool in_tile = int(threadIdx.x) < S;
     const int64_t i = tile * S + threadIdx.x;
-    const bool valid = i < n_src;
+    const bool valid = in_tile && i < n_src;
     double c[3];
     const double* coord[3] = {src.x, src.y, src.z};
     for (int d = 0; d < 3; ++d) {
@@ -362,19 +363,21 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int64_t n_src, 
             nz = float(src.nz[i]);
         }
     }
-    rec[0] = px;
-    rec[1] = py;
-    rec[2] = pz;
-    rec[3] = fmaf(px, px, fmaf(py, py, pz * pz));
-    rec[4] = r0;
-    rec[5] = r1;
-    rec[6] = r2;
-    rec[7] = r3;
-    if (rec_f == 12) {
-        rec[8] = nx;
-        rec[9] = ny;
-        rec[10] = nz;
-        rec[11] = fmaf(nx, px, fmaf(ny, py, nz * pz));  // n . p
+    if (in_tile) {
+        rec[0] = px;
+        rec[1] = py;
+        rec[2] = pz;
+        rec[3] = fmaf(px, px, fmaf(py, py, pz * pz));
+        rec[4] = r0;
+        rec[5] = r1;
+        rec[6] = r2;
+        rec[7] = r3;
+        if (rec_f == 12) {
+            rec[8] = nx;
+            rec[9] = ny;
+            rec[10] = nz;
+            rec[11] = fmaf(nx, px, fmaf(ny, py, nz * pz));  // n . p
+        }
     }
     double rad = block_reduce(double(radius2), true, red);
     if (threadIdx.x == 0) {

@@ -37,7 +37,8 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points",
            "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_interface_transmit",
            "rsi_field_image", "rsi_launch_count", "rsi_timing_enable", "rsi_timing_read",
-           "rsi_ubench"]
+           "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
+           "rsi_batch_destroy"]
 UB = {"ffma": 0, "rsqrt": 1, "sin": 2}
 
 
@@ -65,6 +66,13 @@ class Interface(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rho1", ctypes.c_double),
                 ("c1", ctypes.c_double), ("rho2", ctypes.c_double), ("c2", ctypes.c_double),
                 ("snell_C", ctypes.c_double)]
+
+
+class BatchInstance(ctypes.Structure):
+    _fields_ = [("piston", Surface), ("iface", Surface), ("n_piston", ctypes.c_int64),
+                ("n_iface", ctypes.c_int64), ("piston_set", ctypes.c_uint32),
+                ("iface_set", ctypes.c_uint32), ("transmit", Interface), ("k1", ctypes.c_double),
+                ("k2", ctypes.c_double), ("v0", ctypes.c_double), ("grid", Grid)]
 
 
 class RSIError(RuntimeError):
@@ -105,6 +113,12 @@ def load(path: str | None = None):
         L.rsi_timing_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
         L.rsi_ubench.argtypes = [i32, i32, i32, vp, vp]
+        L.rsi_autotune_stage.argtypes = [ctypes.POINTER(Stage), vp, i64, vp, vp, i64, vp, vp, sz, vp,
+                                         ctypes.POINTER(Stage)]
+        L.rsi_batch_create.argtypes = [ctypes.POINTER(BatchInstance), i32, u64, ctypes.POINTER(Stage),
+                                       ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(sz)]
+        L.rsi_batch_run.argtypes = [vp, vp, sz, vp, vp]
+        L.rsi_batch_destroy.argtypes = [vp]
         _lib = L
         return L
 
@@ -262,6 +276,21 @@ def field_image(g: dict, field, k: float, v0: float = 1.0, fmt: str = "c128", ou
     return out
 
 
+def autotune_stage(st: Stage, src: Points, sigma, tgt: Points, out=None,
+                   workspace: Workspace | None = None, max_workspace: int = 1 << 30,
+                   stream=None) -> Stage:
+    """Fastest FP32C launch shape for this stage (see rsi_autotune_stage)."""
+    if out is None:
+        out = torch.empty(tgt.n, dtype=torch.complex128, device=tgt.buf.device)
+    base = workspace_bytes(st, src.n, tgt.n)
+    ws = (workspace or Workspace(tgt.buf.device)).get(max(base, min(max_workspace, 8 * base)))
+    best = Stage()
+    _check(load().rsi_autotune_stage(ctypes.byref(st), src.ptr(), src.n, _ptr(sigma), tgt.ptr(), tgt.n,
+                                     _ptr(out), _ptr(ws), ws.numel(), _stream(stream),
+                                     ctypes.byref(best)), "rsi_autotune_stage")
+    return best
+
+
 def sync_status(stream=None):
     _check(load().rsi_sync_status(_stream(stream)), "rsi_sync_status")
 
@@ -343,3 +372,72 @@ def run_chain(cfg: dict, precision: str | None = None, targets: Points | None = 
         k_last = wavenumber(freq, media[len(ifaces)]["c"])
         image = field_image(cfg["grid"], phi, k_last, v0, fmt, stream=stream)
     return ChainResult(image, phi, kept)
+
+
+# ---------------------------------------------------------------------------
+# batches of single-interface chains in one CUDA graph (rsi_batch_*)
+# ---------------------------------------------------------------------------
+def batch_instance(cfg: dict) -> BatchInstance:
+    """A BatchInstance from a workload description with exactly one interface."""
+    if len(cfg["interfaces"]) != 1:
+        raise ValueError("batched chains have exactly one interface")
+    b = BatchInstance()
+    pc, it = cfg["piston"], cfg["interfaces"][0]
+    b.piston = surface_struct(dict(pc, kind="disk"))
+    b.iface = surface_struct(it)
+    b.n_piston, b.n_iface = int(pc["n"]), int(it["n"])
+    b.piston_set, b.iface_set = int(pc.get("set_id", 0)), int(it["set_id"])
+    m = cfg["media"]
+    b.transmit = interface_struct(m[0], m[1], snell_invariant(cfg), cfg.get("tmode", "global"))
+    b.k1 = wavenumber(cfg["freq"], m[0]["c"])
+    b.k2 = wavenumber(cfg["freq"], m[1]["c"])
+    b.v0 = float(cfg.get("v0", 1.0))
+    b.grid = grid_struct(cfg["grid"])
+    return b
+
+
+class Batch:
+    """Plan + device buffers of a batch; run() replays one CUDA graph."""
+
+    def __init__(self, cfgs: list, seed: int = 0, shape: Stage | None = None, device="cuda",
+                 allocate: bool = True):
+        L = load()
+        self.cfgs = cfgs
+        arr = (BatchInstance * len(cfgs))(*[batch_instance(c) for c in cfgs])
+        plan, ws, n_img = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_size_t()
+        _check(L.rsi_batch_create(arr, len(cfgs), int(seed), ctypes.byref(shape) if shape else None,
+                                  ctypes.byref(plan), ctypes.byref(ws), ctypes.byref(n_img)),
+               "rsi_batch_create")
+        self.plan = plan
+        self.workspace_bytes = int(ws.value)
+        self.image_elems = int(n_img.value)
+        self.offsets = []
+        off = 0
+        for c in cfgs:
+            self.offsets.append(off)
+            off += int(c["grid"]["nx"]) * int(c["grid"]["nz"])
+        self.ws = self.images = None
+        if allocate:
+            self.ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=device)
+            self.images = torch.empty(self.image_elems, dtype=torch.complex64, device=device)
+
+    def run(self, stream=None) -> torch.Tensor:
+        _check(load().rsi_batch_run(self.plan, _ptr(self.ws), self.ws.numel(), _ptr(self.images),
+                                    _stream(stream)), "rsi_batch_run")
+        return self.images
+
+    def image(self, i: int) -> torch.Tensor:
+        g = self.cfgs[i]["grid"]
+        n = int(g["nx"]) * int(g["nz"])
+        return self.images[self.offsets[i]:self.offsets[i] + n].view(int(g["nz"]), int(g["nx"]))
+
+    def close(self):
+        if self.plan:
+            load().rsi_batch_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

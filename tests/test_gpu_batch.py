@@ -1,0 +1,88 @@
+"""Batched chains in one CUDA graph (rsi_batch_*) against the plain
+per-instance path on the same GPU (<= 1e-3, the bar for batched runs) and
+against the FP64 oracle (<= 1e-4)."""
+import copy
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2408_06765_gb300 import build, rsi
+from paper_2408_06765_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return rsi.load()
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def uneven_batch(curved=False):
+    counts = [(600, 2500), (1500, 700), (300, 4096), (2048, 1999), (100, 5000), (3000, 3000), (257, 333)]
+    cfgs = []
+    for i, (n_p, n_i) in enumerate(counts):
+        cfg = W.small_ragged("fp32c", freq=(1.5 + 1.3 * i) * 1e6, n_piston=n_p, n_iface=n_i, nx=32, nz=24,
+                             tilt=math.radians(20.0) if i == 3 else 0.0)
+        x_t = (i - 3) * 1.5e-3
+        cfg["piston"]["centre"] = (x_t, 0.0, 0.0)
+        cfg["piston"]["set_id"] = 2 * i
+        it = cfg["interfaces"][0]
+        it["centre"] = (x_t, 0.0, it["centre"][2])
+        it["set_id"] = 2 * i + 1
+        if curved and i % 2 == 1:
+            it.update(kind="cyl", R=0.05, wx=0.04, wy=0.04)
+            cfg["tmode"] = "local"
+        cfgs.append(cfg)
+    return cfgs
+
+
+@pytest.mark.parametrize("curved", [False, True])
+def test_batch_matches_plain_path_and_oracle(curved):
+    cfgs = uneven_batch(curved)
+    b = rsi.Batch(cfgs, seed=cfgs[0]["seed"])
+    try:
+        b.run()
+        torch.cuda.synchronize()
+        rsi.sync_status()
+        first = b.images.clone()
+        for i, cfg in enumerate(cfgs):
+            plain = rsi.run_chain(cfg).image.cpu().numpy()
+            got = b.image(i).cpu().numpy()
+            assert rel_l2(got, plain) <= 1e-3
+            assert rel_l2(got, plain) <= 1e-5  # same kernels, different source grouping
+            if i in (2, 3):
+                assert rel_l2(got, oracle.field_image(cfg)) <= 1e-4
+        # replaying the graph reproduces the images bit for bit
+        b.run()
+        torch.cuda.synchronize()
+        rsi.sync_status()
+        assert torch.equal(b.images, first)
+    finally:
+        b.close()
+
+
+def test_autotuned_shape_is_valid_and_agrees():
+    cfg = W.small_ragged("fp32c", n_piston=4000, n_iface=9000)
+    it = cfg["interfaces"][0]
+    src = rsi.make_qmc_points(it, cfg["seed"], it["set_id"], it["n"])
+    tgt = rsi.grid_points(cfg["grid"])
+    sig = torch.ones(it["n"], dtype=torch.complex128, device="cuda")
+    st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", 2 * math.pi * 5e6 / 5900.0, normals=rsi.NORMALS_Z)
+    best = rsi.autotune_stage(st, src, sig, tgt)
+    assert best.tile in (32, 64, 128) and best.tpt in (2, 4) and best.variant in (1, 2)
+    ref = rsi.propagate_stage(st, src, sig, tgt)
+    tuned = rsi.propagate_stage(best, src, sig, tgt)
+    rsi.sync_status()
+    assert rel_l2(tuned.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
+    again = rsi.autotune_stage(st, src, sig, tgt)  # cached
+    assert (again.tile, again.tpt, again.variant) == (best.tile, best.tpt, best.variant)
