@@ -59,8 +59,11 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
-    ap.add_argument("--config", choices=["c2", "c4"], default="c2",
-                    help="c4: the batched broadband scan (2048 instances in one CUDA graph)")
+    ap.add_argument("--config", choices=["c2", "c4", "c5"], default="c2",
+                    help="c4: the batched broadband scan (2048 instances in one CUDA graph); "
+                         "c5: the learned surrogate (train on RSI fields, compare)")
+    ap.add_argument("--fields", type=int, default=20000, help="c5: training fields")
+    ap.add_argument("--epochs", type=int, default=60, help="c5: training epochs")
     ap.add_argument("--sweep", action="store_true",
                     help="with --case stage: time every tile / targets-per-thread / variant")
     return ap.parse_args()
@@ -509,9 +512,78 @@ def run_batch_c4(args):
     b.close()
 
 
+def run_surrogate_c5(args):
+    """c5: generate fields with the batched RSI path, train the BF16 MLP,
+    measure held-out error, inference rate against the RSI path, and the
+    fallback gate."""
+    import numpy as np
+    import torch
+    from paper_2408_06765_gb300 import build, rsi, surrogate
+    from paper_2408_06765_gb300 import workloads as W
+    build.build()
+    n = args.fields
+    params = W.c5_params(n, seed=0)
+    t0 = time.perf_counter()
+    imgs = surrogate.rsi_images(params)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    env = surrogate.demodulate(imgs, params)
+    n_hold = n // 10
+    tr, ho = slice(0, n - n_hold), slice(n - n_hold, n)
+    scale = float(env[tr].pow(2).mean().sqrt())
+    net = surrogate.MLP(batch=256)
+    net.scale = scale
+    t0 = time.perf_counter()
+    losses = surrogate.train(net, params[tr], env[tr] / scale, epochs=args.epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # held-out error (batches of 256)
+    errs = []
+    hp = params[ho]
+    for c0 in range(0, (n_hold // 256) * 256, 256):
+        pb = torch.tensor(hp[c0:c0 + 256], dtype=torch.float32, device="cuda")
+        pred = surrogate.modulate(net.predict(pb) * scale, hp[c0:c0 + 256])
+        errs.append(surrogate.rel_errors(pred, imgs[ho][c0:c0 + 256]).cpu().numpy())
+    errs = np.concatenate(errs)
+    # inference throughput at batch 1024 vs the RSI path on the same fields
+    inf = surrogate.MLP(batch=1024)
+    for a, b_ in zip(inf.W16 + inf.b, net.W16 + net.b):
+        a.copy_(b_)
+    inf.fmat.copy_(net.fmat)
+    pq = torch.tensor(params[:1024], dtype=torch.float32, device="cuda")
+    inf.predict(pq)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        surrogate.modulate(inf.predict(pq) * scale, params[:1024])
+    e1.record()
+    e1.synchronize()
+    nn_fields_s = 10 * 1024 / (e0.elapsed_time(e1) * 1e-3)
+    rsi_fields_s = n / gen_s
+    sur = surrogate.Surrogate(net, params[ho][:len(errs)], errs)
+    est = sur.error_estimate(params[:1024])
+    line = {"config": {"workload": "c5 learned surrogate: 5 inputs -> Fourier features -> 4 x 512 SiLU -> "
+                                   "2 x 128 x 128, BF16 weights, FP32 accumulation",
+                       "fields": n, "held_out": int(len(errs)), "epochs": args.epochs,
+                       "rsi_points": [1 << 14, 1 << 16]},
+            "rsi_generation_s": gen_s, "rsi_fields_per_s": rsi_fields_s,
+            "train_s": train_s, "final_train_loss": losses[-1],
+            "held_out_rel_l2": {"median": float(np.median(errs)), "mean": float(errs.mean()),
+                                "p90": float(np.quantile(errs, 0.9)), "max": float(errs.max())},
+            "reaches_1e-3": bool(np.median(errs) <= 1e-3),
+            "surrogate_fields_per_s_batch1024": nn_fields_s,
+            "speedup_vs_rsi": nn_fields_s / rsi_fields_s,
+            "gate": {"threshold": 1e-2, "fallback_fraction": float(np.mean(est > 1e-2))},
+            "gpu": torch.cuda.get_device_name(0)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.config == "c4" and args.impl == "ours" and args.case == "chain":
+    if args.config == "c5" and args.impl == "ours":
+        run_surrogate_c5(args)
+    elif args.config == "c4" and args.impl == "ours" and args.case == "chain":
         run_batch_c4(args)
     elif args.case == "stage":
         run_stage_case(args)

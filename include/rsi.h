@@ -276,6 +276,48 @@ int rsi_batch_run(rsi_batch_plan *plan, void *workspace, size_t workspace_bytes,
                   void *stream);
 int rsi_batch_destroy(rsi_batch_plan *plan);
 
+/* ---- learned surrogate (step a9; no counterpart in the paper) ------------- */
+/* Building blocks of a Fourier-feature MLP that maps (x-offset, tilt, water
+ * path, frequency, image depth) to the carrier-demodulated image of the RSI
+ * chain; it is trained on fields the RSI kernels compute and falls back to
+ * them when its held-out error is too large.  Matrices are row-major; bf16
+ * arrays are passed as void* (IEEE bfloat16, 2 bytes per element).  All
+ * pointers are device pointers; calls are asynchronous on `stream`.         */
+enum rsi_nn_epilogue {
+    RSI_NN_EPI_F32 = 0,       /* out_f32 = A B^T (+ bias)                              */
+    RSI_NN_EPI_BIAS_SILU = 1, /* z = A B^T + bias: out_f32 = z, out_bf16 = silu(z)     */
+    RSI_NN_EPI_DSILU = 2      /* out_bf16 = (A B^T) * silu'(aux)   (aux: f32, M x N)   */
+};
+/* out = [sin(pi B u), cos(pi B u)] (bf16, batch x 2F) with
+ * u = 2 (p - lo)/(hi - lo) - 1; p: f32 batch x n_in, B: f32 F x n_in.     */
+int rsi_nn_features(const float *params, const float *lo, const float *hi, const float *fmat,
+                    int32_t batch, int32_t n_in, int32_t n_freq, void *out_bf16, void *stream);
+/* C[M x N] = A[M x K] B[N x K]^T on BF16 tensor cores with FP32 accumulation
+ * and the chosen epilogue.  M, N multiples of 128, K a multiple of 32;
+ * A, B 16-byte aligned.  bias: f32 [N] or NULL (F32 epilogue).             */
+int rsi_nn_gemm(int32_t epilogue, const void *A, const void *B, int32_t M, int32_t N, int32_t K,
+                const float *bias, const float *aux, float *out_f32, void *out_bf16, void *stream);
+/* out[c][r] = in[r][c] for a bf16 rows x cols matrix.                      */
+int rsi_nn_transpose(const void *in_bf16, int32_t rows, int32_t cols, void *out_bf16, void *stream);
+/* *loss_out = mean((y - t)^2) over n values (f32); grad_bf16 (may be NULL)
+ * = grad_scale * (y - t).  partial: f64 scratch [n_partial] (the number of
+ * CTAs of the reduction).                                                  */
+int rsi_nn_loss(const float *y, const float *t, int64_t n, float grad_scale, void *grad_bf16,
+                double *partial, int32_t n_partial, float *loss_out, void *stream);
+/* out[c] = sum over rows of a bf16 rows x cols matrix (bias gradients).    */
+int rsi_nn_colsum(const void *m_bf16, int32_t rows, int32_t cols, float *out, void *stream);
+/* One Adam step (Kingma & Ba 2015) on n FP32 master weights w with moments
+ * m, v and gradient g at step >= 1; writes a bf16 copy to w_bf16 if given. */
+int rsi_nn_adam(float *w, float *m, float *v, const float *g, int64_t n, float lr, float beta1,
+                float beta2, float eps, int32_t step, void *w_bf16, void *stream);
+/* bf16 copy of an f32 array.                                               */
+int rsi_nn_cast_bf16(const float *in, int64_t n, void *out_bf16, void *stream);
+/* out = in * exp(sign i psi) per pixel of batch images (complex f32 pairs,
+ * row-major [nz][nx] over `window`, relative coordinates), with
+ * psi = k2 (s x + c (z + depth)) and carrier[b] = (k2, s, c, depth) (f64). */
+int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window, int32_t sign,
+                   const float *in, float *out, void *stream);
+
 /* ---- measurement hooks (no counterpart in the paper) --------------------- */
 /* Number of kernels this library has enqueued in this process.             */
 uint64_t rsi_launch_count(void);

@@ -38,7 +38,9 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_interface_transmit",
            "rsi_field_image", "rsi_launch_count", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
-           "rsi_batch_destroy"]
+           "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
+           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier"]
+NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
 UB = {"ffma": 0, "rsqrt": 1, "sin": 2}
 
 
@@ -119,6 +121,15 @@ def load(path: str | None = None):
                                        ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(sz)]
         L.rsi_batch_run.argtypes = [vp, vp, sz, vp, vp]
         L.rsi_batch_destroy.argtypes = [vp]
+        f32, f64 = ctypes.c_float, ctypes.c_double
+        L.rsi_nn_features.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp]
+        L.rsi_nn_gemm.argtypes = [i32, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp]
+        L.rsi_nn_transpose.argtypes = [vp, i32, i32, vp, vp]
+        L.rsi_nn_loss.argtypes = [vp, vp, i64, f32, vp, vp, i32, vp, vp]
+        L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
+        L.rsi_nn_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
+        L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
+        L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, vp, vp, vp]
         _lib = L
         return L
 
@@ -441,3 +452,56 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# surrogate building blocks (rsi_nn_*)
+# ---------------------------------------------------------------------------
+def nn_features(p, lo, hi, fmat, out, stream=None):
+    _check(load().rsi_nn_features(_ptr(p), _ptr(lo), _ptr(hi), _ptr(fmat), p.shape[0], p.shape[1],
+                                  fmat.shape[0], _ptr(out), _stream(stream)), "rsi_nn_features")
+    return out
+
+
+def nn_gemm(epi: str, A, B, out_f32=None, out_bf16=None, bias=None, aux=None, stream=None):
+    """C[M x N] = A[M x K] B[N x K]^T with an epilogue (see rsi_nn_gemm)."""
+    M, K = A.shape
+    N = B.shape[0]
+    assert B.shape[1] == K
+    _check(load().rsi_nn_gemm(NN_EPI[epi], _ptr(A), _ptr(B), M, N, K, _ptr(bias), _ptr(aux),
+                              _ptr(out_f32), _ptr(out_bf16), _stream(stream)), "rsi_nn_gemm")
+
+
+def nn_transpose(x, out, stream=None):
+    _check(load().rsi_nn_transpose(_ptr(x), x.shape[0], x.shape[1], _ptr(out), _stream(stream)),
+           "rsi_nn_transpose")
+    return out
+
+
+def nn_loss(y, t, grad_scale, grad, partial, loss_out, stream=None):
+    _check(load().rsi_nn_loss(_ptr(y), _ptr(t), y.numel(), float(grad_scale), _ptr(grad),
+                              _ptr(partial), partial.numel(), _ptr(loss_out), _stream(stream)),
+           "rsi_nn_loss")
+
+
+def nn_colsum(m, out, stream=None):
+    _check(load().rsi_nn_colsum(_ptr(m), m.shape[0], m.shape[1], _ptr(out), _stream(stream)),
+           "rsi_nn_colsum")
+
+
+def nn_adam(w, m, v, g, lr, step, w_bf16=None, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().rsi_nn_adam(_ptr(w), _ptr(m), _ptr(v), _ptr(g), w.numel(), float(lr), float(beta1),
+                              float(beta2), float(eps), int(step), _ptr(w_bf16), _stream(stream)),
+           "rsi_nn_adam")
+
+
+def nn_cast_bf16(x, out, stream=None):
+    _check(load().rsi_nn_cast_bf16(_ptr(x), x.numel(), _ptr(out), _stream(stream)), "rsi_nn_cast_bf16")
+    return out
+
+
+def nn_carrier(carrier, window: dict, sign: int, x, out, stream=None):
+    G = grid_struct(window)
+    _check(load().rsi_nn_carrier(_ptr(carrier), carrier.shape[0], ctypes.byref(G), int(sign), _ptr(x),
+                                 _ptr(out), _stream(stream)), "rsi_nn_carrier")
+    return out

@@ -1,0 +1,238 @@
+"""Learned surrogate of the RSI chain (not in the paper): a Fourier-feature MLP
+that maps (x-offset, tilt, water path, frequency, image depth) to the
+128 x 128 field image of one water -> steel chain, trained on images the GPU
+RSI path computes, with the RSI path as its fallback and its judge.
+
+Every numerical step runs in librsi.so (rsi_nn_* kernels: BF16 tensor-core
+GEMMs with FP32 accumulation and fused bias/SiLU epilogues, FP32 master
+weights, Adam); this module sequences the calls and keeps the buffers.
+
+Network (same definition as the FP64 oracle, oracle/mlp.py):
+    u = 2 (p - lo)/(hi - lo) - 1;  h0 = [sin(pi B u), cos(pi B u)]
+    h_l = silu(W_l h_{l-1} + b_l), l = 1..depth;  y = W_out h_depth + b_out
+The output y is the image times exp(-i psi) (the plane-wave carrier of the
+refracted beam, psi = k2 (s x + c (z + depth)), s = (c2/c1) sin(tilt),
+c = sqrt(1 - s^2) or 0 past the critical angle), real and imaginary parts
+interleaved, divided by a fixed amplitude scale.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import rsi
+from . import workloads as W
+
+C1, C2 = W.WATER["c"], W.STEEL["c"]
+LO = np.array([-10e-3, math.radians(-15.0), 20e-3, 2e6, 1e-3])
+HI = np.array([10e-3, math.radians(15.0), 60e-3, 10e6, 20e-3])
+WINDOW = {"x0": -20e-3, "x1": 20e-3, "nx": 128, "z0": 0.0, "z1": 40e-3, "nz": 128}
+
+
+def carrier_coeffs(params) -> np.ndarray:
+    """(k2, s, c, depth) per sample: the refracted plane-wave carrier."""
+    p = np.atleast_2d(np.asarray(params, np.float64))
+    k2 = 2 * np.pi * p[:, 3] / C2
+    s = C2 / C1 * np.sin(p[:, 1])
+    c = np.sqrt(np.clip(1.0 - s * s, 0.0, None))
+    return np.stack([k2, s, c, p[:, 4]], axis=1)
+
+
+class MLP:
+    """Weights, Adam state and activation buffers of the surrogate."""
+
+    def __init__(self, n_freq=128, width=512, depth=4, n_out=2 * 128 * 128, batch=256, seed=0,
+                 sigma_b=2.0, device="cuda"):
+        self.n_in, self.F, self.width, self.depth, self.n_out = 5, n_freq, width, depth, n_out
+        self.batch = batch
+        self.device = device
+        rng = np.random.default_rng(seed)
+        dims = [2 * n_freq] + [width] * depth + [n_out]
+        self.dims = dims
+        f32 = dict(dtype=torch.float32, device=device)
+        self.W, self.b = [], []
+        for i in range(len(dims) - 1):
+            std = math.sqrt(2.0 / dims[i]) if i < len(dims) - 2 else math.sqrt(1.0 / dims[i])
+            self.W.append(torch.tensor(rng.normal(0.0, std, size=(dims[i + 1], dims[i])), **f32))
+            self.b.append(torch.zeros(dims[i + 1], **f32))
+        self.fmat = torch.tensor(rng.normal(0.0, sigma_b, size=(n_freq, 5)), **f32)
+        self.lo = torch.tensor(LO, **f32)
+        self.hi = torch.tensor(HI, **f32)
+        self.W16 = [torch.empty(w.shape, dtype=torch.bfloat16, device=device) for w in self.W]
+        for w, h in zip(self.W, self.W16):
+            rsi.nn_cast_bf16(w, h)
+        self.mW = [torch.zeros_like(w) for w in self.W]
+        self.vW = [torch.zeros_like(w) for w in self.W]
+        self.mb = [torch.zeros_like(b) for b in self.b]
+        self.vb = [torch.zeros_like(b) for b in self.b]
+        self.gW = [torch.empty_like(w) for w in self.W]
+        self.gb = [torch.empty_like(b) for b in self.b]
+        self.step_count = 0
+        self.scale = 1.0
+        self._alloc(batch)
+
+    def _alloc(self, B):
+        d, bf = self.device, torch.bfloat16
+        self.B_alloc = B
+        self.H = [torch.empty((B, n), dtype=bf, device=d) for n in self.dims[:-1]]
+        self.Z = [torch.empty((B, n), dtype=torch.float32, device=d) for n in self.dims[1:-1]]
+        self.y = torch.empty((B, self.n_out), dtype=torch.float32, device=d)
+        self.dy = torch.empty((B, self.n_out), dtype=bf, device=d)
+        self.dZ = [torch.empty((B, n), dtype=bf, device=d) for n in self.dims[1:-1]]
+        self.HT = [torch.empty((n, B), dtype=bf, device=d) for n in self.dims[:-1]]
+        self.dyT = torch.empty((self.n_out, B), dtype=bf, device=d)
+        self.dZT = [torch.empty((n, B), dtype=bf, device=d) for n in self.dims[1:-1]]
+        self.WT = [torch.empty((w.shape[1], w.shape[0]), dtype=bf, device=d) for w in self.W]
+        self.partial = torch.empty(1024, dtype=torch.float64, device=d)
+        self.loss_buf = torch.empty(1, dtype=torch.float32, device=d)
+
+    # -- forward / backward / update ------------------------------------------
+    def forward(self, p) -> torch.Tensor:
+        """p: f32 [B, 5] on the device (B = the allocated batch)."""
+        assert p.shape[0] == self.B_alloc
+        rsi.nn_features(p, self.lo, self.hi, self.fmat, self.H[0])
+        for l in range(self.depth):
+            rsi.nn_gemm("bias_silu", self.H[l], self.W16[l], out_f32=self.Z[l], out_bf16=self.H[l + 1],
+                        bias=self.b[l])
+        rsi.nn_gemm("f32", self.H[self.depth], self.W16[-1], out_f32=self.y, bias=self.b[-1])
+        return self.y
+
+    def loss(self, t, grad: bool = True) -> torch.Tensor:
+        n = self.y.numel()
+        rsi.nn_loss(self.y, t, 2.0 / n, self.dy if grad else None, self.partial, self.loss_buf)
+        return self.loss_buf
+
+    def backward(self):
+        """Gradients of the mean squared error into gW, gb (after loss())."""
+        L = self.depth
+        rsi.nn_transpose(self.dy, self.dyT)
+        rsi.nn_transpose(self.H[L], self.HT[L])
+        rsi.nn_gemm("f32", self.dyT, self.HT[L], out_f32=self.gW[L])
+        rsi.nn_colsum(self.dy, self.gb[L])
+        rsi.nn_transpose(self.W16[L], self.WT[L])
+        rsi.nn_gemm("dsilu", self.dy, self.WT[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1])
+        for l in range(L - 1, -1, -1):
+            rsi.nn_transpose(self.dZ[l], self.dZT[l])
+            rsi.nn_transpose(self.H[l], self.HT[l])
+            rsi.nn_gemm("f32", self.dZT[l], self.HT[l], out_f32=self.gW[l])
+            rsi.nn_colsum(self.dZ[l], self.gb[l])
+            if l > 0:
+                rsi.nn_transpose(self.W16[l], self.WT[l])
+                rsi.nn_gemm("dsilu", self.dZ[l], self.WT[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1])
+
+    def adam(self, lr: float):
+        self.step_count += 1
+        for i in range(len(self.W)):
+            rsi.nn_adam(self.W[i], self.mW[i], self.vW[i], self.gW[i], lr, self.step_count, self.W16[i])
+            rsi.nn_adam(self.b[i], self.mb[i], self.vb[i], self.gb[i], lr, self.step_count)
+
+    def train_step(self, p, t, lr: float) -> torch.Tensor:
+        self.forward(p)
+        loss = self.loss(t)
+        self.backward()
+        self.adam(lr)
+        return loss
+
+    def predict(self, p) -> torch.Tensor:
+        """Envelopes (scaled) for a batch of exactly B_alloc samples."""
+        return self.forward(p)
+
+
+# ---------------------------------------------------------------------------
+# data from the RSI path, training, gate
+# ---------------------------------------------------------------------------
+def rsi_images(params, n_piston=1 << 14, n_iface=1 << 16, chunk=512, index0=0, device="cuda"):
+    """Normalised images k phi / v0 (complex64 [n, 128, 128]) of the c5
+    chains for each parameter row, computed by the batched RSI path."""
+    out = []
+    for c0 in range(0, len(params), chunk):
+        cfgs = [W.c5_instance(params[i], index0 + i, n_piston, n_iface) for i in range(c0, min(len(params), c0 + chunk))]
+        b = rsi.Batch(cfgs, seed=0, device=device)
+        b.run()
+        out.append(b.images.view(len(cfgs), 128, 128).clone())
+        b.close()
+        del b
+    rsi.sync_status()
+    return torch.cat(out, 0)
+
+
+def demodulate(images, params, device="cuda"):
+    """Envelope = image * exp(-i psi), as interleaved f32 [n, 2*128*128]."""
+    car = torch.tensor(carrier_coeffs(params), dtype=torch.float64, device=device)
+    x = torch.view_as_real(images.contiguous()).reshape(images.shape[0], -1)
+    out = torch.empty_like(x)
+    rsi.nn_carrier(car, WINDOW, -1, x, out)
+    return out
+
+
+def modulate(env, params, device="cuda"):
+    """Image (complex64 [n, 128, 128]) from an interleaved envelope."""
+    car = torch.tensor(carrier_coeffs(params), dtype=torch.float64, device=device)
+    out = torch.empty_like(env)
+    rsi.nn_carrier(car, WINDOW, +1, env.contiguous(), out)
+    return torch.view_as_complex(out.view(env.shape[0], 128, 128, 2))
+
+
+def rel_errors(pred, ref):
+    """Per-sample relative L2 error of complex images."""
+    d = (pred - ref).reshape(pred.shape[0], -1)
+    r = ref.reshape(ref.shape[0], -1)
+    return (torch.linalg.vector_norm(d, dim=1) / torch.linalg.vector_norm(r, dim=1)).float()
+
+
+class Surrogate:
+    """Trained network + held-out error table for the fallback gate."""
+
+    def __init__(self, net: MLP, held_params, held_err, threshold=1e-2, k=8):
+        self.net, self.threshold, self.k = net, threshold, k
+        self.held_u = self._norm(held_params)
+        self.held_err = np.asarray(held_err, np.float64)
+
+    @staticmethod
+    def _norm(params):
+        return 2.0 * (np.asarray(params, np.float64) - LO) / (HI - LO) - 1.0
+
+    def error_estimate(self, params) -> np.ndarray:
+        """Mean held-out error of the k nearest held-out samples (in the
+        normalised parameter box) of each query."""
+        u = self._norm(params)
+        d = ((u[:, None, :] - self.held_u[None, :, :]) ** 2).sum(-1)
+        nn = np.argpartition(d, min(self.k, d.shape[1] - 1), axis=1)[:, :self.k]
+        return self.held_err[nn].mean(axis=1)
+
+    def infer(self, params, device="cuda"):
+        """Images for params (batch = the network's batch): surrogate where
+        the error estimate is within the threshold, RSI elsewhere."""
+        params = np.asarray(params, np.float64)
+        p = torch.tensor(params, dtype=torch.float32, device=device)
+        env = self.net.predict(p) * self.net.scale
+        img = modulate(env, params, device)
+        est = self.error_estimate(params)
+        fall = np.nonzero(est > self.threshold)[0]
+        if len(fall):
+            img[torch.tensor(fall, device=device)] = rsi_images(params[fall], index0=10**6).to(img.dtype)
+        return img, est, fall
+
+
+def train(net: MLP, params, env, epochs: int, lr: float = 1e-3, seed: int = 0, log=None):
+    """Adam on shuffled mini-batches of (params, scaled envelopes)."""
+    n = params.shape[0]
+    B = net.B_alloc
+    rng = np.random.default_rng(seed)
+    p_all = torch.tensor(params, dtype=torch.float32, device=net.device)
+    steps = (n // B) * epochs
+    total = 0
+    losses = []
+    for ep in range(epochs):
+        order = torch.tensor(rng.permutation(n)[: (n // B) * B], device=net.device).view(-1, B)
+        for idx in order:
+            frac = total / max(1, steps)
+            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * frac))
+            loss = net.train_step(p_all[idx], env[idx], lr_t)
+            total += 1
+        losses.append(float(loss.item()))
+        if log:
+            log(ep, losses[-1])
+    return losses

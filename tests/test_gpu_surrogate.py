@@ -1,0 +1,180 @@
+"""Surrogate kernels (rsi_nn_*) on the GPU.
+
+GEMM epilogues against a plain PyTorch FP32 reference of the same op; Adam
+against the FP64 oracle; forward and backward of a small network against the
+FP64 oracle MLP (oracle/mlp.py) holding the same BF16-rounded weights.
+Tolerances follow from BF16 (8-bit significand, unit roundoff 2^-9 ~ 2e-3):
+activations are rounded to BF16 between layers, so a few roundoffs per layer
+accumulate over the network."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as omlp
+from paper_2408_06765_gb300 import build, rsi, surrogate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return rsi.load()
+
+
+def rel(a, b):
+    a, b = a.double().flatten(), b.double().flatten()
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (256, 512, 256), (384, 256, 96)])
+def test_gemm_epilogues_match_fp32_reference(M, N, K):
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    ref = A.float() @ B.float().T
+    out = torch.empty(M, N, device="cuda")
+    rsi.nn_gemm("f32", A, B, out_f32=out)
+    assert rel(out, ref) < 1e-5
+    rsi.nn_gemm("f32", A, B, out_f32=out, bias=bias)
+    assert rel(out, ref + bias) < 1e-5
+    h = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    rsi.nn_gemm("bias_silu", A, B, out_f32=out, out_bf16=h, bias=bias)
+    z = ref + bias
+    assert rel(out, z) < 1e-5
+    assert rel(h.float(), torch.nn.functional.silu(z)) < 6e-3
+    aux = torch.randn(M, N, device="cuda", generator=g)
+    rsi.nn_gemm("dsilu", A, B, out_bf16=h, aux=aux)
+    s = torch.sigmoid(aux)
+    assert rel(h.float(), ref * s * (1 + aux * (1 - s))) < 6e-3
+
+
+def test_transpose_colsum_cast():
+    x = torch.randn(300, 70, device="cuda").to(torch.bfloat16)
+    t = torch.empty(70, 300, dtype=torch.bfloat16, device="cuda")
+    rsi.nn_transpose(x, t)
+    assert torch.equal(t, x.T)
+    cs = torch.empty(70, device="cuda")
+    rsi.nn_colsum(x, cs)
+    assert rel(cs, x.float().sum(0)) < 1e-5
+    f = torch.randn(1000, device="cuda")
+    h = torch.empty(1000, dtype=torch.bfloat16, device="cuda")
+    rsi.nn_cast_bf16(f, h)
+    assert torch.equal(h, f.to(torch.bfloat16))
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(0)
+    w0 = rng.normal(size=4096)
+    w = torch.tensor(w0, dtype=torch.float32, device="cuda")
+    m, v = torch.zeros_like(w), torch.zeros_like(w)
+    wo, mo, vo = w0.astype(np.float32).astype(np.float64), np.zeros(4096), np.zeros(4096)
+    for step in range(1, 6):
+        g = rng.normal(size=4096)
+        rsi.nn_adam(w, m, v, torch.tensor(g, dtype=torch.float32, device="cuda"), 1e-3, step)
+        wo, mo, vo = omlp.adam_step(wo, g.astype(np.float32).astype(np.float64), mo, vo, step, 1e-3)
+    assert np.max(np.abs(w.cpu().numpy() - wo)) < 1e-6
+
+
+def test_carrier_round_trip_and_definition():
+    params = surrogate.LO + (surrogate.HI - surrogate.LO) * np.random.default_rng(1).uniform(size=(3, 5))
+    img = torch.randn(3, 128, 128, dtype=torch.complex64, device="cuda")
+    env = surrogate.demodulate(img, params)
+    back = surrogate.modulate(env, params)
+    assert rel(torch.view_as_real(back), torch.view_as_real(img)) < 1e-6
+    # psi at one pixel, restated
+    k2, s, c, depth = surrogate.carrier_coeffs(params)[0]
+    x = -20e-3 + (5 + 0.5) * 40e-3 / 128
+    z = 0.0 + (7 + 0.5) * 40e-3 / 128
+    psi = k2 * (s * x + c * (z + depth))
+    want = complex(img[0, 7, 5]) * np.exp(-1j * psi)
+    got = env[0].view(128, 128, 2)[7, 5]
+    assert abs(complex(got[0], got[1]) - want) < 1e-5 * abs(want) + 1e-6
+
+
+def small_net():
+    return surrogate.MLP(n_freq=64, width=128, depth=2, n_out=256, batch=128, seed=3, sigma_b=1.0)
+
+
+def oracle_params(net):
+    Wq = [w16.double().cpu().numpy() for w16 in net.W16]  # the BF16 weights the GPU multiplies by
+    bq = [b.double().cpu().numpy() for b in net.b]
+    return {"W": Wq, "b": bq}
+
+
+def test_forward_backward_match_fp64_oracle():
+    net = small_net()
+    rng = np.random.default_rng(4)
+    params = surrogate.LO + (surrogate.HI - surrogate.LO) * rng.uniform(size=(128, 5))
+    t = rng.normal(size=(128, 256)) * 0.5
+    p_d = torch.tensor(params, dtype=torch.float32, device="cuda")
+    t_d = torch.tensor(t, dtype=torch.float32, device="cuda")
+    y = net.forward(p_d).clone()
+    loss = float(net.loss(t_d).item())
+    net.backward()
+    torch.cuda.synchronize()
+    P = oracle_params(net)
+    p32 = params.astype(np.float32).astype(np.float64)
+    yo, cache = omlp.forward(P, p32, surrogate.LO.astype(np.float32), surrogate.HI.astype(np.float32),
+                             net.fmat.double().cpu().numpy())
+    go = omlp.backward(P, cache, yo, t)
+    assert rel(y, torch.tensor(yo)) < 2e-2
+    assert abs(loss - omlp.loss(yo, t)) < 2e-2 * omlp.loss(yo, t)
+    for l in range(len(P["W"])):
+        assert rel(net.gW[l], torch.tensor(go["W"][l])) < 5e-2, l
+        assert rel(net.gb[l], torch.tensor(go["b"][l])) < 5e-2, l
+
+
+def test_training_reduces_the_loss():
+    net = small_net()
+    rng = np.random.default_rng(5)
+    params = surrogate.LO + (surrogate.HI - surrogate.LO) * rng.uniform(size=(1024, 5))
+    u = 2 * (params - surrogate.LO) / (surrogate.HI - surrogate.LO) - 1
+    t = np.sin(np.pi * u @ rng.normal(size=(5, 256)) * 0.5)  # smooth target family
+    env = torch.tensor(t, dtype=torch.float32, device="cuda")
+    losses = surrogate.train(net, params, env, epochs=30, lr=3e-3)
+    assert losses[-1] < 0.2 * losses[0]
+
+
+@pytest.mark.slow
+def test_surrogate_pipeline_gain_and_gate():
+    """Train on fields from the batched RSI path (reduced counts), measure the
+    held-out error, the inference rate against the RSI path, and that the gate
+    sends queries whose error estimate exceeds 1e-2 back to the RSI path."""
+    import time
+    from paper_2408_06765_gb300 import workloads as W
+    n = 1536
+    params = W.c5_params(n, seed=1)
+    t0 = time.perf_counter()
+    imgs = surrogate.rsi_images(params, n_piston=1 << 12, n_iface=1 << 14)
+    torch.cuda.synchronize()
+    rsi_rate = n / (time.perf_counter() - t0)
+    env = surrogate.demodulate(imgs, params)
+    tr, ho = slice(0, 1280), slice(1280, 1536)
+    scale = float(env[tr].pow(2).mean().sqrt())
+    net = surrogate.MLP(batch=256)
+    net.scale = scale
+    losses = surrogate.train(net, params[tr], env[tr] / scale, epochs=20, lr=1e-3)
+    assert losses[-1] < losses[0]
+    pb = torch.tensor(params[ho], dtype=torch.float32, device="cuda")
+    pred = surrogate.modulate(net.predict(pb) * scale, params[ho])
+    errs = surrogate.rel_errors(pred, imgs[ho]).cpu().numpy()
+    assert np.all(np.isfinite(errs))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        surrogate.modulate(net.predict(pb) * scale, params[ho])
+    torch.cuda.synchronize()
+    nn_rate = 5 * 256 / (time.perf_counter() - t0)
+    assert nn_rate > rsi_rate  # what the network gains over the method
+    sur = surrogate.Surrogate(net, params[ho], errs, threshold=1e-2)
+    q = params[:256]
+    img, est, fall = sur.infer(q)
+    assert set(fall.tolist()) == set(np.nonzero(est > 1e-2)[0].tolist())
+    if len(fall):
+        ref = surrogate.rsi_images(q[fall], index0=10**6)
+        assert torch.equal(img[torch.tensor(fall, device="cuda")], ref)
