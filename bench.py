@@ -59,31 +59,46 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
-    ap.add_argument("--config", choices=["c2", "c4", "c5"], default="c2",
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5"], default="c2",
                     help="c4: the batched broadband scan (2048 instances in one CUDA graph); "
                          "c5: the learned surrogate (train on RSI fields, compare)")
     ap.add_argument("--fields", type=int, default=20000, help="c5: training fields")
-    ap.add_argument("--epochs", type=int, default=60, help="c5: training epochs")
+    ap.add_argument("--instances", type=int, default=0, help="c4: first N instances only (0 = all)")
+    ap.add_argument("--epochs", type=int, default=300, help="c5: training epochs")
+    ap.add_argument("--sigma-b", type=float, default=0.25, help="c5: Fourier feature scale")
+    ap.add_argument("--lr", type=float, default=1e-3, help="c5: peak learning rate")
     ap.add_argument("--sweep", action="store_true",
                     help="with --case stage: time every tile / targets-per-thread / variant")
     return ap.parse_args()
 
 
-def workload():
+DESCRIPTION = {
+    "c1": "c1 plain RSI in FP64: 4096 piston x 4096 interface (60 mm) x 64^2 image, 5 MHz, "
+          "water -> steel at 50 mm",
+    "c2": "c2 full-image RSI: 2^16 piston x 2^18 interface (80 mm) x 512^2 image, "
+          "f = 2.25/5/10 MHz, water -> steel at 50 mm",
+    "c3": "c3 multilayer RSI: 5 mm piston, 30 mm water, 8 layers of 0.5 mm (9 interfaces of 2^16 "
+          "points), 256^2 image below; flat and concentric-cylinder variants",
+}
+
+
+def workload(name: str = "c2"):
     from paper_2408_06765_gb300 import workloads as W
-    cfgs = W.c2_all()
+    cfgs = {"c1": lambda: [W.c1_plain_fp64()], "c2": W.c2_all,
+            "c3": lambda: [W.c3_multilayer(False), W.c3_multilayer(True)]}[name]()
     pairs = sum(W.pairs_of(c) for c in cfgs)
     pixels = sum(int(c["grid"]["nx"]) * int(c["grid"]["nz"]) for c in cfgs)
     return cfgs, pairs, pixels
 
 
-def config_block(cfgs, n_gpus):
-    return {"workload": "c2 full-image RSI: 2^16 piston x 2^18 interface (80 mm) x 512^2 image, "
-                        "f = 2.25/5/10 MHz, water -> steel at 50 mm",
+def config_block(cfgs, n_gpus, name="c2"):
+    return {"workload": DESCRIPTION[name],
             "frequencies_mhz": [c["freq"] / 1e6 for c in cfgs],
             "n_piston": cfgs[0]["piston"]["n"], "n_interface": cfgs[0]["interfaces"][0]["n"],
+            "interfaces": len(cfgs[0]["interfaces"]),
             "image": [cfgs[0]["grid"]["nz"], cfgs[0]["grid"]["nx"]],
-            "precision": "fp32 pairs, double-float phase, compensated sums",
+            "precision": ("fp64" if cfgs[0]["precision"] == "fp64"
+                          else "fp32 pairs, double-float phase, compensated sums"),
             "l2": "flushed (256 MiB write) before every timed step",
             "parallelism": f"replica per GPU x{n_gpus}" if n_gpus > 1 else "1 GPU"}
 
@@ -182,26 +197,28 @@ def oracle_sample(cfg, seconds: float, seed: int = 0):
     oracle.build()
     pc = cfg["piston"]
     it = cfg["interfaces"][0]
+    last = cfg["interfaces"][-1]
     piston = oracle.make_points(dict(pc, kind="disk"), cfg["seed"], pc["set_id"], pc["n"])
     iface = oracle.make_points(it, cfg["seed"], it["set_id"], it["n"])
+    lface = oracle.make_points(last, cfg["seed"], last["set_id"], last["n"])
     grid = oracle.grid_points(cfg["grid"])
     k1 = oracle.wavenumber(cfg["freq"], cfg["media"][0]["c"])
-    k2 = oracle.wavenumber(cfg["freq"], cfg["media"][1]["c"])
+    kl = oracle.wavenumber(cfg["freq"], cfg["media"][len(cfg["interfaces"])]["c"])
     rng = np.random.default_rng(seed)
-    sig = np.ones(it["n"], np.complex128)
+    sig = np.ones(last["n"], np.complex128)
 
     def run(m1, m2):
-        s1 = rng.choice(it["n"], m1, replace=False)
-        s2 = rng.choice(grid["x"].shape[0], m2, replace=False)
+        s1 = rng.choice(it["n"], min(m1, it["n"]), replace=False)
+        s2 = rng.choice(grid["x"].shape[0], min(m2, grid["x"].shape[0]), replace=False)
         t0 = time.perf_counter()
         phi1 = oracle.piston_field(piston, {k: iface[k][s1] for k in ("x", "y", "z")}, k1)
-        oracle.rsi_field(iface, sig, {k: grid[k][s2] for k in ("x", "y", "z")}, k2)
+        oracle.rsi_field(lface, sig, {k: grid[k][s2] for k in ("x", "y", "z")}, kl)
         dt = time.perf_counter() - t0
-        return dt, pc["n"] * m1 + it["n"] * m2, s1, phi1
+        return dt, pc["n"] * len(s1) + last["n"] * len(s2), s1, phi1
 
     dt, pairs, _, _ = run(32, 8)
     rate = pairs / dt
-    m = max(16, int(seconds * rate / (pc["n"] + it["n"]) / 2))
+    m = max(16, int(seconds * rate / (pc["n"] + last["n"]) / 2))
     dt, pairs, s1, phi1 = run(m, m)
     return {"seconds": dt, "pairs": pairs, "rate": pairs / dt, "m": m,
             "iface_slots_natural": s1, "phi1": phi1, "threads": oracle.default_threads()}
@@ -235,6 +252,12 @@ def reduce_max(v: float, world: int):
     return float(t.item())
 
 
+def aggregate(world: int, units_per_step_per_rank: float, steps: int, local_seconds: float):
+    """Whole-job rate: units of all ranks over the slowest rank's time."""
+    total_s = reduce_max(local_seconds, world)
+    return total_s, world * units_per_step_per_rank * steps / total_s
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -249,7 +272,7 @@ def run_ours(args):
     rsi.load()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    cfgs, pairs_step, pixels_step = workload()
+    cfgs, pairs_step, pixels_step = workload(args.config)
     ws = rsi.Workspace(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -285,8 +308,7 @@ def run_ours(args):
     pis_ms, pis_n, pis_pairs = rsi.timing_read(rsi.STAGE_PISTON)
     rsi.timing_enable(False)
     rsi.sync_status()
-    total_s = reduce_max(sum(step_ms) * 1e-3, world)
-    value = world * pairs_step * args.steps / total_s
+    total_s, value = aggregate(world, pairs_step, args.steps, sum(step_ms) * 1e-3)
 
     # dominant kernel: the RSI stage kernel (interface -> image dominates)
     avg_s = rsi_ms * 1e-3 / max(1, rsi_n)
@@ -305,6 +327,12 @@ def run_ours(args):
             "piston_kernel": {"achieved": (pis_pairs / max(1, pis_n)) / max(pis_avg, 1e-12) / 1e9,
                               "peak": pis_peak / 1e9, "avg_launch_ms": pis_avg * 1e3,
                               "launches": pis_n}}
+    if cfgs[0]["precision"] == "fp64":
+        roof = {"bound": "alu", "kernel": "stage_fp64_kernel", "achieved": achieved / 1e9,
+                "peak": None, "unit": "Gpair/s", "frac": None, "traffic": None,
+                "note": "FP64 path (sqrt, division and sincos in double on the FP64 pipe); "
+                        "no FP64 roofline is modelled",
+                "avg_launch_ms": avg_s * 1e3, "launches": rsi_n}
     traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_file):
         try:
@@ -327,8 +355,8 @@ def run_ours(args):
                 h.copy_(im, non_blocking=True)
             torch.cuda.synchronize()
             e2e_s.append(time.perf_counter() - t0)
-        tot = reduce_max(sum(e2e_s), world)
-        e2e = {"value": world * pairs_step * args.steps / tot, "unit": UNIT,
+        _, e2e_value = aggregate(world, pairs_step, args.steps, sum(e2e_s))
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                "note": "inputs are scalar workload parameters passed by value through the "
                        "C ABI (no array inputs); the three c64 images are read back each step"}
@@ -337,7 +365,7 @@ def run_ours(args):
     err = None
     if rank == 0 and not args.no_cpu_baseline:
         import numpy as np
-        cfg = cfgs[1]
+        cfg = cfgs[min(1, len(cfgs) - 1)]
         smp = oracle_sample(cfg, args.cpu_seconds)
         cpu = {"value": smp["rate"], "unit": UNIT, "cores": smp["threads"], "kind": "oracle",
                "sample": f"c2 at {cfg['freq'] / 1e6:g} MHz: all {cfg['piston']['n']} piston points "
@@ -345,7 +373,7 @@ def run_ours(args):
                          f"{cfg['interfaces'][0]['n']} interface points onto {smp['m']} random "
                          f"pixels ({smp['pairs']:.3g} pairs, {smp['seconds']:.1f} s), FP64"}
         res = rsi.run_chain(cfg, keep=True, workspace=ws, device=dev)
-        (gif, gphi), = res.ifaces
+        gif, gphi = res.ifaces[0]
         idx = gif.field("IDX").cpu().numpy().view(np.uint32)
         slot_of = np.empty_like(idx)
         slot_of[idx] = np.arange(idx.size, dtype=np.uint32)
@@ -356,11 +384,13 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": max(3, args.warmup),
                 "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if cfgs[0]["precision"] == "fp64" else "f32",
                 "data": "synthetic (seeded scrambled-Sobol points; workload parameters only)",
-                "config": config_block(cfgs, world),
+                "config": config_block(cfgs, world, args.config),
                 "field_pts_per_s": world * pixels_step * args.steps / total_s,
-                "rel_l2_err": {"piston_stage_sampled_vs_fp64_oracle": err, "tolerance": 1e-4},
+                "rel_l2_err": {"piston_stage_sampled_vs_fp64_oracle": err,
+                               "tolerance": 1e-5 if cfgs[0]["precision"] == "fp64" else 1e-4},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev)}
         print(json.dumps(line), flush=True)
@@ -375,8 +405,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cfgs, _, _ = workload()
-    cfg = cfgs[1]
+    cfgs, _, _ = workload(args.config if args.config in DESCRIPTION else "c2")
+    cfg = cfgs[min(1, len(cfgs) - 1)]
     per_step = max(2.0, min(20.0, 90.0 / max(1, args.steps + args.warmup)))
     for _ in range(max(1, args.warmup)):
         oracle_sample(cfg, 1.0, seed=99)
@@ -389,12 +419,13 @@ def run_reference(args):
     value = pairs / secs
     cpu = {"value": value, "unit": UNIT, "cores": smp["threads"], "kind": "oracle",
            "sample": f"per step: all piston points onto {smp['m']} interface points + all "
-                     f"interface points onto {smp['m']} pixels of c2 at 5 MHz, FP64"}
+                     f"interface points onto {smp['m']} pixels of {cfg['name']}, FP64"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(1, args.warmup),
             "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_block(cfgs, 1), "cpu_baseline": cpu,
+            "config": config_block(cfgs, 1, args.config if args.config in DESCRIPTION else "c2"),
+            "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -443,6 +474,8 @@ def run_batch_c4(args):
     from paper_2408_06765_gb300 import workloads as W
     build.build()
     cfgs = W.c4_all()
+    if args.instances:
+        cfgs = cfgs[:args.instances]
     pairs = sum(W.pairs_of(c) for c in cfgs)
     pixels = sum(c["grid"]["nx"] * c["grid"]["nz"] for c in cfgs)
     b = rsi.Batch(cfgs, seed=0)
@@ -467,7 +500,7 @@ def run_batch_c4(args):
     total_s = sum(ms) * 1e-3
     # batched vs the plain per-instance loop on the same GPU, on a seeded subset
     rng = np.random.default_rng(0)
-    sub = sorted(rng.choice(len(cfgs), 32, replace=False).tolist())
+    sub = sorted(rng.choice(len(cfgs), min(32, len(cfgs)), replace=False).tolist())
     sub_cfgs = [cfgs[i] for i in sub]
     sb = rsi.Batch(sub_cfgs, seed=0)
     sb.run()
@@ -531,10 +564,10 @@ def run_surrogate_c5(args):
     n_hold = n // 10
     tr, ho = slice(0, n - n_hold), slice(n - n_hold, n)
     scale = float(env[tr].pow(2).mean().sqrt())
-    net = surrogate.MLP(batch=256)
+    net = surrogate.MLP(batch=256, sigma_b=args.sigma_b)
     net.scale = scale
     t0 = time.perf_counter()
-    losses = surrogate.train(net, params[tr], env[tr] / scale, epochs=args.epochs, lr=1e-3)
+    losses = surrogate.train(net, params[tr], env[tr] / scale, epochs=args.epochs, lr=args.lr)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     # held-out error (batches of 256)
@@ -545,6 +578,18 @@ def run_surrogate_c5(args):
         pred = surrogate.modulate(net.predict(pb) * scale, hp[c0:c0 + 256])
         errs.append(surrogate.rel_errors(pred, imgs[ho][c0:c0 + 256]).cpu().numpy())
     errs = np.concatenate(errs)
+    # split of the error: the best complex scale per field (amplitude and
+    # global phase) against what remains (shape)
+    shape_errs = []
+    for c0 in range(0, (n_hold // 256) * 256, 256):
+        pb = torch.tensor(hp[c0:c0 + 256], dtype=torch.float32, device="cuda")
+        pred = surrogate.modulate(net.predict(pb) * scale, hp[c0:c0 + 256]).reshape(256, -1)
+        ref = imgs[ho][c0:c0 + 256].reshape(256, -1)
+        alpha = (pred.conj() * ref).sum(1) / (pred.conj() * pred).sum(1)
+        shape_errs.append(surrogate.rel_errors(alpha[:, None] * pred, ref).cpu().numpy())
+    shape_errs = np.concatenate(shape_errs)
+    tilt_deg = np.degrees(hp[:len(errs), 1])
+    post = np.abs(tilt_deg) > np.degrees(np.arcsin(1480.0 / 5900.0))
     # inference throughput at batch 1024 vs the RSI path on the same fields
     inf = surrogate.MLP(batch=1024)
     for a, b_ in zip(inf.W16 + inf.b, net.W16 + net.b):
@@ -569,8 +614,13 @@ def run_surrogate_c5(args):
                        "rsi_points": [1 << 14, 1 << 16]},
             "rsi_generation_s": gen_s, "rsi_fields_per_s": rsi_fields_s,
             "train_s": train_s, "final_train_loss": losses[-1],
+            "train_loss_curve": losses[:: max(1, len(losses) // 10)],
+            "sigma_b": args.sigma_b, "lr": args.lr,
             "held_out_rel_l2": {"median": float(np.median(errs)), "mean": float(errs.mean()),
                                 "p90": float(np.quantile(errs, 0.9)), "max": float(errs.max())},
+            "held_out_shape_only_rel_l2_median": float(np.median(shape_errs)),
+            "held_out_median_pre_critical": float(np.median(errs[~post])) if (~post).any() else None,
+            "held_out_median_post_critical": float(np.median(errs[post])) if post.any() else None,
             "reaches_1e-3": bool(np.median(errs) <= 1e-3),
             "surrogate_fields_per_s_batch1024": nn_fields_s,
             "speedup_vs_rsi": nn_fields_s / rsi_fields_s,

@@ -314,7 +314,7 @@ int rsi_nn_adam(float *w, float *m, float *v, const float *g, int64_t n, float l
 int rsi_nn_cast_bf16(const float *in, int64_t n, void *out_bf16, void *stream);
 /* out = in * exp(sign i psi) per pixel of batch images (complex f32 pairs,
  * row-major [nz][nx] over `window`, relative coordinates), with
- * psi = k2 (s x + c (z + depth)) and carrier[b] = (k2, s, c, depth) (f64). */
+ * psi = kx x + kz z + phi0 and carrier[b] = (kx, kz, phi0, unused) (f64).  */
 int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window, int32_t sign,
                    const float *in, float *out, void *stream);
 

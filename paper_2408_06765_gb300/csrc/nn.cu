@@ -14,7 +14,7 @@
 //   loss       mean (y - t)^2 and its gradient 2 (y - t)/n  -> bf16
 //   colsum     bias gradients (column sums of a bf16 matrix)
 //   adam       Kingma & Ba (2015) on FP32 master weights, bf16 copy out
-//   carrier    multiply an image by exp(+-i psi), psi = k2 (s x + c (z + depth))
+//   carrier    multiply an image by exp(+-i psi), psi = kx x + kz z + phi0
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -240,7 +240,7 @@ __global__ void cast_kernel(const float* __restrict__ in, int64_t n, bf16* __res
 }
 
 // img[b][j] (complex, float pairs) *= exp(sign * i psi_b(j)),
-// psi = k2 (s x_i + c (z_j + depth)); carrier[b] = (k2, s, c, depth)
+// psi = kx x_i + kz z_j + phi0; carrier[b] = (kx, kz, phi0, unused)
 __global__ void carrier_kernel(const double* __restrict__ carrier, int batch, int nx, int nz, double x0,
                                double dx, double z0, double dz, int sign, const float2* __restrict__ in,
                                float2* __restrict__ out) {
@@ -252,7 +252,7 @@ __global__ void carrier_kernel(const double* __restrict__ carrier, int batch, in
     const int iz = int(j / nx), ix = int(j - int64_t(iz) * nx);
     const double* cb = carrier + 4 * b;
     double x = x0 + (ix + 0.5) * dx, z = z0 + (iz + 0.5) * dz;
-    double psi = cb[0] * (cb[1] * x + cb[2] * (z + cb[3]));
+    double psi = cb[0] * x + cb[1] * z + cb[2];
     double s, c;
     sincospi(psi / M_PI, &s, &c);
     s *= sign;

@@ -10,10 +10,12 @@ weights, Adam); this module sequences the calls and keeps the buffers.
 Network (same definition as the FP64 oracle, oracle/mlp.py):
     u = 2 (p - lo)/(hi - lo) - 1;  h0 = [sin(pi B u), cos(pi B u)]
     h_l = silu(W_l h_{l-1} + b_l), l = 1..depth;  y = W_out h_depth + b_out
-The output y is the image times exp(-i psi) (the plane-wave carrier of the
-refracted beam, psi = k2 (s x + c (z + depth)), s = (c2/c1) sin(tilt),
-c = sqrt(1 - s^2) or 0 past the critical angle), real and imaginary parts
-interleaved, divided by a fixed amplitude scale.
+The output y is the image times exp(-i psi), psi the phase of the refracted
+plane wave: psi = k1 L + k2 (s x + c (z + depth)) with L the water path,
+s = (c2/c1) sin(tilt) and c = sqrt(1 - s^2) (0 past the critical angle), x, z
+measured from the point where the axis meets the interface and from the
+window's top edge; real and imaginary parts interleaved and divided by a
+fixed amplitude scale.
 """
 from __future__ import annotations
 
@@ -32,12 +34,14 @@ WINDOW = {"x0": -20e-3, "x1": 20e-3, "nx": 128, "z0": 0.0, "z1": 40e-3, "nz": 12
 
 
 def carrier_coeffs(params) -> np.ndarray:
-    """(k2, s, c, depth) per sample: the refracted plane-wave carrier."""
+    """(kx, kz, phi0, 0) per sample: psi = kx x + kz z + phi0 is the phase of
+    the refracted plane wave (water path phase k1 L included)."""
     p = np.atleast_2d(np.asarray(params, np.float64))
+    k1 = 2 * np.pi * p[:, 3] / C1
     k2 = 2 * np.pi * p[:, 3] / C2
     s = C2 / C1 * np.sin(p[:, 1])
     c = np.sqrt(np.clip(1.0 - s * s, 0.0, None))
-    return np.stack([k2, s, c, p[:, 4]], axis=1)
+    return np.stack([k2 * s, k2 * c, k1 * p[:, 2] + k2 * c * p[:, 4], np.zeros(len(p))], axis=1)
 
 
 class MLP:

