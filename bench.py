@@ -561,7 +561,9 @@ def run_surrogate_c5(args):
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     env = surrogate.demodulate(imgs, params)
-    n_hold = n // 10
+    n_hold = max(256, n // 10)  # at least one inference batch
+    if n_hold >= n:
+        raise SystemExit("c5 needs more than 256 fields")
     tr, ho = slice(0, n - n_hold), slice(n - n_hold, n)
     scale = float(env[tr].pow(2).mean().sqrt())
     net = surrogate.MLP(batch=256, sigma_b=args.sigma_b)

@@ -332,6 +332,13 @@ uint64_t rsi_launch_count(void);
 int rsi_timing_enable(int32_t on);
 int rsi_timing_read(int32_t kind, double *total_ms, int64_t *launches, double *pairs);
 
+/* Exercises the device-side failure path without a fault: one CTA waits on
+ * an mbarrier that nothing completes, gives up after `cycles` SM clocks
+ * (1 .. 2^32) exactly as the stage kernels' bounded waits do, records
+ * RSI_E_TIMEOUT in the status word and exits; rsi_sync_status() then returns
+ * RSI_E_TIMEOUT (and clears the word).                                      */
+int rsi_selftest_wait_timeout(int64_t cycles, void *stream);
+
 /* Throughput probes for the ALU roofline: `iters` iterations of 8
  * independent dependency chains per thread of one operation,
  *   RSI_UB_FFMA  fused multiply-add (FP32 pipe)

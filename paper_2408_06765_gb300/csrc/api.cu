@@ -131,3 +131,30 @@ int rsi_num_sms() {
     }
     return cached[dev];
 }
+
+// ---------------------------------------------------------------------------
+// self-test of the device-side failure path: every thread of one CTA waits on
+// an mbarrier that nothing completes, with a limit of `cycles`; the expired
+// wait records RSI_DEV_TIMEOUT in the status word (as the stage kernels do)
+// and the kernel returns.  Nothing faults or hangs.
+// ---------------------------------------------------------------------------
+static __global__ void wait_timeout_kernel(long long cycles, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    bool ok = mbar_wait_bounded(smem_u32(&bar), 0, cycles);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(status, RSI_DEV_TIMEOUT);
+}
+
+extern "C" int rsi_selftest_wait_timeout(int64_t cycles, void* stream) {
+    if (cycles < 1 || cycles > (int64_t(1) << 32))
+        return rsi_fail(RSI_E_INVAL, "rsi_selftest_wait_timeout: cycles out of range");
+    int* st = rsi_status_ptr();
+    if (!st) return RSI_E_CUDA;
+    wait_timeout_kernel<<<1, 64, 0, static_cast<cudaStream_t>(stream)>>>(cycles, st);
+    RSI_CHECK_LAUNCH("wait_timeout_kernel");
+    return RSI_OK;
+}

@@ -39,7 +39,8 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_field_image", "rsi_launch_count", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
-           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier"]
+           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier",
+           "rsi_selftest_wait_timeout"]
 NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
 UB = {"ffma": 0, "rsqrt": 1, "sin": 2}
 
@@ -130,6 +131,7 @@ def load(path: str | None = None):
         L.rsi_nn_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
         L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
         L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, vp, vp, vp]
+        L.rsi_selftest_wait_timeout.argtypes = [i64, vp]
         _lib = L
         return L
 
