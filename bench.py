@@ -158,13 +158,13 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def measure_unit_rates(rsi, torch):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    blocks, iters = sms * 8, 4096
+    blocks, iters = sms * 8, 65536
     sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
     rates = {}
     for kind in ("ffma", "rsqrt", "sin"):
         rsi.ubench(kind, blocks, 64, sink)  # warm-up
         best = float("inf")
-        for _ in range(3):
+        for _ in range(5):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             rsi.ubench(kind, blocks, iters, sink)
@@ -175,13 +175,17 @@ def measure_unit_rates(rsi, torch):
     return rates
 
 
-def alu_roofline(kind: str, rates: dict):
-    """Peak pairs/s of a stage kernel: the tighter of the issue limit (one warp
-    instruction per scheduler per clock, measured as the FFMA rate) and the
-    MUFU limit (measured rsqrt rate)."""
+# sm_100-family unit counts per SM per clock: 4 schedulers x 32 lanes issue
+# (FP32 FMA rate), 16 MUFU lanes; the probes in rsi_ubench confirm them.
+ISSUE_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
+
+
+def alu_roofline(kind: str, n_sm: int, clock_hz: float):
+    """Peak pairs/s of a stage kernel at `clock_hz`: the tighter of the issue
+    limit (one warp instruction per scheduler per clock) and the MUFU limit."""
     o = OPS[kind]
-    issue = (o["fp32"] + o["mufu"] + o["lds"]) / rates["ffma"]
-    mufu = o["mufu"] / rates["rsqrt"]
+    issue = (o["fp32"] + o["mufu"] + o["lds"]) / (ISSUE_LANES_PER_SM * n_sm * clock_hz)
+    mufu = o["mufu"] / (MUFU_LANES_PER_SM * n_sm * clock_hz)
     return 1.0 / max(issue, mufu), ("mufu" if mufu >= issue else "issue")
 
 
@@ -284,7 +288,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     rsi.sync_status()
 
-    rates = measure_unit_rates(rsi, torch)
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
@@ -304,6 +307,7 @@ def run_ours(args):
     launches = rsi.launch_count() - n0
     barrier(world)
     clk = clocks.stop()
+    rates = measure_unit_rates(rsi, torch)  # cross-check of the unit counts, GPU warm
     rsi_ms, rsi_n, rsi_pairs = rsi.timing_read(rsi.STAGE_RSI)
     pis_ms, pis_n, pis_pairs = rsi.timing_read(rsi.STAGE_PISTON)
     rsi.timing_enable(False)
@@ -313,16 +317,21 @@ def run_ours(args):
     # dominant kernel: the RSI stage kernel (interface -> image dominates)
     avg_s = rsi_ms * 1e-3 / max(1, rsi_n)
     achieved = (rsi_pairs / max(1, rsi_n)) / avg_s
-    peak, limiter = alu_roofline("rsi", rates)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_hz = (clk["sm_mhz"] if clk and clk.get("sm_mhz") else
+              rates["ffma"] / (ISSUE_LANES_PER_SM * n_sm) / 1e6) * 1e6
+    peak, limiter = alu_roofline("rsi", n_sm, clk_hz)
     pis_avg = pis_ms * 1e-3 / max(1, pis_n)
-    pis_peak, _ = alu_roofline("piston", rates)
+    pis_peak, _ = alu_roofline("piston", n_sm, clk_hz)
     roof = {"bound": "alu", "kernel": "stage_fp32_kernel<RSI>", "achieved": achieved / 1e9,
             "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
             "limiter": limiter,
             "ops_per_pair": OPS["rsi"],
-            "peak_source": "measured in this run: FFMA issue rate and MUFU rsqrt rate "
-                           "(rsi_ubench), same clocks as the timed region",
-            "unit_rates_tops": {k: v / 1e12 for k, v in rates.items()},
+            "peak_source": "unit counts (128 issue lanes, 16 MUFU lanes per SM per clock) x "
+                           f"{n_sm} SMs x the median SM clock of the timed region "
+                           f"({clk_hz / 1e6:.0f} MHz)",
+            "probe_rates_tops": {k: v / 1e12 for k, v in rates.items()},
+            "probe_lanes_per_sm_clock": {k: v / (n_sm * clk_hz) for k, v in rates.items()},
             "avg_launch_ms": avg_s * 1e3, "launches": rsi_n,
             "piston_kernel": {"achieved": (pis_pairs / max(1, pis_n)) / max(pis_avg, 1e-12) / 1e9,
                               "peak": pis_peak / 1e9, "avg_launch_ms": pis_avg * 1e3,

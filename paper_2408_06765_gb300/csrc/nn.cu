@@ -56,12 +56,36 @@ __device__ __forceinline__ float dsilu_(float z) {
     return s * (1.0f + z * (1.0f - s));
 }
 
-// M % 128 == 0, N % 128 == 0, K % 32 == 0 (checked on the host)
+// epilogue of one pair of neighbouring outputs (row, col), (row, col + 1)
+template <int EPI>
+__device__ __forceinline__ void epilogue2(float v0, float v1, size_t o, int col, const float* __restrict__ bias,
+                                          const float* __restrict__ aux, float* __restrict__ outf,
+                                          bf16* __restrict__ outh) {
+    if (EPI == 0) {  // F32 (+ bias)
+        if (bias) {
+            v0 += bias[col];
+            v1 += bias[col + 1];
+        }
+        *reinterpret_cast<float2*>(outf + o) = make_float2(v0, v1);
+    } else if (EPI == 1) {  // BIAS_SILU
+        v0 += bias[col];
+        v1 += bias[col + 1];
+        *reinterpret_cast<float2*>(outf + o) = make_float2(v0, v1);
+        *reinterpret_cast<__nv_bfloat162*>(outh + o) = __floats2bfloat162_rn(silu_(v0), silu_(v1));
+    } else {  // DSILU
+        const float2 z = *reinterpret_cast<const float2*>(aux + o);
+        *reinterpret_cast<__nv_bfloat162*>(outh + o) = __floats2bfloat162_rn(v0 * dsilu_(z.x), v1 * dsilu_(z.y));
+    }
+}
+
+// M % 128 == 0, N % 128 == 0, K % 32 == 0 (checked on the host).  With
+// gridDim.z > 1 (split K), CTA z covers k-tiles [z*kts, (z+1)*kts) and writes
+// plain FP32 partial sums to outf + z*M*N; splitk_reduce_kernel finishes.
 template <int EPI>
 __global__ void __launch_bounds__(GEMM_THREADS)
     gemm_tn_kernel(const bf16* __restrict__ A, const bf16* __restrict__ B, int M, int N, int K,
                    const float* __restrict__ bias, const float* __restrict__ aux, float* __restrict__ outf,
-                   bf16* __restrict__ outh) {
+                   bf16* __restrict__ outh, int kts) {
     extern __shared__ __align__(128) uint8_t smem_raw[];
     bf16* sA = reinterpret_cast<bf16*>(smem_raw);
     bf16* sB = sA + STAGES * BM * LDS;
@@ -84,17 +108,18 @@ __global__ void __launch_bounds__(GEMM_THREADS)
             cp_async16(&sB[(stage * BN + row) * LDS + col], &B[size_t(bn + row) * K + k0 + col]);
         }
     };
-    const int KT = K / BK;
+    const int kt0 = blockIdx.z * kts;
+    const int KT = min(K / BK - kt0, kts);
 #pragma unroll
     for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < KT) load_stage(s, s * BK);
+        if (s < KT) load_stage(s, (kt0 + s) * BK);
         cp_async_commit();
     }
     for (int kt = 0; kt < KT; ++kt) {
         cp_async_wait<STAGES - 2>();
         __syncthreads();
         const int nk = kt + STAGES - 1;
-        if (nk < KT) load_stage(nk % STAGES, nk * BK);
+        if (nk < KT) load_stage(nk % STAGES, (kt0 + nk) * BK);
         cp_async_commit();
         const int st = kt % STAGES;
 #pragma unroll
@@ -132,24 +157,30 @@ __global__ void __launch_bounds__(GEMM_THREADS)
                 const int row = bm + wm + mi * 16 + (lane >> 2) + half * 8;
                 const int col = bn + wn + ni * 8 + (lane & 3) * 2;
                 const size_t o = size_t(row) * N + col;
-                float v0 = acc[mi][ni][2 * half], v1 = acc[mi][ni][2 * half + 1];
-                if (EPI == 0) {  // F32 (+ bias)
-                    if (bias) {
-                        v0 += bias[col];
-                        v1 += bias[col + 1];
-                    }
-                    *reinterpret_cast<float2*>(outf + o) = make_float2(v0, v1);
-                } else if (EPI == 1) {  // BIAS_SILU
-                    v0 += bias[col];
-                    v1 += bias[col + 1];
-                    *reinterpret_cast<float2*>(outf + o) = make_float2(v0, v1);
-                    *reinterpret_cast<__nv_bfloat162*>(outh + o) = __floats2bfloat162_rn(silu_(v0), silu_(v1));
-                } else {  // DSILU
-                    const float2 z = *reinterpret_cast<const float2*>(aux + o);
-                    *reinterpret_cast<__nv_bfloat162*>(outh + o) =
-                        __floats2bfloat162_rn(v0 * dsilu_(z.x), v1 * dsilu_(z.y));
-                }
+                const float v0 = acc[mi][ni][2 * half], v1 = acc[mi][ni][2 * half + 1];
+                if (gridDim.z > 1)
+                    *reinterpret_cast<float2*>(outf + size_t(blockIdx.z) * M * N + o) = make_float2(v0, v1);
+                else
+                    epilogue2<EPI>(v0, v1, o, col, bias, aux, outf, outh);
             }
+}
+
+// sums the split-K partial sums in split order, then applies the epilogue
+template <int EPI>
+__global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits, int M, int N,
+                                     const float* __restrict__ bias, const float* __restrict__ aux,
+                                     float* __restrict__ outf, bf16* __restrict__ outh) {
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // pair index
+    const int64_t total = int64_t(M) * N / 2;
+    if (q >= total) return;
+    const size_t o = size_t(q) * 2;
+    float v0 = 0.0f, v1 = 0.0f;
+    for (int z = 0; z < splits; ++z) {
+        const float2 p = *reinterpret_cast<const float2*>(part + size_t(z) * M * N + o);
+        v0 += p.x;
+        v1 += p.y;
+    }
+    epilogue2<EPI>(v0, v1, o, int(o % size_t(N)), bias, aux, outf, outh);
 }
 
 __global__ void features_kernel(const float* __restrict__ p, const float* __restrict__ lo,
@@ -262,7 +293,7 @@ __global__ void carrier_kernel(const double* __restrict__ carrier, int batch, in
 
 template <int EPI>
 int gemm_launch(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const float* aux, float* outf,
-                bf16* outh, cudaStream_t s) {
+                bf16* outh, int splits, float* work, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(gemm_tn_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -270,9 +301,19 @@ int gemm_launch(const bf16* A, const bf16* B, int M, int N, int K, const float* 
                      "cudaFuncSetAttribute(gemm)");
         attr = true;
     }
-    dim3 grid(N / BN, M / BM);
-    gemm_tn_kernel<EPI><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(A, B, M, N, K, bias, aux, outf, outh);
+    const int kt = K / BK;
+    const int kts = (kt + splits - 1) / splits;
+    splits = (kt + kts - 1) / kts;
+    dim3 grid(N / BN, M / BM, splits);
+    gemm_tn_kernel<EPI><<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(A, B, M, N, K, bias, aux, splits > 1 ? work : outf,
+                                                             outh, kts);
     RSI_CHECK_LAUNCH("gemm_tn_kernel");
+    if (splits > 1) {
+        int64_t pairs = int64_t(M) * N / 2;
+        splitk_reduce_kernel<EPI><<<unsigned((pairs + 255) / 256), 256, 0, s>>>(work, splits, M, N, bias, aux,
+                                                                                 outf, outh);
+        RSI_CHECK_LAUNCH("splitk_reduce_kernel");
+    }
     return RSI_OK;
 }
 
@@ -292,8 +333,12 @@ extern "C" int rsi_nn_features(const float* params, const float* lo, const float
 }
 
 extern "C" int rsi_nn_gemm(int32_t epilogue, const void* A, const void* B, int32_t M, int32_t N, int32_t K,
-                           const float* bias, const float* aux, float* out_f32, void* out_bf16, void* stream) {
+                           const float* bias, const float* aux, float* out_f32, void* out_bf16, int32_t splits,
+                           float* workspace, void* stream) {
     if (!A || !B || M < 1 || N < 1 || K < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: bad arguments");
+    if (splits < 1 || splits > K / BK || (splits > 1 && !workspace))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: splits must be in [1, K/32] and need a workspace");
+    if (misaligned(workspace, 8)) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: misaligned workspace");
     if (M % BM || N % BN || K % BK)
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: M, N must be multiples of 128 and K of 32 (got %d %d %d)", M, N,
                         K);
@@ -307,13 +352,13 @@ extern "C" int rsi_nn_gemm(int32_t epilogue, const void* A, const void* B, int32
     switch (epilogue) {
         case RSI_NN_EPI_F32:
             if (!out_f32) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: F32 epilogue needs out_f32");
-            return gemm_launch<0>(a, b, M, N, K, bias, nullptr, out_f32, nullptr, s);
+            return gemm_launch<0>(a, b, M, N, K, bias, nullptr, out_f32, nullptr, splits, workspace, s);
         case RSI_NN_EPI_BIAS_SILU:
             if (!out_f32 || !oh || !bias) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: BIAS_SILU needs bias and outputs");
-            return gemm_launch<1>(a, b, M, N, K, bias, nullptr, out_f32, oh, s);
+            return gemm_launch<1>(a, b, M, N, K, bias, nullptr, out_f32, oh, splits, workspace, s);
         case RSI_NN_EPI_DSILU:
             if (!aux || !oh) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: DSILU needs aux and out_bf16");
-            return gemm_launch<2>(a, b, M, N, K, nullptr, aux, nullptr, oh, s);
+            return gemm_launch<2>(a, b, M, N, K, nullptr, aux, nullptr, oh, splits, workspace, s);
         default:
             return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: unknown epilogue %d", epilogue);
     }

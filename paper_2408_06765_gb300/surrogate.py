@@ -90,6 +90,12 @@ class MLP:
         self.dZT = [torch.empty((n, B), dtype=bf, device=d) for n in self.dims[1:-1]]
         self.WT = [torch.empty((w.shape[1], w.shape[0]), dtype=bf, device=d) for w in self.W]
         self.partial = torch.empty(1024, dtype=torch.float64, device=d)
+        # split K for the backward GEMM through the output layer (few output
+        # tiles, K = n_out): about two CTAs per SM
+        tiles = (B // 128) * (self.width // 128)
+        self.splits_out = max(1, min(self.n_out // 32, (2 * 152) // max(1, tiles)))
+        self.work = torch.empty(self.splits_out * B * self.width if self.splits_out > 1 else 1,
+                                dtype=torch.float32, device=d)
         self.loss_buf = torch.empty(1, dtype=torch.float32, device=d)
 
     # -- forward / backward / update ------------------------------------------
@@ -116,7 +122,8 @@ class MLP:
         rsi.nn_gemm("f32", self.dyT, self.HT[L], out_f32=self.gW[L])
         rsi.nn_colsum(self.dy, self.gb[L])
         rsi.nn_transpose(self.W16[L], self.WT[L])
-        rsi.nn_gemm("dsilu", self.dy, self.WT[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1])
+        rsi.nn_gemm("dsilu", self.dy, self.WT[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1],
+                    splits=self.splits_out, workspace=self.work)
         for l in range(L - 1, -1, -1):
             rsi.nn_transpose(self.dZ[l], self.dZT[l])
             rsi.nn_transpose(self.H[l], self.HT[l])

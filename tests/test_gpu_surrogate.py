@@ -51,6 +51,13 @@ def test_gemm_epilogues_match_fp32_reference(M, N, K):
     rsi.nn_gemm("dsilu", A, B, out_bf16=h, aux=aux)
     s = torch.sigmoid(aux)
     assert rel(h.float(), ref * s * (1 + aux * (1 - s))) < 6e-3
+    # split K: the same results through partial sums
+    splits = K // 32
+    work = torch.empty(splits * M * N, device="cuda")
+    rsi.nn_gemm("f32", A, B, out_f32=out, bias=bias, splits=splits, workspace=work)
+    assert rel(out, ref + bias) < 1e-5
+    rsi.nn_gemm("dsilu", A, B, out_bf16=h, aux=aux, splits=splits, workspace=work)
+    assert rel(h.float(), ref * s * (1 + aux * (1 - s))) < 6e-3
 
 
 def test_transpose_colsum_cast():
