@@ -156,6 +156,24 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # throughput probes -> ALU roofline
 # ---------------------------------------------------------------------------
+def recorded_traffic():
+    """DRAM bytes per RSI-stage launch from the committed ncu summary, if the
+    kernel source is still the one the counters were taken on; else None."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "traffic_stage_fp32_rsi_c2.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"stage_fp32_kernel_rsi_dram_bytes_per_launch (\d+) source_sha256_16 (\w+)",
+                  open(path).read())
+    if not m:
+        return None
+    h = hashlib.sha256()
+    for f in ("stage_fp32_body.cuh", "stage_fp32.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2408_06765_gb300", "csrc", f), "rb").read())
+    return int(m.group(1)) if h.hexdigest()[:16] == m.group(2) else None
+
+
 def measure_unit_rates(rsi, torch):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     blocks, iters = sms * 8, 65536
@@ -342,12 +360,8 @@ def run_ours(args):
                 "note": "FP64 path (sqrt, division and sincos in double on the FP64 pipe); "
                         "no FP64 roofline is modelled",
                 "avg_launch_ms": avg_s * 1e3, "launches": rsi_n}
-    traffic_file = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_file):
-        try:
-            roof["traffic"] = json.load(open(traffic_file)).get("stage_fp32_kernel_rsi_bytes_per_launch")
-        except (OSError, ValueError):
-            pass
+    if cfgs[0]["precision"] != "fp64" and args.config == "c2":
+        roof["traffic"] = recorded_traffic()
 
     e2e = None
     if not args.no_e2e:
