@@ -123,7 +123,7 @@ __global__ void batch_prep_kernel(const BPrep* __restrict__ preps, const BPrepTi
 }
 
 template <int KIND, int NORM, int TPT, int VAR>
-__global__ void __launch_bounds__(kThreads, TPT == 2 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, TPT == 2 ? RSI_FP32_MIN_BLOCKS : 2)
     batch_stage_kernel(const BStageInst* __restrict__ insts, const BItem* __restrict__ items, int64_t n_items,
                        TwoPiSplit tp, size_t max_tile_bytes, unsigned long long* counter, int* status) {
     extern __shared__ __align__(128) uint8_t smem[];

@@ -25,9 +25,18 @@
 
 #include "stage.cuh"
 
+// Build-time tuning knobs (the defaults are the measured best).
+#ifndef RSI_FP32_MIN_BLOCKS
+#define RSI_FP32_MIN_BLOCKS 3  // resident CTAs per SM asked of the compiler at 2 targets/thread
+#endif
+#ifndef RSI_FP32_UNROLL
+#define RSI_FP32_UNROLL 2  // unrolling of the loop over a tile's sources
+#endif
+
 namespace rsi_fp32 {
 
 constexpr int kThreads = 256;
+constexpr int kUnroll = RSI_FP32_UNROLL;
 
 struct TgtRef {
     float Dx, Dy, Dz, mx, my, mz, R, R2, tau;
@@ -223,7 +232,7 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
             ai[q] = 0.0f;
         }
         if (__all_sync(0xffffffffu, far_lane)) {
-#pragma unroll 2
+#pragma unroll kUnroll
             for (int i = 0; i < w.S; ++i) {
                 const float4 ra = rec[i * rec_f4];
                 const float4 rb = rec[i * rec_f4 + 1];
@@ -232,7 +241,7 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
                 for (int q = 0; q < TPT; ++q) pair_far<KIND, NORM, VAR>(ref[q], ra, rb, rn, k, ar[q], ai[q]);
             }
         } else {
-#pragma unroll 2
+#pragma unroll kUnroll
             for (int i = 0; i < w.S; ++i) {
                 const float4 ra = rec[i * rec_f4];
                 const float4 rb = rec[i * rec_f4 + 1];
