@@ -292,14 +292,19 @@ enum rsi_nn_epilogue {
  * u = 2 (p - lo)/(hi - lo) - 1; p: f32 batch x n_in, B: f32 F x n_in.     */
 int rsi_nn_features(const float *params, const float *lo, const float *hi, const float *fmat,
                     int32_t batch, int32_t n_in, int32_t n_freq, void *out_bf16, void *stream);
+enum rsi_nn_engine {
+    RSI_NN_ENGINE_MMA_SYNC = 0, /* warp-level mma.sync m16n8k16 (K % 32 == 0)          */
+    RSI_NN_ENGINE_TCGEN05 = 1   /* tcgen05.mma 128x128x16, accumulators in tensor memory
+                                   (K % 64 == 0)                                      */
+};
 /* C[M x N] = A[M x K] B[N x K]^T on BF16 tensor cores with FP32 accumulation
- * and the chosen epilogue.  M, N multiples of 128, K a multiple of 32;
- * A, B 16-byte aligned.  bias: f32 [N] or NULL (F32 epilogue).  splits > 1
- * splits K across CTAs (for few output tiles and long K): partial sums go to
- * workspace (f32 [splits][M][N], caller-allocated) and a second kernel adds
- * them in split order and applies the epilogue.                            */
-int rsi_nn_gemm(int32_t epilogue, const void *A, const void *B, int32_t M, int32_t N, int32_t K,
-                const float *bias, const float *aux, float *out_f32, void *out_bf16,
+ * and the chosen epilogue.  M, N multiples of 128; A, B 16-byte aligned.
+ * bias: f32 [N] or NULL (F32 epilogue).  splits > 1 splits K across CTAs
+ * (for few output tiles and long K): partial sums go to workspace
+ * (f32 [splits][M][N], caller-allocated) and a second kernel adds them in
+ * split order and applies the epilogue.                                    */
+int rsi_nn_gemm(int32_t epilogue, int32_t engine, const void *A, const void *B, int32_t M, int32_t N,
+                int32_t K, const float *bias, const float *aux, float *out_f32, void *out_bf16,
                 int32_t splits, float *workspace, void *stream);
 /* out[c][r] = in[r][c] for a bf16 rows x cols matrix.                      */
 int rsi_nn_transpose(const void *in_bf16, int32_t rows, int32_t cols, void *out_bf16, void *stream);

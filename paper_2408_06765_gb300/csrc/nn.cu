@@ -4,9 +4,12 @@
 // RSI chain, trained on fields the RSI kernels compute.
 //
 //   features   u = 2 (p - lo)/(hi - lo) - 1, h0 = [sin(pi B u), cos(pi B u)]  (bf16)
-//   gemm_tn    C[M x N] = A[M x K] B[N x K]^T on BF16 tensor cores (mma.sync
-//              m16n8k16, FP32 accumulation), ldmatrix fragments, a 3-stage
-//              cp.async pipeline, and fused epilogues:
+//   gemm       C[M x N] = A[M x K] B[N x K]^T on BF16 tensor cores with FP32
+//              accumulation, two engines: tcgen05 (TMA-fed, 128-byte
+//              swizzled stages, UMMA 128 x 256 x 16 into tensor memory, a
+//              producer lane and an MMA lane on mbarriers) and mma.sync
+//              (m16n8k16 fragments via ldmatrix, 3-stage cp.async pipeline);
+//              both with split K and the fused epilogues:
 //                F32        C (+ bias)                       -> f32
 //                BIAS_SILU  z = C + bias -> f32 z, bf16 silu(z)
 //                DSILU      C * silu'(aux)                   -> bf16   (backprop)
@@ -15,10 +18,12 @@
 //   colsum     bias gradients (column sums of a bf16 matrix)
 //   adam       Kingma & Ba (2015) on FP32 master weights, bf16 copy out
 //   carrier    multiply an image by exp(+-i psi), psi = kx x + kz z + phi0
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
 
 #include "rsi_internal.cuh"
+#include "umma.cuh"
 
 namespace {
 
@@ -183,6 +188,132 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits,
     epilogue2<EPI>(v0, v1, o, int(o % size_t(N)), bias, aux, outf, outh);
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 engine.  One CTA computes a TBM x TBN tile of C, accumulating in
+// tensor memory (TBN f32 columns).  K advances in tiles of 64 (128 bytes of
+// bf16, one 128-byte swizzle row) through a ring of TC_STAGES shared-memory
+// stages: warp 0 (one lane) loads A and B tiles with TMA, completing on the
+// stage's `full` barrier; warp 1 (one lane) waits for it, issues the four
+// 128 x TBN x 16 MMAs and commits them to the stage's `empty` barrier, which
+// frees the stage for the producer.  After the last k-tile all four warps
+// read their 32 accumulator lanes with tcgen05.ld and apply the epilogue.
+// Every wait is bounded; on a timeout the CTA drains its copies and MMAs,
+// frees tensor memory and records RSI_DEV_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 128;
+constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
+
+template <int TBN>
+struct TcCfg {
+    static constexpr uint32_t B_BYTES = TBN * TC_BK * 2;
+    static constexpr uint32_t STAGE = TC_A_BYTES + B_BYTES;
+    static constexpr size_t SMEM = size_t(TC_STAGES) * STAGE + 1024;  // + alignment slack
+    static constexpr uint32_t IDESC = rsi_umma::idesc_bf16_f32(TC_BM, TBN);
+};
+
+template <int EPI, int TBN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                   int K, const float* __restrict__ bias, const float* __restrict__ aux, float* __restrict__ outf,
+                   bf16* __restrict__ outh, int kts, int* status) {
+    using C = TcCfg<TBN>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bm = blockIdx.y * TC_BM, bn = blockIdx.x * TBN;
+    const int kt0 = blockIdx.z * kts;
+    const int KT = min(K / TC_BK - kt0, kts);
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;  // swizzle atoms need 1024-B alignment
+
+    if (warp == 0) {
+        rsi_umma::tmem_alloc(smem_u32(&tmem_slot), TBN);
+        rsi_umma::tmem_relinquish();
+    }
+    if (tid == 32) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(&done), 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (tid == 64) {
+        rsi_umma::prefetch_tmap(&tmA);
+        rsi_umma::prefetch_tmap(&tmB);
+    }
+    rsi_umma::fence_before_sync();
+    __syncthreads();
+    rsi_umma::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {  // producer
+        int issued = 0;
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % TC_STAGES;
+            if (abort_flag) break;
+            if (kt >= TC_STAGES && !mbar_wait_bounded(smem_u32(&empty[s]), uint32_t(kt / TC_STAGES - 1) & 1u)) {
+                abort_flag = 1;
+                break;
+            }
+            const uint32_t sa = base + uint32_t(s) * C::STAGE, sb = sa + TC_A_BYTES;
+            mbar_expect_tx(smem_u32(&full[s]), C::STAGE);
+            const int k0 = (kt0 + kt) * TC_BK;
+            rsi_umma::tma_load_2d(sa, &tmA, k0, bm, smem_u32(&full[s]));
+            rsi_umma::tma_load_2d(sb, &tmB, k0, bn, smem_u32(&full[s]));
+            issued = kt + 1;
+        }
+        // the copies still in flight land before the CTA can exit
+        for (int kt = max(0, issued - TC_STAGES); kt < issued; ++kt)
+            if (!mbar_wait_bounded(smem_u32(&full[kt % TC_STAGES]), uint32_t(kt / TC_STAGES) & 1u)) abort_flag = 1;
+    } else if (warp == 1 && lane == 0) {  // MMA issuer
+        for (int kt = 0; kt < KT; ++kt) {
+            const int s = kt % TC_STAGES;
+            if (abort_flag) break;
+            if (!mbar_wait_bounded(smem_u32(&full[s]), uint32_t(kt / TC_STAGES) & 1u)) {
+                abort_flag = 1;
+                break;
+            }
+            rsi_umma::fence_after_sync();
+            const uint32_t sa = base + uint32_t(s) * C::STAGE, sb = sa + TC_A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                rsi_umma::mma_f16(tmem, rsi_umma::smem_desc_sw128(sa + kk * 32), rsi_umma::smem_desc_sw128(sb + kk * 32),
+                                  C::IDESC, (kt | kk) != 0);
+            rsi_umma::commit(smem_u32(&empty[s]));
+        }
+        rsi_umma::commit(smem_u32(&done));  // arrives when every MMA issued above has completed
+    }
+    __syncwarp();
+    bool failed = !mbar_wait_bounded(smem_u32(&done), 0);
+    failed = __syncthreads_or(failed || abort_flag);
+    if (!failed) {
+        rsi_umma::fence_after_sync();
+        const int row = bm + warp * 32 + lane;
+#pragma unroll 1
+        for (int cb = 0; cb < TBN; cb += 32) {
+            float v[32];
+            rsi_umma::ld_32x32b_x32(tmem + (uint32_t(warp * 32) << 16) + uint32_t(cb), v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                const int col = bn + cb + j;
+                const size_t o = size_t(row) * N + col;
+                if (gridDim.z > 1)
+                    *reinterpret_cast<float2*>(outf + size_t(blockIdx.z) * M * N + o) = make_float2(v[j], v[j + 1]);
+                else
+                    epilogue2<EPI>(v[j], v[j + 1], o, col, bias, aux, outf, outh);
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(status, RSI_DEV_TIMEOUT);
+    }
+    rsi_umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) rsi_umma::tmem_dealloc(tmem, TBN);
+}
+
 __global__ void features_kernel(const float* __restrict__ p, const float* __restrict__ lo,
                                 const float* __restrict__ hi, const float* __restrict__ Bm, int batch, int n_in,
                                 int F, bf16* __restrict__ out) {
@@ -291,6 +422,80 @@ __global__ void carrier_kernel(const double* __restrict__ carrier, int batch, in
     out[q] = make_float2(float(v.x * c - v.y * s), float(v.x * s + v.y * c));
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// tensor map of a row-major bf16 matrix [rows x K]: boxes of 64 x box_rows,
+// 128-byte swizzle, zero fill outside the matrix
+int make_tmap(CUtensorMap* tm, const bf16* ptr, int rows, int K, int box_rows) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return rsi_fail(RSI_E_CUDA, "rsi_nn_gemm: cuTensorMapEncodeTiled is not available");
+    const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(K) * sizeof(bf16)};
+    const cuuint32_t box[2] = {cuuint32_t(TC_BK), cuuint32_t(box_rows)};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return rsi_fail(RSI_E_CUDA, "rsi_nn_gemm: cuTensorMapEncodeTiled failed (%d)", int(r));
+    return RSI_OK;
+}
+
+template <int EPI, int TBN>
+int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const float* aux,
+                      float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
+    using C = TcCfg<TBN>;
+    static bool attr = false;
+    if (!attr) {
+        RSI_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<EPI, TBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          int(C::SMEM)),
+                     "cudaFuncSetAttribute(gemm_tc)");
+        attr = true;
+    }
+    int* status = rsi_status_ptr();
+    if (!status) return RSI_E_CUDA;
+    CUtensorMap ta, tb;
+    int rc = make_tmap(&ta, A, M, K, TC_BM);
+    if (rc) return rc;
+    rc = make_tmap(&tb, B, N, K, TBN);
+    if (rc) return rc;
+    const int kt = K / TC_BK;
+    const int kts = (kt + splits - 1) / splits;
+    splits = (kt + kts - 1) / kts;
+    dim3 grid(N / TBN, M / TC_BM, splits);
+    gemm_tc_kernel<EPI, TBN><<<grid, TC_THREADS, C::SMEM, s>>>(ta, tb, M, N, K, bias, aux, splits > 1 ? work : outf,
+                                                               outh, kts, status);
+    RSI_CHECK_LAUNCH("gemm_tc_kernel");
+    if (splits > 1) {
+        int64_t pairs = int64_t(M) * N / 2;
+        splitk_reduce_kernel<EPI><<<unsigned((pairs + 255) / 256), 256, 0, s>>>(work, splits, M, N, bias, aux,
+                                                                                 outf, outh);
+        RSI_CHECK_LAUNCH("splitk_reduce_kernel");
+    }
+    return RSI_OK;
+}
+
+template <int EPI>
+int gemm_tc_launch(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const float* aux,
+                   float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
+    if (N % 256 == 0) return gemm_tc_launch_bn<EPI, 256>(A, B, M, N, K, bias, aux, outf, outh, splits, work, s);
+    return gemm_tc_launch_bn<EPI, 128>(A, B, M, N, K, bias, aux, outf, outh, splits, work, s);
+}
+
 template <int EPI>
 int gemm_launch(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const float* aux, float* outf,
                 bf16* outh, int splits, float* work, cudaStream_t s) {
@@ -332,10 +537,14 @@ extern "C" int rsi_nn_features(const float* params, const float* lo, const float
     return RSI_OK;
 }
 
-extern "C" int rsi_nn_gemm(int32_t epilogue, const void* A, const void* B, int32_t M, int32_t N, int32_t K,
-                           const float* bias, const float* aux, float* out_f32, void* out_bf16, int32_t splits,
-                           float* workspace, void* stream) {
+extern "C" int rsi_nn_gemm(int32_t epilogue, int32_t engine, const void* A, const void* B, int32_t M, int32_t N,
+                           int32_t K, const float* bias, const float* aux, float* out_f32, void* out_bf16,
+                           int32_t splits, float* workspace, void* stream) {
     if (!A || !B || M < 1 || N < 1 || K < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: bad arguments");
+    if (engine != RSI_NN_ENGINE_MMA_SYNC && engine != RSI_NN_ENGINE_TCGEN05)
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: unknown engine %d", engine);
+    if (engine == RSI_NN_ENGINE_TCGEN05 && K % TC_BK)
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: the tcgen05 engine needs K % 64 == 0 (got %d)", K);
     if (splits < 1 || splits > K / BK || (splits > 1 && !workspace))
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: splits must be in [1, K/32] and need a workspace");
     if (misaligned(workspace, 8)) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: misaligned workspace");
@@ -349,16 +558,20 @@ extern "C" int rsi_nn_gemm(int32_t epilogue, const void* A, const void* B, int32
     const bf16* a = static_cast<const bf16*>(A);
     const bf16* b = static_cast<const bf16*>(B);
     bf16* oh = static_cast<bf16*>(out_bf16);
+    const bool tc = engine == RSI_NN_ENGINE_TCGEN05;
     switch (epilogue) {
         case RSI_NN_EPI_F32:
             if (!out_f32) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: F32 epilogue needs out_f32");
-            return gemm_launch<0>(a, b, M, N, K, bias, nullptr, out_f32, nullptr, splits, workspace, s);
+            return tc ? gemm_tc_launch<0>(a, b, M, N, K, bias, nullptr, out_f32, nullptr, splits, workspace, s)
+                      : gemm_launch<0>(a, b, M, N, K, bias, nullptr, out_f32, nullptr, splits, workspace, s);
         case RSI_NN_EPI_BIAS_SILU:
             if (!out_f32 || !oh || !bias) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: BIAS_SILU needs bias and outputs");
-            return gemm_launch<1>(a, b, M, N, K, bias, nullptr, out_f32, oh, splits, workspace, s);
+            return tc ? gemm_tc_launch<1>(a, b, M, N, K, bias, nullptr, out_f32, oh, splits, workspace, s)
+                      : gemm_launch<1>(a, b, M, N, K, bias, nullptr, out_f32, oh, splits, workspace, s);
         case RSI_NN_EPI_DSILU:
             if (!aux || !oh) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: DSILU needs aux and out_bf16");
-            return gemm_launch<2>(a, b, M, N, K, nullptr, aux, nullptr, oh, splits, workspace, s);
+            return tc ? gemm_tc_launch<2>(a, b, M, N, K, nullptr, aux, nullptr, oh, splits, workspace, s)
+                      : gemm_launch<2>(a, b, M, N, K, nullptr, aux, nullptr, oh, splits, workspace, s);
         default:
             return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: unknown epilogue %d", epilogue);
     }

@@ -42,6 +42,7 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier",
            "rsi_selftest_wait_timeout"]
 NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
+NN_ENGINE = {"mma_sync": 0, "tcgen05": 1}
 UB = {"ffma": 0, "rsqrt": 1, "sin": 2}
 
 
@@ -124,7 +125,7 @@ def load(path: str | None = None):
         L.rsi_batch_destroy.argtypes = [vp]
         f32, f64 = ctypes.c_float, ctypes.c_double
         L.rsi_nn_features.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp]
-        L.rsi_nn_gemm.argtypes = [i32, vp, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp]
+        L.rsi_nn_gemm.argtypes = [i32, i32, vp, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp]
         L.rsi_nn_transpose.argtypes = [vp, i32, i32, vp, vp]
         L.rsi_nn_loss.argtypes = [vp, vp, i64, f32, vp, vp, i32, vp, vp]
         L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
@@ -466,15 +467,15 @@ def nn_features(p, lo, hi, fmat, out, stream=None):
 
 
 def nn_gemm(epi: str, A, B, out_f32=None, out_bf16=None, bias=None, aux=None, splits: int = 1,
-            workspace=None, stream=None):
+            workspace=None, engine: str = "mma_sync", stream=None):
     """C[M x N] = A[M x K] B[N x K]^T with an epilogue (see rsi_nn_gemm)."""
     M, K = A.shape
     N = B.shape[0]
     assert B.shape[1] == K
     if splits > 1:
         assert workspace is not None and workspace.numel() >= splits * M * N
-    _check(load().rsi_nn_gemm(NN_EPI[epi], _ptr(A), _ptr(B), M, N, K, _ptr(bias), _ptr(aux),
-                              _ptr(out_f32), _ptr(out_bf16), int(splits), _ptr(workspace),
+    _check(load().rsi_nn_gemm(NN_EPI[epi], NN_ENGINE[engine], _ptr(A), _ptr(B), M, N, K, _ptr(bias),
+                              _ptr(aux), _ptr(out_f32), _ptr(out_bf16), int(splits), _ptr(workspace),
                               _stream(stream)), "rsi_nn_gemm")
 
 

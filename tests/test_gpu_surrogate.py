@@ -60,6 +60,40 @@ def test_gemm_epilogues_match_fp32_reference(M, N, K):
     assert rel(h.float(), ref * s * (1 + aux * (1 - s))) < 6e-3
 
 
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 512, 256), (384, 256, 128), (256, 384, 1024)])
+def test_gemm_tcgen05_matches_fp32_reference(M, N, K):
+    """The tcgen05 engine (accumulators in tensor memory) against the same
+    FP32 reference, every epilogue, with and without split K."""
+    g = torch.Generator(device="cuda").manual_seed(7 * M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    aux = torch.randn(M, N, device="cuda", generator=g)
+    ref = A.float() @ B.float().T
+    s = torch.sigmoid(aux)
+    out = torch.empty(M, N, device="cuda")
+    h = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    for splits in (1, K // 64):
+        work = torch.empty(splits * M * N, device="cuda") if splits > 1 else None
+        kw = dict(splits=splits, workspace=work, engine="tcgen05")
+        out.fill_(float("nan"))
+        rsi.nn_gemm("f32", A, B, out_f32=out, **kw)
+        assert rel(out, ref) < 1e-5, splits
+        rsi.nn_gemm("f32", A, B, out_f32=out, bias=bias, **kw)
+        assert rel(out, ref + bias) < 1e-5, splits
+        rsi.nn_gemm("bias_silu", A, B, out_f32=out, out_bf16=h, bias=bias, **kw)
+        assert rel(out, ref + bias) < 1e-5, splits
+        assert rel(h.float(), torch.nn.functional.silu(ref + bias)) < 6e-3, splits
+        rsi.nn_gemm("dsilu", A, B, out_bf16=h, aux=aux, **kw)
+        assert rel(h.float(), ref * s * (1 + aux * (1 - s))) < 6e-3, splits
+    # both engines sum the same products in FP32: results agree closely
+    o2 = torch.empty_like(out)
+    rsi.nn_gemm("f32", A, B, out_f32=out, engine="tcgen05")
+    rsi.nn_gemm("f32", A, B, out_f32=o2, engine="mma_sync")
+    assert rel(out, o2) < 1e-6
+    rsi.sync_status()  # raises if a kernel recorded a timeout
+
+
 def test_transpose_colsum_cast():
     x = torch.randn(300, 70, device="cuda").to(torch.bfloat16)
     t = torch.empty(70, 300, dtype=torch.bfloat16, device="cuda")
