@@ -18,6 +18,7 @@
 //   colsum     bias gradients (column sums of a bf16 matrix)
 //   adam       Kingma & Ba (2015) on FP32 master weights, bf16 copy out
 //   carrier    multiply an image by exp(+-i psi), psi = kx x + kz z + phi0
+#include <algorithm>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
@@ -188,53 +189,113 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits,
     epilogue2<EPI>(v0, v1, o, int(o % size_t(N)), bias, aux, outf, outh);
 }
 
+// epilogue of four neighbouring outputs (row, col .. col + 3); o, col % 4 == 0
+template <int EPI>
+__device__ __forceinline__ void epilogue4(float4 v, size_t o, int col, const float* __restrict__ bias,
+                                          const float* __restrict__ aux, float* __restrict__ outf,
+                                          bf16* __restrict__ outh) {
+    if (EPI != 2 && bias) {
+        const float4 b = *reinterpret_cast<const float4*>(bias + col);
+        v.x += b.x;
+        v.y += b.y;
+        v.z += b.z;
+        v.w += b.w;
+    }
+    if (EPI != 2) *reinterpret_cast<float4*>(outf + o) = v;
+    if (EPI == 1) {
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(silu_(v.x), silu_(v.y));
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(silu_(v.z), silu_(v.w));
+        uint2 u = make_uint2(*reinterpret_cast<uint32_t*>(&h0), *reinterpret_cast<uint32_t*>(&h1));
+        *reinterpret_cast<uint2*>(outh + o) = u;
+    } else if (EPI == 2) {
+        const float4 z = *reinterpret_cast<const float4*>(aux + o);
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x * dsilu_(z.x), v.y * dsilu_(z.y));
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(v.z * dsilu_(z.z), v.w * dsilu_(z.w));
+        uint2 u = make_uint2(*reinterpret_cast<uint32_t*>(&h0), *reinterpret_cast<uint32_t*>(&h1));
+        *reinterpret_cast<uint2*>(outh + o) = u;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// tcgen05 engine.  One CTA computes a TBM x TBN tile of C, accumulating in
-// tensor memory (TBN f32 columns).  K advances in tiles of 64 (128 bytes of
-// bf16, one 128-byte swizzle row) through a ring of TC_STAGES shared-memory
-// stages: warp 0 (one lane) loads A and B tiles with TMA, completing on the
-// stage's `full` barrier; warp 1 (one lane) waits for it, issues the four
-// 128 x TBN x 16 MMAs and commits them to the stage's `empty` barrier, which
-// frees the stage for the producer.  After the last k-tile all four warps
-// read their 32 accumulator lanes with tcgen05.ld and apply the epilogue.
-// Every wait is bounded; on a timeout the CTA drains its copies and MMAs,
-// frees tensor memory and records RSI_DEV_TIMEOUT.
+// tcgen05 engine: a persistent kernel, one CTA per SM, looping over output
+// tiles of 128 x TBN (and, with split K, over K ranges).  Warp roles:
+//   warp 0, one lane   TMA producer: A and B k-tiles (64 wide, 128 bytes of
+//                      bf16 = one 128-byte swizzle row) into a ring of
+//                      TC_STAGES shared-memory stages, completing on the
+//                      stage's `full` barrier
+//   warp 1, one lane   MMA issuer: waits for `full`, issues four
+//                      128 x TBN x 16 tcgen05.mma into one of two tensor-
+//                      memory accumulators, commits them to the stage's
+//                      `empty` barrier (frees the stage) and, after a tile's
+//                      last k-tile, to the accumulator's `acc_full` barrier
+//   warps 2-5          epilogue: tcgen05.ld of their 32 accumulator lanes,
+//                      through shared memory into row-contiguous stores with
+//                      the fused epilogue, then `acc_empty` frees the
+//                      accumulator; so the epilogue of one tile overlaps the
+//                      main loop of the next.
+// Every wait is bounded; on a timeout all roles stop, the CTA drains its
+// copies and MMAs, frees tensor memory and records RSI_DEV_TIMEOUT.
 // ---------------------------------------------------------------------------
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 128;
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 192;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
+constexpr int TC_EPI_LD = 36;  // floats per row of an epilogue staging buffer (conflict-free float4)
+constexpr uint32_t TC_EPI_BYTES = 4 * 32 * TC_EPI_LD * 4;
 
 template <int TBN>
 struct TcCfg {
     static constexpr uint32_t B_BYTES = TBN * TC_BK * 2;
     static constexpr uint32_t STAGE = TC_A_BYTES + B_BYTES;
-    static constexpr size_t SMEM = size_t(TC_STAGES) * STAGE + 1024;  // + alignment slack
+    static constexpr size_t SMEM = size_t(TC_STAGES) * STAGE + TC_EPI_BYTES + 1024;  // + alignment slack
     static constexpr uint32_t IDESC = rsi_umma::idesc_bf16_f32(TC_BM, TBN);
 };
+
+struct TcTile {
+    int m0, n0, kt0, KT, z;
+};
+// tile t -> (m, n, split): groups of up to 16 row blocks sweep N together so
+// that CTAs running at the same time share A and B tiles in L2
+__device__ __forceinline__ TcTile tc_tile(int t, int m_tiles, int n_tiles, int TBN, int kt_total, int kts) {
+    const int mn = m_tiles * n_tiles;
+    const int z = t / mn, r = t - z * mn;
+    const int G = 16, g = r / (G * n_tiles), w = r - g * G * n_tiles;
+    const int gm = min(G, m_tiles - g * G);
+    TcTile T;
+    T.m0 = (g * G + w % gm) * TC_BM;
+    T.n0 = (w / gm) * TBN;
+    T.z = z;
+    T.kt0 = z * kts;
+    T.KT = min(kt_total - T.kt0, kts);
+    return T;
+}
 
 template <int EPI, int TBN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, const float* __restrict__ bias, const float* __restrict__ aux, float* __restrict__ outf,
-                   bf16* __restrict__ outh, int kts, int* status) {
+                   bf16* __restrict__ outh, int kts, int splits, int* status) {
     using C = TcCfg<TBN>;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], done;
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2], done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bm = blockIdx.y * TC_BM, bn = blockIdx.x * TBN;
-    const int kt0 = blockIdx.z * kts;
-    const int KT = min(K / TC_BK - kt0, kts);
+    const int m_tiles = M / TC_BM, n_tiles = N / TBN, kt_total = K / TC_BK;
+    const int total = m_tiles * n_tiles * splits;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;  // swizzle atoms need 1024-B alignment
+    float* epi_buf = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) + TC_STAGES * C::STAGE);
 
     if (warp == 0) {
-        rsi_umma::tmem_alloc(smem_u32(&tmem_slot), TBN);
+        rsi_umma::tmem_alloc(smem_u32(&tmem_slot), 2 * TBN);
         rsi_umma::tmem_relinquish();
     }
     if (tid == 32) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&acc_full[a]), 1);
+            mbar_init(smem_u32(&acc_empty[a]), 4);  // one arrival per epilogue warp
         }
         mbar_init(smem_u32(&done), 1);
         abort_flag = 0;
@@ -249,69 +310,113 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     rsi_umma::fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0) {  // producer
-        int issued = 0;
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % TC_STAGES;
-            if (abort_flag) break;
-            if (kt >= TC_STAGES && !mbar_wait_bounded(smem_u32(&empty[s]), uint32_t(kt / TC_STAGES - 1) & 1u)) {
-                abort_flag = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int it = 0;
+            for (int t = blockIdx.x; t < total && !abort_flag; t += gridDim.x) {
+                const TcTile T = tc_tile(t, m_tiles, n_tiles, TBN, kt_total, kts);
+                for (int kt = 0; kt < T.KT; ++kt, ++it) {
+                    const int s = it % TC_STAGES;
+                    if (it >= TC_STAGES &&
+                        !mbar_wait_bounded(smem_u32(&empty[s]), uint32_t(it / TC_STAGES - 1) & 1u)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const uint32_t sa = base + uint32_t(s) * C::STAGE;
+                    mbar_expect_tx(smem_u32(&full[s]), C::STAGE);
+                    const int k0 = (T.kt0 + kt) * TC_BK;
+                    rsi_umma::tma_load_2d(sa, &tmA, k0, T.m0, smem_u32(&full[s]));
+                    rsi_umma::tma_load_2d(sa + TC_A_BYTES, &tmB, k0, T.n0, smem_u32(&full[s]));
+                }
             }
-            const uint32_t sa = base + uint32_t(s) * C::STAGE, sb = sa + TC_A_BYTES;
-            mbar_expect_tx(smem_u32(&full[s]), C::STAGE);
-            const int k0 = (kt0 + kt) * TC_BK;
-            rsi_umma::tma_load_2d(sa, &tmA, k0, bm, smem_u32(&full[s]));
-            rsi_umma::tma_load_2d(sb, &tmB, k0, bn, smem_u32(&full[s]));
-            issued = kt + 1;
+            // the copies still in flight land before the CTA can exit
+            for (int j = max(0, it - TC_STAGES); j < it; ++j)
+                if (!mbar_wait_bounded(smem_u32(&full[j % TC_STAGES]), uint32_t(j / TC_STAGES) & 1u))
+                    abort_flag = 1;
         }
-        // the copies still in flight land before the CTA can exit
-        for (int kt = max(0, issued - TC_STAGES); kt < issued; ++kt)
-            if (!mbar_wait_bounded(smem_u32(&full[kt % TC_STAGES]), uint32_t(kt / TC_STAGES) & 1u)) abort_flag = 1;
-    } else if (warp == 1 && lane == 0) {  // MMA issuer
-        for (int kt = 0; kt < KT; ++kt) {
-            const int s = kt % TC_STAGES;
-            if (abort_flag) break;
-            if (!mbar_wait_bounded(smem_u32(&full[s]), uint32_t(kt / TC_STAGES) & 1u)) {
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int it = 0, tc = 0;
+            for (int t = blockIdx.x; t < total && !abort_flag; t += gridDim.x, ++tc) {
+                const TcTile T = tc_tile(t, m_tiles, n_tiles, TBN, kt_total, kts);
+                const int acc = tc & 1;
+                if (tc >= 2 && !mbar_wait_bounded(smem_u32(&acc_empty[acc]), uint32_t(tc / 2 - 1) & 1u)) {
+                    abort_flag = 1;
+                    break;
+                }
+                rsi_umma::fence_after_sync();
+                const uint32_t d = tmem + uint32_t(acc * TBN);
+                bool ok = true;
+                for (int kt = 0; kt < T.KT; ++kt, ++it) {
+                    const int s = it % TC_STAGES;
+                    if (!mbar_wait_bounded(smem_u32(&full[s]), uint32_t(it / TC_STAGES) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    rsi_umma::fence_after_sync();
+                    const uint32_t sa = base + uint32_t(s) * C::STAGE, sb = sa + TC_A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk)
+                        rsi_umma::mma_f16(d, rsi_umma::smem_desc_sw128(sa + kk * 32),
+                                          rsi_umma::smem_desc_sw128(sb + kk * 32), C::IDESC, (kt | kk) != 0);
+                    rsi_umma::commit(smem_u32(&empty[s]));
+                }
+                if (!ok) {
+                    abort_flag = 1;
+                    break;
+                }
+                rsi_umma::commit(smem_u32(&acc_full[acc]));
+            }
+            rsi_umma::commit(smem_u32(&done));  // arrives when every MMA issued above has completed
+        }
+    } else {  // epilogue warps 2..5: TMEM lane quarter q = warp % 4
+        const int q = warp & 3;
+        float* buf = epi_buf + q * 32 * TC_EPI_LD;
+        int tc = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
+            if (__any_sync(0xffffffffu, abort_flag)) break;  // warp-uniform: tcgen05.ld below is .sync.aligned
+            const TcTile T = tc_tile(t, m_tiles, n_tiles, TBN, kt_total, kts);
+            const int acc = tc & 1;
+            const bool ok = mbar_wait_bounded(smem_u32(&acc_full[acc]), uint32_t(tc / 2) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
                 abort_flag = 1;
                 break;
             }
             rsi_umma::fence_after_sync();
-            const uint32_t sa = base + uint32_t(s) * C::STAGE, sb = sa + TC_A_BYTES;
+            float* out = splits > 1 ? outf + size_t(T.z) * M * N : outf;
+#pragma unroll 1
+            for (int cb = 0; cb < TBN; cb += 32) {
+                float v[32];
+                rsi_umma::ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * TBN + cb), v);
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk)
-                rsi_umma::mma_f16(tmem, rsi_umma::smem_desc_sw128(sa + kk * 32), rsi_umma::smem_desc_sw128(sb + kk * 32),
-                                  C::IDESC, (kt | kk) != 0);
-            rsi_umma::commit(smem_u32(&empty[s]));
+                for (int i = 0; i < 8; ++i)
+                    *reinterpret_cast<float4*>(buf + lane * TC_EPI_LD + 4 * i) =
+                        make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + (lane >> 3), c4 = lane & 7;
+                    const float4 w = *reinterpret_cast<const float4*>(buf + rr * TC_EPI_LD + 4 * c4);
+                    const int col = T.n0 + cb + 4 * c4;
+                    const size_t o = size_t(T.m0 + q * 32 + rr) * N + col;
+                    if (splits > 1)
+                        *reinterpret_cast<float4*>(out + o) = w;
+                    else
+                        epilogue4<EPI>(w, o, col, bias, aux, outf, outh);
+                }
+                __syncwarp();
+            }
+            rsi_umma::fence_before_sync();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
         }
-        rsi_umma::commit(smem_u32(&done));  // arrives when every MMA issued above has completed
     }
     __syncwarp();
     bool failed = !mbar_wait_bounded(smem_u32(&done), 0);
     failed = __syncthreads_or(failed || abort_flag);
-    if (!failed) {
-        rsi_umma::fence_after_sync();
-        const int row = bm + warp * 32 + lane;
-#pragma unroll 1
-        for (int cb = 0; cb < TBN; cb += 32) {
-            float v[32];
-            rsi_umma::ld_32x32b_x32(tmem + (uint32_t(warp * 32) << 16) + uint32_t(cb), v);
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                const int col = bn + cb + j;
-                const size_t o = size_t(row) * N + col;
-                if (gridDim.z > 1)
-                    *reinterpret_cast<float2*>(outf + size_t(blockIdx.z) * M * N + o) = make_float2(v[j], v[j + 1]);
-                else
-                    epilogue2<EPI>(v[j], v[j + 1], o, col, bias, aux, outf, outh);
-            }
-        }
-    } else if (tid == 0) {
-        atomicExch(status, RSI_DEV_TIMEOUT);
-    }
+    if (failed && tid == 0) atomicExch(status, RSI_DEV_TIMEOUT);
     rsi_umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) rsi_umma::tmem_dealloc(tmem, TBN);
+    if (warp == 0) rsi_umma::tmem_dealloc(tmem, 2 * TBN);
 }
 
 __global__ void features_kernel(const float* __restrict__ p, const float* __restrict__ lo,
@@ -422,6 +527,16 @@ __global__ void carrier_kernel(const double* __restrict__ carrier, int batch, in
     out[q] = make_float2(float(v.x * c - v.y * s), float(v.x * s + v.y * c));
 }
 
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 1;
+    }
+    return n;
+}
+
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -476,9 +591,10 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, const f
     const int kt = K / TC_BK;
     const int kts = (kt + splits - 1) / splits;
     splits = (kt + kts - 1) / kts;
-    dim3 grid(N / TBN, M / TC_BM, splits);
+    const int tiles = (M / TC_BM) * (N / TBN) * splits;
+    const int grid = std::min(tiles, sm_count());
     gemm_tc_kernel<EPI, TBN><<<grid, TC_THREADS, C::SMEM, s>>>(ta, tb, M, N, K, bias, aux, splits > 1 ? work : outf,
-                                                               outh, kts, status);
+                                                               outh, kts, splits, status);
     RSI_CHECK_LAUNCH("gemm_tc_kernel");
     if (splits > 1) {
         int64_t pairs = int64_t(M) * N / 2;
@@ -545,6 +661,9 @@ extern "C" int rsi_nn_gemm(int32_t epilogue, int32_t engine, const void* A, cons
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: unknown engine %d", engine);
     if (engine == RSI_NN_ENGINE_TCGEN05 && K % TC_BK)
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: the tcgen05 engine needs K % 64 == 0 (got %d)", K);
+    if (engine == RSI_NN_ENGINE_TCGEN05 && (misaligned(out_f32, 16) || misaligned(aux, 16) || misaligned(bias, 16) ||
+                                            misaligned(out_bf16, 8) || misaligned(workspace, 16)))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: the tcgen05 engine needs 16-byte aligned f32 and 8-byte bf16 outputs");
     if (splits < 1 || splits > K / BK || (splits > 1 && !workspace))
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: splits must be in [1, K/32] and need a workspace");
     if (misaligned(workspace, 8)) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: misaligned workspace");
