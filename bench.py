@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--epochs", type=int, default=300, help="c5: training epochs")
     ap.add_argument("--sigma-b", type=float, default=0.25, help="c5: Fourier feature scale")
     ap.add_argument("--lr", type=float, default=1e-3, help="c5: peak learning rate")
+    ap.add_argument("--engine", choices=["tcgen05", "mma_sync"], default="tcgen05", help="c5: GEMM engine")
     ap.add_argument("--sweep", action="store_true",
                     help="with --case stage: time every tile / targets-per-thread / variant")
     return ap.parse_args()
@@ -568,6 +569,19 @@ def run_batch_c4(args):
     b.close()
 
 
+def measured_peaks():
+    """Copy bandwidth and bf16 GEMM throughput measured on this GPU model
+    (MEASURED_PEAKS.json beside this file), else the fallback figures."""
+    f = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(f) as fh:
+            d = json.load(fh)
+        d["source"] = "measured"
+        return d
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
 def run_surrogate_c5(args):
     """c5: generate fields with the batched RSI path, train the BF16 MLP,
     measure held-out error, inference rate against the RSI path, and the
@@ -589,7 +603,7 @@ def run_surrogate_c5(args):
         raise SystemExit("c5 needs more than 256 fields")
     tr, ho = slice(0, n - n_hold), slice(n - n_hold, n)
     scale = float(env[tr].pow(2).mean().sqrt())
-    net = surrogate.MLP(batch=256, sigma_b=args.sigma_b)
+    net = surrogate.MLP(batch=256, sigma_b=args.sigma_b, engine=args.engine)
     net.scale = scale
     t0 = time.perf_counter()
     losses = surrogate.train(net, params[tr], env[tr] / scale, epochs=args.epochs, lr=args.lr)
@@ -616,7 +630,7 @@ def run_surrogate_c5(args):
     tilt_deg = np.degrees(hp[:len(errs), 1])
     post = np.abs(tilt_deg) > np.degrees(np.arcsin(1480.0 / 5900.0))
     # inference throughput at batch 1024 vs the RSI path on the same fields
-    inf = surrogate.MLP(batch=1024)
+    inf = surrogate.MLP(batch=1024, engine=args.engine)
     for a, b_ in zip(inf.W16 + inf.b, net.W16 + net.b):
         a.copy_(b_)
     inf.fmat.copy_(net.fmat)
@@ -630,6 +644,32 @@ def run_surrogate_c5(args):
     e1.record()
     e1.synchronize()
     nn_fields_s = 10 * 1024 / (e0.elapsed_time(e1) * 1e-3)
+    # the dominant kernel: the output-layer GEMM of inference, [1024 x 512] x
+    # [512 x 32768] with FP32 output (128 MiB, larger than L2), timed alone
+    H, Wo = inf.H[inf.depth], inf.W16[-1]
+    gemm = lambda: rsi.nn_gemm("f32", H, Wo, out_f32=inf.y, bias=inf.b[-1], engine=args.engine)
+    for _ in range(3):
+        gemm()
+    e0.record()
+    for _ in range(20):
+        gemm()
+    e1.record()
+    e1.synchronize()
+    gemm_ms = e0.elapsed_time(e1) / 20
+    gemm_flops = 2.0 * H.shape[0] * Wo.shape[0] * H.shape[1]
+    peaks = measured_peaks()
+    tf = gemm_flops / (gemm_ms * 1e-3) / 1e12
+    # one training step (batch 256: forward, loss, backward, Adam)
+    p0 = torch.tensor(params[:256], dtype=torch.float32, device="cuda")
+    t0_ = (env[:256] / scale).contiguous()
+    for _ in range(3):
+        net.train_step(p0, t0_, 0.0)
+    e0.record()
+    for _ in range(20):
+        net.train_step(p0, t0_, 0.0)
+    e1.record()
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1) / 20
     rsi_fields_s = n / gen_s
     sur = surrogate.Surrogate(net, params[ho][:len(errs)], errs)
     est = sur.error_estimate(params[:1024])
@@ -648,6 +688,11 @@ def run_surrogate_c5(args):
             "held_out_median_post_critical": float(np.median(errs[post])) if post.any() else None,
             "reaches_1e-3": bool(np.median(errs) <= 1e-3),
             "surrogate_fields_per_s_batch1024": nn_fields_s,
+            "engine": args.engine, "train_step_ms_batch256": step_ms,
+            "roofline": {"kernel": "output-layer GEMM 1024 x 32768 x 512, f32 out", "bound": "tensor",
+                         "achieved": tf, "peak": peaks.get("bf16_tflops"), "unit": "TFLOP/s",
+                         "frac": tf / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
+                         "peak_source": peaks["source"] + " bf16 burst", "ms": gemm_ms},
             "speedup_vs_rsi": nn_fields_s / rsi_fields_s,
             "gate": {"threshold": 1e-2, "fallback_fraction": float(np.mean(est > 1e-2))},
             "gpu": torch.cuda.get_device_name(0)}

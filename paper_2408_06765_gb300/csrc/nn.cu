@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
+#include <string.h>
 
 #include "rsi_internal.cuh"
 #include "umma.cuh"
@@ -228,18 +229,23 @@ __device__ __forceinline__ void epilogue4(float4 v, size_t o, int col, const flo
 //                      memory accumulators, commits them to the stage's
 //                      `empty` barrier (frees the stage) and, after a tile's
 //                      last k-tile, to the accumulator's `acc_full` barrier
-//   warps 2-5          epilogue: tcgen05.ld of their 32 accumulator lanes,
-//                      through shared memory into row-contiguous stores with
-//                      the fused epilogue, then `acc_empty` frees the
-//                      accumulator; so the epilogue of one tile overlaps the
-//                      main loop of the next.
+//   warps 2-9          epilogue, two warps per 32-lane quarter of tensor
+//                      memory (each takes half the columns): tcgen05.ld of
+//                      32 x 32 blocks into registers, then `acc_empty` frees
+//                      the accumulator, so the epilogue of one tile overlaps
+//                      the main loop of the next.  F32 output (and split-K
+//                      partial sums) leave as TMA bulk stores of the block
+//                      staged in the 128-byte-swizzled layout; the other
+//                      epilogues go through shared memory into
+//                      row-contiguous stores.
 // Every wait is bounded; on a timeout all roles stop, the CTA drains its
 // copies and MMAs, frees tensor memory and records RSI_DEV_TIMEOUT.
 // ---------------------------------------------------------------------------
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 192;
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_EPI_WARPS = 8, TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
-constexpr int TC_EPI_LD = 36;  // floats per row of an epilogue staging buffer (conflict-free float4)
-constexpr uint32_t TC_EPI_BYTES = 4 * 32 * TC_EPI_LD * 4;
+// epilogue staging: per warp 32 rows x 32 floats, 16-byte chunk j of row r
+// stored at chunk j ^ (r & 7) (conflict-free row writes and column reads)
+constexpr uint32_t TC_EPI_BYTES = TC_EPI_WARPS * 32 * 32 * 4;
 
 template <int TBN>
 struct TcCfg {
@@ -270,9 +276,12 @@ __device__ __forceinline__ TcTile tc_tile(int t, int m_tiles, int n_tiles, int T
 
 template <int EPI, int TBN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                   int K, const float* __restrict__ bias, const float* __restrict__ aux, float* __restrict__ outf,
-                   bf16* __restrict__ outh, int kts, int splits, int* status) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, int M, int N, int K, const float* __restrict__ bias,
+                   const float* __restrict__ aux, float* __restrict__ outf, bf16* __restrict__ outh, int kts,
+                   int splits, int* status) {
+    // F32 output and split-K partials: TMA stores through tmC (f32 [splits*M x N])
+    const bool tma_store = EPI == 0 || splits > 1;
     using C = TcCfg<TBN>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2], done;
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&acc_full[a]), 1);
-            mbar_init(smem_u32(&acc_empty[a]), 4);  // one arrival per epilogue warp
+            mbar_init(smem_u32(&acc_empty[a]), TC_EPI_WARPS);  // one arrival per epilogue warp
         }
         mbar_init(smem_u32(&done), 1);
         abort_flag = 0;
@@ -304,6 +313,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (tid == 64) {
         rsi_umma::prefetch_tmap(&tmA);
         rsi_umma::prefetch_tmap(&tmB);
+        if (tma_store) rsi_umma::prefetch_tmap(&tmC);
     }
     rsi_umma::fence_before_sync();
     __syncthreads();
@@ -369,9 +379,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             rsi_umma::commit(smem_u32(&done));  // arrives when every MMA issued above has completed
         }
-    } else {  // epilogue warps 2..5: TMEM lane quarter q = warp % 4
-        const int q = warp & 3;
-        float* buf = epi_buf + q * 32 * TC_EPI_LD;
+    } else {  // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        float* buf = epi_buf + (warp - 2) * 32 * 32;
         int tc = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
             if (__any_sync(0xffffffffu, abort_flag)) break;  // warp-uniform: tcgen05.ld below is .sync.aligned
@@ -384,25 +394,70 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             rsi_umma::fence_after_sync();
             float* out = splits > 1 ? outf + size_t(T.z) * M * N : outf;
+            if (tma_store) {
+                // buf is 1024-byte aligned: 32 rows of 128 B in 128-byte-swizzle atoms
+                const uint32_t sbuf = smem_u32(buf);
+                const bool with_bias = splits == 1 && bias != nullptr;
 #pragma unroll 1
-            for (int cb = 0; cb < TBN; cb += 32) {
+                for (int cb = h * (TBN / 2); cb < (h + 1) * (TBN / 2); cb += 32) {
+                    float v[32];
+                    rsi_umma::ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * TBN + cb), v);
+                    if (cb + 32 == (h + 1) * (TBN / 2)) {  // this warp's last read of the accumulator
+                        rsi_umma::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
+                    }
+                    if (with_bias) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 b = *reinterpret_cast<const float4*>(bias + T.n0 + cb + 4 * i);
+                            v[4 * i] += b.x;
+                            v[4 * i + 1] += b.y;
+                            v[4 * i + 2] += b.z;
+                            v[4 * i + 3] += b.w;
+                        }
+                    }
+                    if (lane == 0) rsi_umma::bulk_wait_read0();  // the previous block has left buf
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        *reinterpret_cast<float4*>(buf + lane * 32 + 4 * (i ^ (lane & 7))) =
+                            make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    rsi_umma::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        rsi_umma::tma_store_2d(&tmC, T.n0 + cb, T.z * M + T.m0 + q * 32, sbuf);
+                        rsi_umma::bulk_commit();
+                    }
+                }
+                continue;
+            }
+#pragma unroll 1
+            for (int cb = h * (TBN / 2); cb < (h + 1) * (TBN / 2); cb += 32) {
                 float v[32];
                 rsi_umma::ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * TBN + cb), v);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    *reinterpret_cast<float4*>(buf + lane * TC_EPI_LD + 4 * i) =
+                    *reinterpret_cast<float4*>(buf + lane * 32 + 4 * (i ^ (lane & 7))) =
                         make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
                 __syncwarp();
+                const int c4 = lane & 7, col = T.n0 + cb + 4 * c4;
+                float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (EPI != 2 && splits == 1 && bias) bv = *reinterpret_cast<const float4*>(bias + col);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const int rr = 4 * i + (lane >> 3), c4 = lane & 7;
-                    const float4 w = *reinterpret_cast<const float4*>(buf + rr * TC_EPI_LD + 4 * c4);
-                    const int col = T.n0 + cb + 4 * c4;
+                    const int rr = 4 * i + (lane >> 3);
+                    float4 w = *reinterpret_cast<const float4*>(buf + rr * 32 + 4 * (c4 ^ (rr & 7)));
                     const size_t o = size_t(T.m0 + q * 32 + rr) * N + col;
-                    if (splits > 1)
+                    if (splits > 1) {
                         *reinterpret_cast<float4*>(out + o) = w;
-                    else
-                        epilogue4<EPI>(w, o, col, bias, aux, outf, outh);
+                    } else {
+                        w.x += bv.x;
+                        w.y += bv.y;
+                        w.z += bv.z;
+                        w.w += bv.w;
+                        epilogue4<EPI>(w, o, col, nullptr, aux, outf, outh);
+                    }
                 }
                 __syncwarp();
             }
@@ -410,6 +465,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
         }
     }
+    if (tma_store && warp >= 2 && lane == 0) rsi_umma::bulk_wait0();  // this warp's stores are complete
     __syncwarp();
     bool failed = !mbar_wait_bounded(smem_u32(&done), 0);
     failed = __syncthreads_or(failed || abort_flag);
@@ -554,18 +610,19 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// tensor map of a row-major bf16 matrix [rows x K]: boxes of 64 x box_rows,
+// tensor map of a row-major matrix [rows x cols] of `type` (2 or 4 bytes):
+// boxes of box_cols x box_rows (box_cols x element size = 128 bytes),
 // 128-byte swizzle, zero fill outside the matrix
-int make_tmap(CUtensorMap* tm, const bf16* ptr, int rows, int K, int box_rows) {
+int make_tmap(CUtensorMap* tm, CUtensorMapDataType type, size_t esize, const void* ptr, int64_t rows, int cols,
+              int box_cols, int box_rows) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return rsi_fail(RSI_E_CUDA, "rsi_nn_gemm: cuTensorMapEncodeTiled is not available");
-    const cuuint64_t dims[2] = {cuuint64_t(K), cuuint64_t(rows)};
-    const cuuint64_t strides[1] = {cuuint64_t(K) * sizeof(bf16)};
-    const cuuint32_t box[2] = {cuuint32_t(TC_BK), cuuint32_t(box_rows)};
+    const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(cols) * esize};
+    const cuuint32_t box[2] = {cuuint32_t(box_cols), cuuint32_t(box_rows)};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(tm, type, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return rsi_fail(RSI_E_CUDA, "rsi_nn_gemm: cuTensorMapEncodeTiled failed (%d)", int(r));
     return RSI_OK;
 }
@@ -583,18 +640,24 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, const f
     }
     int* status = rsi_status_ptr();
     if (!status) return RSI_E_CUDA;
-    CUtensorMap ta, tb;
-    int rc = make_tmap(&ta, A, M, K, TC_BM);
+    CUtensorMap ta, tb, tc;
+    int rc = make_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, M, K, TC_BK, TC_BM);
     if (rc) return rc;
-    rc = make_tmap(&tb, B, N, K, TBN);
+    rc = make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, N, K, TC_BK, TBN);
     if (rc) return rc;
     const int kt = K / TC_BK;
     const int kts = (kt + splits - 1) / splits;
     splits = (kt + kts - 1) / kts;
+    memset(&tc, 0, sizeof(tc));
+    if (EPI == 0 || splits > 1) {  // f32 blocks of 32 x 32 leave by TMA: the output or the partial sums
+        rc = make_tmap(&tc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, splits > 1 ? static_cast<const void*>(work) : outf,
+                       int64_t(splits) * M, N, 32, 32);
+        if (rc) return rc;
+    }
     const int tiles = (M / TC_BM) * (N / TBN) * splits;
     const int grid = std::min(tiles, sm_count());
-    gemm_tc_kernel<EPI, TBN><<<grid, TC_THREADS, C::SMEM, s>>>(ta, tb, M, N, K, bias, aux, splits > 1 ? work : outf,
-                                                               outh, kts, splits, status);
+    gemm_tc_kernel<EPI, TBN><<<grid, TC_THREADS, C::SMEM, s>>>(ta, tb, tc, M, N, K, bias, aux,
+                                                               splits > 1 ? work : outf, outh, kts, splits, status);
     RSI_CHECK_LAUNCH("gemm_tc_kernel");
     if (splits > 1) {
         int64_t pairs = int64_t(M) * N / 2;

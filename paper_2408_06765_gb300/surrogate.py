@@ -48,9 +48,10 @@ class MLP:
     """Weights, Adam state and activation buffers of the surrogate."""
 
     def __init__(self, n_freq=128, width=512, depth=4, n_out=2 * 128 * 128, batch=256, seed=0,
-                 sigma_b=2.0, device="cuda"):
+                 sigma_b=2.0, device="cuda", engine="tcgen05"):
         self.n_in, self.F, self.width, self.depth, self.n_out = 5, n_freq, width, depth, n_out
         self.batch = batch
+        self.engine = engine  # GEMM engine: "tcgen05" (tensor memory) or "mma_sync"
         self.device = device
         rng = np.random.default_rng(seed)
         dims = [2 * n_freq] + [width] * depth + [n_out]
@@ -91,9 +92,14 @@ class MLP:
         self.WT = [torch.empty((w.shape[1], w.shape[0]), dtype=bf, device=d) for w in self.W]
         self.partial = torch.empty(1024, dtype=torch.float64, device=d)
         # split K for the backward GEMM through the output layer (few output
-        # tiles, K = n_out): about two CTAs per SM
-        tiles = (B // 128) * (self.width // 128)
-        self.splits_out = max(1, min(self.n_out // 32, (2 * 152) // max(1, tiles)))
+        # tiles, K = n_out): about one (tcgen05, persistent) or two (mma.sync)
+        # CTAs per SM
+        if self.engine == "tcgen05":
+            tiles = (B // 128) * (self.width // (256 if self.width % 256 == 0 else 128))
+            self.splits_out = max(1, min(self.n_out // 64, 152 // max(1, tiles)))
+        else:
+            tiles = (B // 128) * (self.width // 128)
+            self.splits_out = max(1, min(self.n_out // 32, (2 * 152) // max(1, tiles)))
         self.work = torch.empty(self.splits_out * B * self.width if self.splits_out > 1 else 1,
                                 dtype=torch.float32, device=d)
         self.loss_buf = torch.empty(1, dtype=torch.float32, device=d)
@@ -105,8 +111,8 @@ class MLP:
         rsi.nn_features(p, self.lo, self.hi, self.fmat, self.H[0])
         for l in range(self.depth):
             rsi.nn_gemm("bias_silu", self.H[l], self.W16[l], out_f32=self.Z[l], out_bf16=self.H[l + 1],
-                        bias=self.b[l])
-        rsi.nn_gemm("f32", self.H[self.depth], self.W16[-1], out_f32=self.y, bias=self.b[-1])
+                        bias=self.b[l], engine=self.engine)
+        rsi.nn_gemm("f32", self.H[self.depth], self.W16[-1], out_f32=self.y, bias=self.b[-1], engine=self.engine)
         return self.y
 
     def loss(self, t, grad: bool = True) -> torch.Tensor:
@@ -119,19 +125,20 @@ class MLP:
         L = self.depth
         rsi.nn_transpose(self.dy, self.dyT)
         rsi.nn_transpose(self.H[L], self.HT[L])
-        rsi.nn_gemm("f32", self.dyT, self.HT[L], out_f32=self.gW[L])
+        rsi.nn_gemm("f32", self.dyT, self.HT[L], out_f32=self.gW[L], engine=self.engine)
         rsi.nn_colsum(self.dy, self.gb[L])
         rsi.nn_transpose(self.W16[L], self.WT[L])
         rsi.nn_gemm("dsilu", self.dy, self.WT[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1],
-                    splits=self.splits_out, workspace=self.work)
+                    splits=self.splits_out, workspace=self.work, engine=self.engine)
         for l in range(L - 1, -1, -1):
             rsi.nn_transpose(self.dZ[l], self.dZT[l])
             rsi.nn_transpose(self.H[l], self.HT[l])
-            rsi.nn_gemm("f32", self.dZT[l], self.HT[l], out_f32=self.gW[l])
+            rsi.nn_gemm("f32", self.dZT[l], self.HT[l], out_f32=self.gW[l], engine=self.engine)
             rsi.nn_colsum(self.dZ[l], self.gb[l])
             if l > 0:
                 rsi.nn_transpose(self.W16[l], self.WT[l])
-                rsi.nn_gemm("dsilu", self.dZ[l], self.WT[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1])
+                rsi.nn_gemm("dsilu", self.dZ[l], self.WT[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1],
+                            engine=self.engine)
 
     def adam(self, lr: float):
         self.step_count += 1

@@ -140,8 +140,8 @@ def test_carrier_round_trip_and_definition():
     assert abs(complex(got[0], got[1]) - want) < 1e-5 * abs(want) + 1e-6
 
 
-def small_net():
-    return surrogate.MLP(n_freq=64, width=128, depth=2, n_out=256, batch=128, seed=3, sigma_b=1.0)
+def small_net(engine="tcgen05"):
+    return surrogate.MLP(n_freq=64, width=128, depth=2, n_out=256, batch=128, seed=3, sigma_b=1.0, engine=engine)
 
 
 def oracle_params(net):
@@ -150,8 +150,9 @@ def oracle_params(net):
     return {"W": Wq, "b": bq}
 
 
-def test_forward_backward_match_fp64_oracle():
-    net = small_net()
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+def test_forward_backward_match_fp64_oracle(engine):
+    net = small_net(engine)
     rng = np.random.default_rng(4)
     params = surrogate.LO + (surrogate.HI - surrogate.LO) * rng.uniform(size=(128, 5))
     t = rng.normal(size=(128, 256)) * 0.5
