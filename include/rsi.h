@@ -297,20 +297,28 @@ enum rsi_nn_engine {
     RSI_NN_ENGINE_TCGEN05 = 1   /* tcgen05.mma 128x128x16, accumulators in tensor memory
                                    (K % 64 == 0)                                      */
 };
+enum rsi_nn_layout {
+    RSI_NN_A_T = 1, /* A is stored as [K x M] row-major (its transpose)       */
+    RSI_NN_B_T = 2  /* B is stored as [K x N] row-major                       */
+};
 /* C[M x N] = A[M x K] B[N x K]^T on BF16 tensor cores with FP32 accumulation
- * and the chosen epilogue.  M, N multiples of 128; A, B 16-byte aligned.
+ * and the chosen epilogue.  A, B row-major [M x K], [N x K] (K contiguous)
+ * unless `layout` says otherwise (tcgen05 engine only).  M, N multiples of
+ * 128; A, B 16-byte aligned (the tcgen05 engine: every pointer 16-byte
+ * aligned).
  * bias: f32 [N] or NULL (F32 epilogue).  splits > 1 splits K across CTAs
  * (for few output tiles and long K): partial sums go to workspace
  * (f32 [splits][M][N], caller-allocated) and a second kernel adds them in
  * split order and applies the epilogue.                                    */
-int rsi_nn_gemm(int32_t epilogue, int32_t engine, const void *A, const void *B, int32_t M, int32_t N,
-                int32_t K, const float *bias, const float *aux, float *out_f32, void *out_bf16,
+int rsi_nn_gemm(int32_t epilogue, int32_t engine, int32_t layout, const void *A, const void *B, int32_t M,
+                int32_t N, int32_t K, const float *bias, const float *aux, float *out_f32, void *out_bf16,
                 int32_t splits, float *workspace, void *stream);
 /* out[c][r] = in[r][c] for a bf16 rows x cols matrix.                      */
 int rsi_nn_transpose(const void *in_bf16, int32_t rows, int32_t cols, void *out_bf16, void *stream);
-/* *loss_out = mean((y - t)^2) over n values (f32); grad_bf16 (may be NULL)
- * = grad_scale * (y - t).  partial: f64 scratch [n_partial] (the number of
- * CTAs of the reduction).                                                  */
+/* *loss_out = mean((y - t)^2) over n values (f32, n % 4 == 0, y and t
+ * 16-byte aligned); grad_bf16 (may be NULL, 8-byte aligned) = grad_scale *
+ * (y - t).  partial: f64 scratch [n_partial] (the number of CTAs of the
+ * reduction).                                                              */
 int rsi_nn_loss(const float *y, const float *t, int64_t n, float grad_scale, void *grad_bf16,
                 double *partial, int32_t n_partial, float *loss_out, void *stream);
 /* out[c] = sum over rows of a bf16 rows x cols matrix (bias gradients).    */

@@ -277,11 +277,13 @@ __device__ __forceinline__ TcTile tc_tile(int t, int m_tiles, int n_tiles, int T
 template <int EPI, int TBN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmC, int M, int N, int K, const float* __restrict__ bias,
-                   const float* __restrict__ aux, float* __restrict__ outf, bf16* __restrict__ outh, int kts,
+                   const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH, int M, int N,
+                   int K, int layout, const float* __restrict__ bias, const float* __restrict__ aux, int kts,
                    int splits, int* status) {
-    // F32 output and split-K partials: TMA stores through tmC (f32 [splits*M x N])
-    const bool tma_store = EPI == 0 || splits > 1;
+    // layout bit 0: A is stored [K x M] (MN-major), bit 1: B is stored [K x N]
+    const bool a_mn = layout & 1, b_mn = layout & 2;
+    // outputs leave by TMA stores: f32 (F32, BIAS_SILU's z, split-K partial
+    // sums) through tmC over [splits*M x N], bf16 (BIAS_SILU, DSILU) through tmH
     using C = TcCfg<TBN>;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES], acc_full[2], acc_empty[2], done;
@@ -313,7 +315,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (tid == 64) {
         rsi_umma::prefetch_tmap(&tmA);
         rsi_umma::prefetch_tmap(&tmB);
-        if (tma_store) rsi_umma::prefetch_tmap(&tmC);
+        if (EPI != 2 || splits > 1) rsi_umma::prefetch_tmap(&tmC);
+        if (EPI != 0 && splits == 1) rsi_umma::prefetch_tmap(&tmH);
     }
     rsi_umma::fence_before_sync();
     __syncthreads();
@@ -335,8 +338,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t sa = base + uint32_t(s) * C::STAGE;
                     mbar_expect_tx(smem_u32(&full[s]), C::STAGE);
                     const int k0 = (T.kt0 + kt) * TC_BK;
-                    rsi_umma::tma_load_2d(sa, &tmA, k0, T.m0, smem_u32(&full[s]));
-                    rsi_umma::tma_load_2d(sa + TC_A_BYTES, &tmB, k0, T.n0, smem_u32(&full[s]));
+                    if (a_mn)  // boxes of 64 M x 64 K, 8 KB apart
+                        for (int j = 0; j < TC_BM / 64; ++j)
+                            rsi_umma::tma_load_2d(sa + j * 8192u, &tmA, T.m0 + 64 * j, k0, smem_u32(&full[s]));
+                    else
+                        rsi_umma::tma_load_2d(sa, &tmA, k0, T.m0, smem_u32(&full[s]));
+                    if (b_mn)
+                        for (int j = 0; j < TBN / 64; ++j)
+                            rsi_umma::tma_load_2d(sa + TC_A_BYTES + j * 8192u, &tmB, T.n0 + 64 * j, k0,
+                                                  smem_u32(&full[s]));
+                    else
+                        rsi_umma::tma_load_2d(sa + TC_A_BYTES, &tmB, k0, T.n0, smem_u32(&full[s]));
                 }
             }
             // the copies still in flight land before the CTA can exit
@@ -346,6 +358,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
+            const uint32_t idesc = C::IDESC | (uint32_t(a_mn) << 15) | (uint32_t(b_mn) << 16);
             int it = 0, tc = 0;
             for (int t = blockIdx.x; t < total && !abort_flag; t += gridDim.x, ++tc) {
                 const TcTile T = tc_tile(t, m_tiles, n_tiles, TBN, kt_total, kts);
@@ -366,9 +379,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     rsi_umma::fence_after_sync();
                     const uint32_t sa = base + uint32_t(s) * C::STAGE, sb = sa + TC_A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk)
-                        rsi_umma::mma_f16(d, rsi_umma::smem_desc_sw128(sa + kk * 32),
-                                          rsi_umma::smem_desc_sw128(sb + kk * 32), C::IDESC, (kt | kk) != 0);
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        const uint64_t da = a_mn ? rsi_umma::smem_desc_mn_sw128(sa + kk * 2048, 8192)
+                                                 : rsi_umma::smem_desc_sw128(sa + kk * 32);
+                        const uint64_t db = b_mn ? rsi_umma::smem_desc_mn_sw128(sb + kk * 2048, 8192)
+                                                 : rsi_umma::smem_desc_sw128(sb + kk * 32);
+                        rsi_umma::mma_f16(d, da, db, idesc, (kt | kk) != 0);
+                    }
                     rsi_umma::commit(smem_u32(&empty[s]));
                 }
                 if (!ok) {
@@ -393,30 +410,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 break;
             }
             rsi_umma::fence_after_sync();
-            float* out = splits > 1 ? outf + size_t(T.z) * M * N : outf;
-            if (tma_store) {
-                // buf is 1024-byte aligned: 32 rows of 128 B in 128-byte-swizzle atoms
-                const uint32_t sbuf = smem_u32(buf);
-                const bool with_bias = splits == 1 && bias != nullptr;
+            const uint32_t sbuf = smem_u32(buf);  // 1024-byte aligned: 32 rows of 128 B, 128-byte swizzle atoms
+            const int row0 = T.m0 + q * 32;       // this warp's first output row; lane = row - row0
 #pragma unroll 1
-                for (int cb = h * (TBN / 2); cb < (h + 1) * (TBN / 2); cb += 32) {
-                    float v[32];
-                    rsi_umma::ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * TBN + cb), v);
-                    if (cb + 32 == (h + 1) * (TBN / 2)) {  // this warp's last read of the accumulator
-                        rsi_umma::fence_before_sync();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
-                    }
-                    if (with_bias) {
+            for (int cb = h * (TBN / 2); cb < (h + 1) * (TBN / 2); cb += 32) {
+                const int col0 = T.n0 + cb;
+                float a[32];
+                if (EPI == 2 && splits == 1) {  // the pre-activations this row's outputs need, ahead of the TMEM read
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float4 b = *reinterpret_cast<const float4*>(bias + T.n0 + cb + 4 * i);
-                            v[4 * i] += b.x;
-                            v[4 * i + 1] += b.y;
-                            v[4 * i + 2] += b.z;
-                            v[4 * i + 3] += b.w;
-                        }
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 z = *reinterpret_cast<const float4*>(aux + size_t(row0 + lane) * N + col0 + 4 * i);
+                        a[4 * i] = z.x;
+                        a[4 * i + 1] = z.y;
+                        a[4 * i + 2] = z.z;
+                        a[4 * i + 3] = z.w;
                     }
+                }
+                float v[32];
+                rsi_umma::ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * TBN + cb), v);
+                if (cb + 32 == (h + 1) * (TBN / 2)) {  // this warp's last read of the accumulator
+                    rsi_umma::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
+                }
+                if (EPI != 2 && splits == 1 && bias != nullptr) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 b = *reinterpret_cast<const float4*>(bias + col0 + 4 * i);
+                        v[4 * i] += b.x;
+                        v[4 * i + 1] += b.y;
+                        v[4 * i + 2] += b.z;
+                        v[4 * i + 3] += b.w;
+                    }
+                }
+                if (EPI != 2 || splits > 1) {  // f32 block: output, z, or partial sums of split T.z
                     if (lane == 0) rsi_umma::bulk_wait_read0();  // the previous block has left buf
                     __syncwarp();
 #pragma unroll
@@ -426,46 +453,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     rsi_umma::fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        rsi_umma::tma_store_2d(&tmC, T.n0 + cb, T.z * M + T.m0 + q * 32, sbuf);
+                        rsi_umma::tma_store_2d(&tmC, col0, T.z * M + row0, sbuf);
                         rsi_umma::bulk_commit();
                     }
                 }
-                continue;
-            }
-#pragma unroll 1
-            for (int cb = h * (TBN / 2); cb < (h + 1) * (TBN / 2); cb += 32) {
-                float v[32];
-                rsi_umma::ld_32x32b_x32(tmem + (uint32_t(q * 32) << 16) + uint32_t(acc * TBN + cb), v);
+                if (EPI != 0 && splits == 1) {  // bf16 block (dense 64-byte rows): silu(z) or C * silu'(aux)
+                    uint32_t hw[16];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    *reinterpret_cast<float4*>(buf + lane * 32 + 4 * (i ^ (lane & 7))) =
-                        make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                __syncwarp();
-                const int c4 = lane & 7, col = T.n0 + cb + 4 * c4;
-                float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (EPI != 2 && splits == 1 && bias) bv = *reinterpret_cast<const float4*>(bias + col);
+                    for (int j = 0; j < 16; ++j) {
+                        const float x0 = EPI == 1 ? silu_(v[2 * j]) : v[2 * j] * dsilu_(a[2 * j]);
+                        const float x1 = EPI == 1 ? silu_(v[2 * j + 1]) : v[2 * j + 1] * dsilu_(a[2 * j + 1]);
+                        __nv_bfloat162 p2 = __floats2bfloat162_rn(x0, x1);
+                        hw[j] = *reinterpret_cast<uint32_t*>(&p2);
+                    }
+                    if (lane == 0) rsi_umma::bulk_wait_read0();
+                    __syncwarp();
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int rr = 4 * i + (lane >> 3);
-                    float4 w = *reinterpret_cast<const float4*>(buf + rr * 32 + 4 * (c4 ^ (rr & 7)));
-                    const size_t o = size_t(T.m0 + q * 32 + rr) * N + col;
-                    if (splits > 1) {
-                        *reinterpret_cast<float4*>(out + o) = w;
-                    } else {
-                        w.x += bv.x;
-                        w.y += bv.y;
-                        w.z += bv.z;
-                        w.w += bv.w;
-                        epilogue4<EPI>(w, o, col, nullptr, aux, outf, outh);
+                    for (int c = 0; c < 4; ++c)
+                        *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(buf) + lane * 64 + 16 * c) =
+                            make_uint4(hw[4 * c], hw[4 * c + 1], hw[4 * c + 2], hw[4 * c + 3]);
+                    rsi_umma::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        rsi_umma::tma_store_2d(&tmH, col0, row0, sbuf);
+                        rsi_umma::bulk_commit();
                     }
                 }
-                __syncwarp();
             }
-            rsi_umma::fence_before_sync();
-            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
         }
     }
-    if (tma_store && warp >= 2 && lane == 0) rsi_umma::bulk_wait0();  // this warp's stores are complete
+    if (warp >= 2 && lane == 0) rsi_umma::bulk_wait0();  // this warp's stores are complete
     __syncwarp();
     bool failed = !mbar_wait_bounded(smem_u32(&done), 0);
     failed = __syncthreads_or(failed || abort_flag);
@@ -507,17 +524,28 @@ __global__ void transpose_kernel(const bf16* __restrict__ in, int rows, int cols
 }
 
 // per-block partial sums of (y - t)^2 and the gradient scale * (y - t) in bf16
+// n % 4 == 0.  Each thread sums its squared differences in FP32 (at most a
+// few dozen terms), blocks combine in FP64; partial[blockIdx.x] = block sum.
 __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict__ t, int64_t n, float gscale,
                             bf16* __restrict__ grad, double* __restrict__ partial) {
     __shared__ double red[32];
-    double acc = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
-        float d = y[i] - t[i];
-        acc += double(d) * d;
-        if (grad) grad[i] = __float2bfloat16_rn(gscale * d);
+    float acc = 0.0f;
+    const int64_t n4 = n / 4;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4*>(y)[i];
+        const float4 b = reinterpret_cast<const float4*>(t)[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        acc += (d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3);
+        if (grad) {
+            __nv_bfloat162 g0 = __floats2bfloat162_rn(gscale * d0, gscale * d1);
+            __nv_bfloat162 g1 = __floats2bfloat162_rn(gscale * d2, gscale * d3);
+            reinterpret_cast<uint2*>(grad)[i] =
+                make_uint2(*reinterpret_cast<uint32_t*>(&g0), *reinterpret_cast<uint32_t*>(&g1));
+        }
     }
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    double da = acc;
+    for (int o = 16; o; o >>= 1) da += __shfl_xor_sync(0xffffffffu, da, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = da;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -525,23 +553,35 @@ __global__ void loss_kernel(const float* __restrict__ y, const float* __restrict
         partial[blockIdx.x] = s;
     }
 }
-
+// one block of 256 threads: strided sums, then a fixed-order tree
 __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, double scale, float* out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += partial[i];
-        *out = float(s * scale);
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (int(threadIdx.x) < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = float(red[0] * scale);
+}
+// out[c] = sum over rows of m[r][c]: blocks of 32 columns x 8 row lanes,
+// each lane sums every 8th row, the 8 lane sums are added in a fixed order
+__global__ void colsum_kernel(const bf16* __restrict__ m, int rows, int cols, float* __restrict__ out) {
+    __shared__ float red[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    float s = 0.0f;
+    if (c < cols)
+        for (int r = threadIdx.y; r < rows; r += 8) s += __bfloat162float(m[size_t(r) * cols + c]);
+    red[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < cols) {
+        float t = 0.0f;
+        for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+        out[c] = t;
     }
 }
-
-__global__ void colsum_kernel(const bf16* __restrict__ m, int rows, int cols, float* __restrict__ out) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols) return;
-    float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += __bfloat162float(m[size_t(r) * cols + c]);
-    out[c] = s;
-}
-
 __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
                             float c1, float c2, bf16* __restrict__ wh) {
@@ -611,25 +651,25 @@ EncodeTiledFn encode_tiled() {
 }
 
 // tensor map of a row-major matrix [rows x cols] of `type` (2 or 4 bytes):
-// boxes of box_cols x box_rows (box_cols x element size = 128 bytes),
-// 128-byte swizzle, zero fill outside the matrix
+// boxes of box_cols x box_rows, zero fill outside the matrix; with the
+// 128-byte swizzle a box row is 128 bytes
 int make_tmap(CUtensorMap* tm, CUtensorMapDataType type, size_t esize, const void* ptr, int64_t rows, int cols,
-              int box_cols, int box_rows) {
+              int box_cols, int box_rows, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     EncodeTiledFn fn = encode_tiled();
     if (!fn) return rsi_fail(RSI_E_CUDA, "rsi_nn_gemm: cuTensorMapEncodeTiled is not available");
     const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
     const cuuint64_t strides[1] = {cuuint64_t(cols) * esize};
     const cuuint32_t box[2] = {cuuint32_t(box_cols), cuuint32_t(box_rows)};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(tm, type, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(tm, type, 2, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return rsi_fail(RSI_E_CUDA, "rsi_nn_gemm: cuTensorMapEncodeTiled failed (%d)", int(r));
     return RSI_OK;
 }
 
 template <int EPI, int TBN>
-int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const float* aux,
-                      float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
+int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, int layout, const float* bias,
+                      const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
     using C = TcCfg<TBN>;
     static bool attr = false;
     if (!attr) {
@@ -640,24 +680,31 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, const f
     }
     int* status = rsi_status_ptr();
     if (!status) return RSI_E_CUDA;
-    CUtensorMap ta, tb, tc;
-    int rc = make_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, M, K, TC_BK, TC_BM);
+    CUtensorMap ta, tb, tc, th;
+    int rc = (layout & RSI_NN_A_T) ? make_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, K, M, 64, TC_BK)
+                                   : make_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, M, K, TC_BK, TC_BM);
     if (rc) return rc;
-    rc = make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, N, K, TC_BK, TBN);
+    rc = (layout & RSI_NN_B_T) ? make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, K, N, 64, TC_BK)
+                               : make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, N, K, TC_BK, TBN);
     if (rc) return rc;
     const int kt = K / TC_BK;
     const int kts = (kt + splits - 1) / splits;
     splits = (kt + kts - 1) / kts;
     memset(&tc, 0, sizeof(tc));
-    if (EPI == 0 || splits > 1) {  // f32 blocks of 32 x 32 leave by TMA: the output or the partial sums
+    memset(&th, 0, sizeof(th));
+    if (EPI != 2 || splits > 1) {  // f32 blocks of 32 x 32: the output, z, or the partial sums
         rc = make_tmap(&tc, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, splits > 1 ? static_cast<const void*>(work) : outf,
                        int64_t(splits) * M, N, 32, 32);
         if (rc) return rc;
     }
+    if (EPI != 0 && splits == 1) {  // bf16 blocks of 32 x 32, dense 64-byte rows in shared memory
+        rc = make_tmap(&th, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, outh, M, N, 32, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
+        if (rc) return rc;
+    }
     const int tiles = (M / TC_BM) * (N / TBN) * splits;
     const int grid = std::min(tiles, sm_count());
-    gemm_tc_kernel<EPI, TBN><<<grid, TC_THREADS, C::SMEM, s>>>(ta, tb, tc, M, N, K, bias, aux,
-                                                               splits > 1 ? work : outf, outh, kts, splits, status);
+    gemm_tc_kernel<EPI, TBN><<<grid, TC_THREADS, C::SMEM, s>>>(ta, tb, tc, th, M, N, K, layout, bias, aux, kts,
+                                                               splits, status);
     RSI_CHECK_LAUNCH("gemm_tc_kernel");
     if (splits > 1) {
         int64_t pairs = int64_t(M) * N / 2;
@@ -669,10 +716,11 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, const f
 }
 
 template <int EPI>
-int gemm_tc_launch(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const float* aux,
-                   float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
-    if (N % 256 == 0) return gemm_tc_launch_bn<EPI, 256>(A, B, M, N, K, bias, aux, outf, outh, splits, work, s);
-    return gemm_tc_launch_bn<EPI, 128>(A, B, M, N, K, bias, aux, outf, outh, splits, work, s);
+int gemm_tc_launch(const bf16* A, const bf16* B, int M, int N, int K, int layout, const float* bias,
+                   const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
+    if (N % 256 == 0)
+        return gemm_tc_launch_bn<EPI, 256>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
+    return gemm_tc_launch_bn<EPI, 128>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
 }
 
 template <int EPI>
@@ -716,17 +764,19 @@ extern "C" int rsi_nn_features(const float* params, const float* lo, const float
     return RSI_OK;
 }
 
-extern "C" int rsi_nn_gemm(int32_t epilogue, int32_t engine, const void* A, const void* B, int32_t M, int32_t N,
-                           int32_t K, const float* bias, const float* aux, float* out_f32, void* out_bf16,
+extern "C" int rsi_nn_gemm(int32_t epilogue, int32_t engine, int32_t layout, const void* A, const void* B, int32_t M,
+                           int32_t N, int32_t K, const float* bias, const float* aux, float* out_f32, void* out_bf16,
                            int32_t splits, float* workspace, void* stream) {
     if (!A || !B || M < 1 || N < 1 || K < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: bad arguments");
     if (engine != RSI_NN_ENGINE_MMA_SYNC && engine != RSI_NN_ENGINE_TCGEN05)
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: unknown engine %d", engine);
+    if (layout & ~(RSI_NN_A_T | RSI_NN_B_T) || (layout && engine != RSI_NN_ENGINE_TCGEN05))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: layout %d needs the tcgen05 engine", layout);
     if (engine == RSI_NN_ENGINE_TCGEN05 && K % TC_BK)
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: the tcgen05 engine needs K % 64 == 0 (got %d)", K);
     if (engine == RSI_NN_ENGINE_TCGEN05 && (misaligned(out_f32, 16) || misaligned(aux, 16) || misaligned(bias, 16) ||
-                                            misaligned(out_bf16, 8) || misaligned(workspace, 16)))
-        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: the tcgen05 engine needs 16-byte aligned f32 and 8-byte bf16 outputs");
+                                            misaligned(out_bf16, 16) || misaligned(workspace, 16)))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: the tcgen05 engine needs 16-byte aligned outputs, bias and aux");
     if (splits < 1 || splits > K / BK || (splits > 1 && !workspace))
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: splits must be in [1, K/32] and need a workspace");
     if (misaligned(workspace, 8)) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: misaligned workspace");
@@ -744,15 +794,15 @@ extern "C" int rsi_nn_gemm(int32_t epilogue, int32_t engine, const void* A, cons
     switch (epilogue) {
         case RSI_NN_EPI_F32:
             if (!out_f32) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: F32 epilogue needs out_f32");
-            return tc ? gemm_tc_launch<0>(a, b, M, N, K, bias, nullptr, out_f32, nullptr, splits, workspace, s)
+            return tc ? gemm_tc_launch<0>(a, b, M, N, K, layout, bias, nullptr, out_f32, nullptr, splits, workspace, s)
                       : gemm_launch<0>(a, b, M, N, K, bias, nullptr, out_f32, nullptr, splits, workspace, s);
         case RSI_NN_EPI_BIAS_SILU:
             if (!out_f32 || !oh || !bias) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: BIAS_SILU needs bias and outputs");
-            return tc ? gemm_tc_launch<1>(a, b, M, N, K, bias, nullptr, out_f32, oh, splits, workspace, s)
+            return tc ? gemm_tc_launch<1>(a, b, M, N, K, layout, bias, nullptr, out_f32, oh, splits, workspace, s)
                       : gemm_launch<1>(a, b, M, N, K, bias, nullptr, out_f32, oh, splits, workspace, s);
         case RSI_NN_EPI_DSILU:
             if (!aux || !oh) return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: DSILU needs aux and out_bf16");
-            return tc ? gemm_tc_launch<2>(a, b, M, N, K, nullptr, aux, nullptr, oh, splits, workspace, s)
+            return tc ? gemm_tc_launch<2>(a, b, M, N, K, layout, nullptr, aux, nullptr, oh, splits, workspace, s)
                       : gemm_launch<2>(a, b, M, N, K, nullptr, aux, nullptr, oh, splits, workspace, s);
         default:
             return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: unknown epilogue %d", epilogue);
@@ -770,19 +820,21 @@ extern "C" int rsi_nn_transpose(const void* in_bf16, int32_t rows, int32_t cols,
 
 extern "C" int rsi_nn_loss(const float* y, const float* t, int64_t n, float grad_scale, void* grad_bf16,
                            double* partial, int32_t n_partial, float* loss_out, void* stream) {
-    if (!y || !t || n < 1 || !partial || n_partial < 1 || !loss_out)
-        return rsi_fail(RSI_E_INVAL, "rsi_nn_loss: bad arguments");
+    if (!y || !t || n < 1 || n % 4 || !partial || n_partial < 1 || !loss_out)
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_loss: bad arguments (n must be a positive multiple of 4)");
+    if (misaligned(y, 16) || misaligned(t, 16) || misaligned(grad_bf16, 8))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_loss: misaligned pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     loss_kernel<<<n_partial, 256, 0, s>>>(y, t, n, grad_scale, static_cast<bf16*>(grad_bf16), partial);
     RSI_CHECK_LAUNCH("loss_kernel");
-    sum_partials_kernel<<<1, 32, 0, s>>>(partial, n_partial, 1.0 / double(n), loss_out);
+    sum_partials_kernel<<<1, 256, 0, s>>>(partial, n_partial, 1.0 / double(n), loss_out);
     RSI_CHECK_LAUNCH("sum_partials_kernel");
     return RSI_OK;
 }
 
 extern "C" int rsi_nn_colsum(const void* m_bf16, int32_t rows, int32_t cols, float* out, void* stream) {
     if (!m_bf16 || !out || rows < 1 || cols < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_colsum: bad arguments");
-    colsum_kernel<<<(cols + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+    colsum_kernel<<<(cols + 31) / 32, dim3(32, 8), 0, static_cast<cudaStream_t>(stream)>>>(
         static_cast<const bf16*>(m_bf16), rows, cols, out);
     RSI_CHECK_LAUNCH("colsum_kernel");
     return RSI_OK;

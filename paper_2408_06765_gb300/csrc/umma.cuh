@@ -13,7 +13,7 @@
 //   bits 61-63  swizzle mode (0 = none, 2 = 128-byte)
 // Instruction descriptor (32 bits) of kind::f16:
 //   bits 4-5 D format (1 = f32), 7-9 A format (1 = bf16), 10-12 B format
-//   (1 = bf16), 15 / 16 A / B major (0 = K-major), 17-22 N >> 3,
+//   (1 = bf16), 15 / 16 A / B major (0 = K-major, 1 = MN-major), 17-22 N >> 3,
 //   24-28 M >> 4; everything else 0 (dense, no negation, no saturation).
 #pragma once
 
@@ -38,6 +38,16 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
 __host__ __device__ constexpr uint64_t smem_desc_sw128(uint32_t smem_addr) {
     return (uint64_t((smem_addr >> 4) & 0x3FFFu)) | (uint64_t(1) << 16) | (uint64_t(1024 >> 4) << 32) |
            (uint64_t(1) << 46) | (uint64_t(2) << 61);
+}
+
+// MN-major tile written by TMA with the 128-byte swizzle in boxes of 64 MN
+// elements (128 B) x 64 k rows (8 KB, rows k at 128 B): the stride between
+// 8-row groups along K is 1024 B, the stride between 64-element blocks along
+// M (or N) is lbo_bytes (8 KB, one box); the k-th 16-deep slice starts
+// 16 x 128 bytes further.
+__host__ __device__ constexpr uint64_t smem_desc_mn_sw128(uint32_t smem_addr, uint32_t lbo_bytes) {
+    return (uint64_t((smem_addr >> 4) & 0x3FFFu)) | (uint64_t((lbo_bytes >> 4) & 0x3FFFu) << 16) |
+           (uint64_t(1024 >> 4) << 32) | (uint64_t(1) << 46) | (uint64_t(2) << 61);
 }
 
 // byte offset of element (row r, k) in a K-major no-swizzle tile whose core

@@ -125,7 +125,7 @@ def load(path: str | None = None):
         L.rsi_batch_destroy.argtypes = [vp]
         f32, f64 = ctypes.c_float, ctypes.c_double
         L.rsi_nn_features.argtypes = [vp, vp, vp, vp, i32, i32, i32, vp, vp]
-        L.rsi_nn_gemm.argtypes = [i32, i32, vp, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp]
+        L.rsi_nn_gemm.argtypes = [i32, i32, i32, vp, vp, i32, i32, i32, vp, vp, vp, vp, i32, vp, vp]
         L.rsi_nn_transpose.argtypes = [vp, i32, i32, vp, vp]
         L.rsi_nn_loss.argtypes = [vp, vp, i64, f32, vp, vp, i32, vp, vp]
         L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
@@ -467,14 +467,16 @@ def nn_features(p, lo, hi, fmat, out, stream=None):
 
 
 def nn_gemm(epi: str, A, B, out_f32=None, out_bf16=None, bias=None, aux=None, splits: int = 1,
-            workspace=None, engine: str = "mma_sync", stream=None):
-    """C[M x N] = A[M x K] B[N x K]^T with an epilogue (see rsi_nn_gemm)."""
-    M, K = A.shape
-    N = B.shape[0]
-    assert B.shape[1] == K
+            workspace=None, engine: str = "mma_sync", a_t: bool = False, b_t: bool = False, stream=None):
+    """C[M x N] = A[M x K] B[N x K]^T with an epilogue (see rsi_nn_gemm).
+    a_t: A is given as its transpose [K x M]; b_t: B is given as [K x N]."""
+    K, M = A.shape if a_t else A.shape[::-1]
+    N = B.shape[1] if b_t else B.shape[0]
+    assert (B.shape[0] if b_t else B.shape[1]) == K
     if splits > 1:
         assert workspace is not None and workspace.numel() >= splits * M * N
-    _check(load().rsi_nn_gemm(NN_EPI[epi], NN_ENGINE[engine], _ptr(A), _ptr(B), M, N, K, _ptr(bias),
+    layout = (1 if a_t else 0) | (2 if b_t else 0)
+    _check(load().rsi_nn_gemm(NN_EPI[epi], NN_ENGINE[engine], layout, _ptr(A), _ptr(B), M, N, K, _ptr(bias),
                               _ptr(aux), _ptr(out_f32), _ptr(out_bf16), int(splits), _ptr(workspace),
                               _stream(stream)), "rsi_nn_gemm")
 

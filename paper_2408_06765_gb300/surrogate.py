@@ -123,22 +123,40 @@ class MLP:
     def backward(self):
         """Gradients of the mean squared error into gW, gb (after loss())."""
         L = self.depth
-        rsi.nn_transpose(self.dy, self.dyT)
-        rsi.nn_transpose(self.H[L], self.HT[L])
-        rsi.nn_gemm("f32", self.dyT, self.HT[L], out_f32=self.gW[L], engine=self.engine)
+        tc = self.engine == "tcgen05"
+        # gW[L] = dy^T H[L]; dZ[L-1] = (dy W[L]) * silu'(Z[L-1]).  The tcgen05
+        # engine reads the stored matrices in either orientation; the mma.sync
+        # engine needs K-contiguous copies.
+        if tc:
+            rsi.nn_gemm("f32", self.dy, self.H[L], out_f32=self.gW[L], engine="tcgen05", a_t=True, b_t=True)
+        else:
+            rsi.nn_transpose(self.dy, self.dyT)
+            rsi.nn_transpose(self.H[L], self.HT[L])
+            rsi.nn_gemm("f32", self.dyT, self.HT[L], out_f32=self.gW[L], engine=self.engine)
         rsi.nn_colsum(self.dy, self.gb[L])
-        rsi.nn_transpose(self.W16[L], self.WT[L])
-        rsi.nn_gemm("dsilu", self.dy, self.WT[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1],
-                    splits=self.splits_out, workspace=self.work, engine=self.engine)
+        if tc:
+            rsi.nn_gemm("dsilu", self.dy, self.W16[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1],
+                        splits=self.splits_out, workspace=self.work, engine="tcgen05", b_t=True)
+        else:
+            rsi.nn_transpose(self.W16[L], self.WT[L])
+            rsi.nn_gemm("dsilu", self.dy, self.WT[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1],
+                        splits=self.splits_out, workspace=self.work, engine=self.engine)
         for l in range(L - 1, -1, -1):
-            rsi.nn_transpose(self.dZ[l], self.dZT[l])
-            rsi.nn_transpose(self.H[l], self.HT[l])
-            rsi.nn_gemm("f32", self.dZT[l], self.HT[l], out_f32=self.gW[l], engine=self.engine)
+            if tc:
+                rsi.nn_gemm("f32", self.dZ[l], self.H[l], out_f32=self.gW[l], engine="tcgen05", a_t=True, b_t=True)
+            else:
+                rsi.nn_transpose(self.dZ[l], self.dZT[l])
+                rsi.nn_transpose(self.H[l], self.HT[l])
+                rsi.nn_gemm("f32", self.dZT[l], self.HT[l], out_f32=self.gW[l], engine=self.engine)
             rsi.nn_colsum(self.dZ[l], self.gb[l])
             if l > 0:
-                rsi.nn_transpose(self.W16[l], self.WT[l])
-                rsi.nn_gemm("dsilu", self.dZ[l], self.WT[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1],
-                            engine=self.engine)
+                if tc:
+                    rsi.nn_gemm("dsilu", self.dZ[l], self.W16[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1],
+                                engine="tcgen05", b_t=True)
+                else:
+                    rsi.nn_transpose(self.W16[l], self.WT[l])
+                    rsi.nn_gemm("dsilu", self.dZ[l], self.WT[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1],
+                                engine=self.engine)
 
     def adam(self, lr: float):
         self.step_count += 1

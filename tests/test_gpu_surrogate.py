@@ -94,6 +94,43 @@ def test_gemm_tcgen05_matches_fp32_reference(M, N, K):
     rsi.sync_status()  # raises if a kernel recorded a timeout
 
 
+@pytest.mark.parametrize("a_t,b_t", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 512, 256), (384, 256, 192)])
+def test_gemm_tcgen05_operand_layouts(M, N, K, a_t, b_t):
+    """Operands read in their stored orientation: A as [K x M], B as [K x N]."""
+    g = torch.Generator(device="cuda").manual_seed(3 * M + N + K + 2 * a_t + b_t)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    aux = torch.randn(M, N, device="cuda", generator=g)
+    ref = A.float() @ B.float().T
+    As = A.T.contiguous() if a_t else A
+    Bs = B.T.contiguous() if b_t else B
+    out = torch.full((M, N), float("nan"), device="cuda")
+    rsi.nn_gemm("f32", As, Bs, out_f32=out, engine="tcgen05", a_t=a_t, b_t=b_t)
+    assert rel(out, ref) < 1e-5
+    o2 = torch.empty_like(out)
+    rsi.nn_gemm("f32", A, B, out_f32=o2, engine="tcgen05")
+    assert rel(out, o2) < 1e-6
+    h = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+    s = torch.sigmoid(aux)
+    rsi.nn_gemm("dsilu", As, Bs, out_bf16=h, aux=aux, engine="tcgen05", a_t=a_t, b_t=b_t)
+    assert rel(h.float(), ref * s * (1 + aux * (1 - s))) < 6e-3
+    splits = K // 64
+    if splits > 1:
+        work = torch.empty(splits * M * N, device="cuda")
+        rsi.nn_gemm("f32", As, Bs, out_f32=out, splits=splits, workspace=work, engine="tcgen05", a_t=a_t, b_t=b_t)
+        assert rel(out, ref) < 1e-5
+    rsi.sync_status()
+
+
+def test_gemm_layout_needs_tcgen05():
+    A = torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda")
+    out = torch.empty(128, 128, device="cuda")
+    with pytest.raises(rsi.RSIError):
+        rsi.nn_gemm("f32", A.T.contiguous(), torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda"),
+                    out_f32=out, engine="mma_sync", a_t=True)
+
+
 def test_transpose_colsum_cast():
     x = torch.randn(300, 70, device="cuda").to(torch.bfloat16)
     t = torch.empty(70, 300, dtype=torch.bfloat16, device="cuda")
