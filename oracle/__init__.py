@@ -96,6 +96,8 @@ def lib():
                 f.argtypes = [ctypes.c_double] * 8 + [_D]
             L.orc_transmit.restype = None
             L.orc_transmit.argtypes = [_I64, ctypes.c_int] + [ctypes.c_double] * 5 + [_D] * 9
+            L.orc_reflect.restype = None
+            L.orc_reflect.argtypes = [_I64, ctypes.c_int] + [ctypes.c_double] * 5 + [_D] * 9
             _lib = L
     return _lib
 
@@ -240,6 +242,29 @@ def transmit(pts: dict, phi, medium_in: dict, medium_out: dict, snell_C: float,
     return sre + 1j * sim, tre + 1j * tim
 
 
+def reflect(pts: dict, phi, medium_in: dict, medium_out: dict, snell_C: float,
+            mode: str = "global"):
+    """Source density of the reflected field, sigma_r = R12 phi (the reflected
+    field on the interface taken as R12 times the incident field, Sec. 2.1);
+    returns (sigma_r, R)."""
+    nx, ny, nz = (_f64(pts[key]) for key in ("nx", "ny", "nz"))
+    phi = np.ascontiguousarray(phi, np.complex128)
+    pre, pim = _f64(phi.real), _f64(phi.imag)
+    n = nx.shape[0]
+    sre, sim, rre, rim = (np.empty(n, np.float64) for _ in range(4))
+    lib().orc_reflect(n, TMODES[mode], float(medium_in["rho"]), float(medium_in["c"]),
+                      float(medium_out["rho"]), float(medium_out["c"]), float(snell_C),
+                      _p(nx), _p(ny), _p(nz), _p(pre), _p(pim), _p(sre), _p(sim),
+                      _p(rre), _p(rim))
+    return sre + 1j * sim, rre + 1j * rim
+
+
+def flip_normals(pts: dict) -> dict:
+    """The same points with every normal reversed (pointing into the medium
+    the field came from)."""
+    return dict(pts, nx=-np.asarray(pts["nx"]), ny=-np.asarray(pts["ny"]), nz=-np.asarray(pts["nz"]))
+
+
 # ---------------------------------------------------------------------------
 # Whole chain: piston -> interfaces -> image (Sec. 2.1, Fig. rayleigh-sommerfeld_integral)
 # ---------------------------------------------------------------------------
@@ -290,3 +315,38 @@ def field_image(cfg: dict, nthreads: int | None = None):
     phi, _ = chain(cfg, None, nthreads)
     k_last = wavenumber(cfg["freq"], cfg["media"][len(cfg["interfaces"])]["c"])
     return (k_last / float(cfg.get("v0", 1.0))) * phi.reshape(int(g["nz"]), int(g["nx"]))
+
+
+def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False):
+    """Full field of a one-interface workload on both sides (Fig.
+    rayleigh-sommerfeld_integral): in medium 1 the incident field (Eq.
+    incident_field) plus the reflected field, the first Rayleigh-Sommerfeld
+    solution over the interface with source density R12 phi_i, wave number
+    k1 and normals pointing back into medium 1; in medium 2 the transmitted
+    field (Eq. approximated_transmitted_field).  cfg["grid_water"] and
+    cfg["grid_solid"] are the medium-1 and medium-2 windows (same nx).
+
+    Returns the normalised image k phi / v0, shape [nz_w + nz_s][nx] (medium-1
+    rows first), or with parts=True a dict of its fields."""
+    seed = int(cfg.get("seed", 0))
+    freq, v0 = float(cfg["freq"]), float(cfg.get("v0", 1.0))
+    m = cfg["media"]
+    C = snell_invariant(cfg)
+    mode = cfg.get("tmode", "global")
+    k1, k2 = wavenumber(freq, m[0]["c"]), wavenumber(freq, m[1]["c"])
+    pc, it = cfg["piston"], cfg["interfaces"][0]
+    piston = make_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]))
+    iface = make_points(it, seed, int(it["set_id"]), int(it["n"]))
+    gw, gs = grid_points(cfg["grid_water"]), grid_points(cfg["grid_solid"])
+    phi_if = piston_field(piston, iface, k1, v0, nthreads)
+    sig_t, _ = transmit(iface, phi_if, m[0], m[1], C, mode)
+    sig_r, _ = reflect(iface, phi_if, m[0], m[1], C, mode)
+    phi_inc = piston_field(piston, gw, k1, v0, nthreads)
+    phi_ref = rsi_field(flip_normals(iface), sig_r, gw, k1, nthreads)
+    phi_tr = rsi_field(iface, sig_t, gs, k2, nthreads)
+    if parts:
+        return {"interface": phi_if, "incident": phi_inc, "reflected": phi_ref, "transmitted": phi_tr}
+    w, sg = cfg["grid_water"], cfg["grid_solid"]
+    top = (k1 / v0) * (phi_inc + phi_ref).reshape(int(w["nz"]), int(w["nx"]))
+    bot = (k2 / v0) * phi_tr.reshape(int(sg["nz"]), int(sg["nx"]))
+    return np.concatenate([top, bot], axis=0)

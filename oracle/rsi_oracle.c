@@ -32,6 +32,11 @@
  *                      invariant of Eq. root_searching; the source density of
  *                      Eq. approximated_transmitted_field is T12 * phi_i since
  *                      (rho1/rho2)(1+R12) = T12 (Eq. reflection_coefficient).
+ *   orc_reflect        source density of the reflected field in medium 1,
+ *                      R12 * phi_i: the plane-wave approximation of the
+ *                      reflected field on the interface (Sec. 2.1, with
+ *                      Eq. reflection_coefficient), same incidence angles as
+ *                      orc_transmit.
  *   orc_rsi_field      first Rayleigh-Sommerfeld solution, Eq. rayleigh_sommerfeld
  *                      (Sec. 2.1), over weighted source points; the sign of
  *                      its bracket is read as explained at rsi_range().
@@ -452,5 +457,44 @@ void orc_transmit(int64_t n, int mode, double rho1, double c1, double rho2, doub
             T_re[i] = creal(T);
         if (T_im)
             T_im[i] = cimag(T);
+    }
+}
+
+/* Source density of the reflected field, sigma_i = R12(alpha1_i) phi_i(P_i)
+ * (the reflected field on the interface is taken as R12 times the incident
+ * field, Sec. 2.1; R12 from Eq. reflection_coefficient).  The incidence
+ * angles follow the same two modes as orc_transmit.  Writes R (re, im) when
+ * R_re/R_im are non-NULL.                                                   */
+void orc_reflect(int64_t n, int mode, double rho1, double c1, double rho2, double c2,
+                 double snell_C, const double *nx, const double *ny, const double *nz,
+                 const double *phi_re, const double *phi_im,
+                 double *sig_re, double *sig_im, double *R_re, double *R_im)
+{
+    double s1g = c1 * snell_C;
+    double dxv = s1g, dyv = 0.0, dzv = sqrt(fmax(0.0, 1.0 - s1g * s1g));
+    for (int64_t i = 0; i < n; ++i) {
+        double complex cos1, cos2;
+        if (mode == 0) {
+            cos1 = cos_from_sin(c1 * snell_C);
+            cos2 = cos_from_sin(c2 * snell_C);
+        } else {
+            double c = dxv * nx[i] + dyv * ny[i] + dzv * nz[i];
+            if (c < 0.0)
+                c = 0.0;
+            if (c > 1.0)
+                c = 1.0;
+            double s = sqrt(1.0 - c * c);
+            cos1 = c;
+            cos2 = cos_from_sin(c2 / c1 * s);
+        }
+        double complex R = orc_R12(rho1, c1, rho2, c2, cos1, cos2);
+        double complex phi = phi_re[i] + I * phi_im[i];
+        double complex sig = R * phi;
+        sig_re[i] = creal(sig);
+        sig_im[i] = cimag(sig);
+        if (R_re)
+            R_re[i] = creal(R);
+        if (R_im)
+            R_im[i] = cimag(R);
     }
 }

@@ -333,3 +333,70 @@ def test_field_image_is_normalised_chain():
     phi, _ = oracle.chain(cfg)
     assert img.shape == (3, 5)
     assert np.allclose(img.ravel(), oracle.wavenumber(3e6, 5900.0) / 2.0 * phi, rtol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# reflected field in medium 1 (Sec. 2.1, plane-wave reflection approximation)
+# ---------------------------------------------------------------------------
+def test_reflection_from_a_denser_plane_is_the_scaled_image_source():
+    # Equal sound speeds, rho2 = 3 rho1: R12 = (rho2 - rho1)/(rho2 + rho1) = 1/2
+    # at every angle.  A point source at z = -d below the plane z = 0 leaves
+    # the reflected value R12 e^{ikR}/R on the plane; the first
+    # Rayleigh-Sommerfeld solution with the normal pointing back into medium 1
+    # reproduces the outgoing field of the mirror source at z = +d, times R12,
+    # everywhere in z < 0.  Keeping the stored +z normal gives exactly the
+    # negative, so the reversed normals are what this pins.
+    k = 2 * np.pi / 1e-3
+    d = 4e-3
+    src = plane_quadrature(0.03, 0.75e-3, 12, window=(0.012, 0.03))
+    R = np.sqrt(src["x"] ** 2 + src["y"] ** 2 + d * d)
+    phi_i = np.exp(1j * k * R) / R
+    m1, m2 = {"rho": 1000.0, "c": 1480.0}, {"rho": 3000.0, "c": 1480.0}
+    sig_r, Rc = oracle.reflect(src, phi_i, m1, m2, math.sin(0.3) / 1480.0, "global")
+    assert np.allclose(Rc, 0.5, atol=1e-15)
+    tq = np.array([[0, 0, -5e-3], [3e-3, 2e-3, -10e-3], [0, 0, -0.4e-3], [1e-3, 0, -1.5e-3]])
+    got = oracle.rsi_field(oracle.flip_normals(src), sig_r, points(tq), k)
+    Rq = np.sqrt(tq[:, 0] ** 2 + tq[:, 1] ** 2 + (tq[:, 2] - d) ** 2)
+    want = 0.5 * np.exp(1j * k * Rq) / Rq
+    assert np.max(np.abs(got - want) / np.abs(want)) < 1e-6
+    unflipped = oracle.rsi_field(src, sig_r, points(tq), k)
+    assert np.allclose(unflipped, -got, rtol=1e-12, atol=0)
+
+
+def test_reflection_coefficient_matches_its_closed_forms():
+    # Normal incidence: R12 = (Z2 - Z1)/(Z2 + Z1); past the critical angle
+    # |R12| = 1; and 1 + R12 = (rho2/rho1) T12 (Eq. reflection_coefficient
+    # against Eq. transmission_coefficient), point by point.
+    w, st = {"rho": 1000.0, "c": 1480.0}, {"rho": 7800.0, "c": 5900.0}
+    pts = {"nx": np.zeros(3), "ny": np.zeros(3), "nz": np.ones(3)}
+    phi = np.array([1.0, 2.0 - 1.0j, 0.5j])
+    sig, R = oracle.reflect(pts, phi, w, st, 0.0, "global")
+    z1, z2 = 1000.0 * 1480.0, 7800.0 * 5900.0
+    assert np.allclose(R, (z2 - z1) / (z2 + z1), rtol=1e-15)
+    assert np.allclose(sig, R * phi, rtol=1e-15)
+    C = math.sin(math.radians(20.0)) / 1480.0  # beyond the first critical angle (14.5 deg)
+    _, Rp = oracle.reflect(pts, phi, w, st, C, "global")
+    assert np.allclose(np.abs(Rp), 1.0, rtol=1e-14)
+    for C in (0.0, math.sin(math.radians(7.0)) / 1480.0, math.sin(math.radians(20.0)) / 1480.0):
+        _, Rr = oracle.reflect(pts, phi, w, st, C, "global")
+        _, T = oracle.transmit(pts, phi, w, st, C, "global")
+        assert np.allclose(1.0 + Rr, (7800.0 / 1000.0) * T, rtol=1e-14)
+
+
+def test_two_medium_matched_media_reflect_nothing():
+    # Identical media: R12 = 0, so medium 1 holds the incident field alone and
+    # medium 2 is the single-interface chain of the same points.
+    from paper_2408_06765_gb300 import workloads as W
+    cfg = W.f1_small()
+    cfg["media"] = [dict(W.WATER), dict(W.WATER)]
+    cfg["piston"]["n"], cfg["interfaces"][0]["n"] = 600, 900
+    parts = oracle.two_medium(cfg, parts=True)
+    assert np.all(parts["reflected"] == 0)
+    img = oracle.two_medium(cfg)
+    gw, gs = cfg["grid_water"], cfg["grid_solid"]
+    k = oracle.wavenumber(cfg["freq"], 1480.0)
+    pist = oracle.make_points(dict(cfg["piston"], kind="disk"), 0, 0, 600)
+    direct = oracle.piston_field(pist, oracle.grid_points(gw), k)
+    assert np.array_equal(img[: gw["nz"]], k * direct.reshape(gw["nz"], gw["nx"]))
+    below, _ = oracle.chain(dict(cfg, grid=gs))
+    assert np.array_equal(img[gw["nz"]:], k * below.reshape(gs["nz"], gs["nx"]))
