@@ -132,8 +132,12 @@ enum rsi_precision {
                           compensated accumulation across tiles              */
 };
 enum rsi_normals {
-    RSI_NORMALS_Z = 0,     /* every source normal is +z (flat interface)       */
-    RSI_NORMALS_POINTS = 1 /* use the per-point normals                         */
+    RSI_NORMALS_Z = 0,          /* every source normal is +z (flat interface)  */
+    RSI_NORMALS_POINTS = 1,     /* use the per-point normals                    */
+    RSI_NORMALS_NEG_Z = 2,      /* every source normal is -z: a flat interface
+                                   radiating back into the medium the field
+                                   came from (the reflected field, Sec. 2.1)   */
+    RSI_NORMALS_POINTS_NEG = 3  /* the per-point normals reversed              */
 };
 
 typedef struct rsi_stage {
@@ -212,6 +216,16 @@ typedef struct rsi_interface {
 int rsi_interface_transmit(const rsi_interface *it, const void *points, int64_t n,
                            const double *phi, double *sigma, void *stream);
 
+/* Source density of the reflected field in medium 1: sigma[i] = R12(a1_i)
+ * phi[i], the reflected field on the interface taken as R12 times the
+ * incident field (Sec. 2.1), R12 of Eq. reflection_coefficient,
+ *   R12 = (rho2 c2 cos a1 - rho1 c1 cos a2) / (rho2 c2 cos a1 + rho1 c1 cos a2),
+ * with the same incidence angles, modes and arguments as
+ * rsi_interface_transmit.  It radiates into medium 1 through
+ * rsi_propagate_stage (RSI, k of medium 1, normals reversed).               */
+int rsi_interface_reflect(const rsi_interface *it, const void *points, int64_t n,
+                          const double *phi, double *sigma, void *stream);
+
 /* ---- field image (step a7) ------------------------------------------------- */
 enum rsi_image_format {
     RSI_IMG_C128 = 0, /* complex double [nz][nx]                                */
@@ -222,6 +236,12 @@ enum rsi_image_format {
  * velocity amplitude k phi / v0 of Fig. oblique_incidence).                */
 int rsi_field_image(const rsi_grid *g, const double *field, double k, double v0,
                     int32_t format, void *out, void *stream);
+/* out[j] = (k / v0) (field_a[j] + field_b[j]): the image of a medium holding
+ * two fields at once, e.g. the incident plus the reflected field in medium 1
+ * (Fig. rayleigh-sommerfeld_integral).  field_b may be NULL (then as
+ * rsi_field_image).                                                        */
+int rsi_field_image_sum(const rsi_grid *g, const double *field_a, const double *field_b, double k,
+                        double v0, int32_t format, void *out, void *stream);
 
 /* ---- autotuning of the launch shape --------------------------------------- */
 /* Times the FP32C launch shapes of one stage on the given data -- tile size

@@ -317,7 +317,7 @@ def field_image(cfg: dict, nthreads: int | None = None):
     return (k_last / float(cfg.get("v0", 1.0))) * phi.reshape(int(g["nz"]), int(g["nx"]))
 
 
-def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False):
+def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False, pixels=None):
     """Full field of a one-interface workload on both sides (Fig.
     rayleigh-sommerfeld_integral): in medium 1 the incident field (Eq.
     incident_field) plus the reflected field, the first Rayleigh-Sommerfeld
@@ -327,7 +327,8 @@ def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False):
     cfg["grid_solid"] are the medium-1 and medium-2 windows (same nx).
 
     Returns the normalised image k phi / v0, shape [nz_w + nz_s][nx] (medium-1
-    rows first), or with parts=True a dict of its fields."""
+    rows first), with `pixels` (flat indices into that image) only those
+    values, or with parts=True a dict of its fields."""
     seed = int(cfg.get("seed", 0))
     freq, v0 = float(cfg["freq"]), float(cfg.get("v0", 1.0))
     m = cfg["media"]
@@ -338,6 +339,12 @@ def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False):
     piston = make_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]))
     iface = make_points(it, seed, int(it["set_id"]), int(it["n"]))
     gw, gs = grid_points(cfg["grid_water"]), grid_points(cfg["grid_solid"])
+    n_w = int(cfg["grid_water"]["nx"]) * int(cfg["grid_water"]["nz"])
+    if pixels is not None:
+        pixels = np.asarray(pixels, np.int64)
+        pw, ps = pixels[pixels < n_w], pixels[pixels >= n_w] - n_w
+        gw = {key: gw[key][pw] for key in ("x", "y", "z")}
+        gs = {key: gs[key][ps] for key in ("x", "y", "z")}
     phi_if = piston_field(piston, iface, k1, v0, nthreads)
     sig_t, _ = transmit(iface, phi_if, m[0], m[1], C, mode)
     sig_r, _ = reflect(iface, phi_if, m[0], m[1], C, mode)
@@ -346,6 +353,8 @@ def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False):
     phi_tr = rsi_field(iface, sig_t, gs, k2, nthreads)
     if parts:
         return {"interface": phi_if, "incident": phi_inc, "reflected": phi_ref, "transmitted": phi_tr}
+    if pixels is not None:  # pixels are sorted: medium-1 values first
+        return np.concatenate([(k1 / v0) * (phi_inc + phi_ref), (k2 / v0) * phi_tr])
     w, sg = cfg["grid_water"], cfg["grid_solid"]
     top = (k1 / v0) * (phi_inc + phi_ref).reshape(int(w["nz"]), int(w["nx"]))
     bot = (k2 / v0) * phi_tr.reshape(int(sg["nz"]), int(sg["nx"]))

@@ -31,9 +31,11 @@ __device__ __forceinline__ Cplx cos_of_sin(double s) {
     return {0.0, sqrt(-q)};
 }
 
-// sigma = T12 phi at a point with unit normal (nx, ny, nz)
-__device__ __forceinline__ double2 transmit_point(const rsi_interface& it, double nx, double nz, double2 phi) {
-    Cplx cos1, cos2;
+// cosines of the incidence and refraction angles at a point with unit
+// normal (nx, ny, nz): one angle per interface (global) or against the local
+// normal (local)
+__device__ __forceinline__ void incidence_cosines(const rsi_interface& it, double nx, double nz, Cplx& cos1,
+                                                  Cplx& cos2) {
     if (it.mode == RSI_T_GLOBAL) {
         cos1 = cos_of_sin(it.c1 * it.snell_C);
         cos2 = cos_of_sin(it.c2 * it.snell_C);
@@ -46,12 +48,31 @@ __device__ __forceinline__ double2 transmit_point(const rsi_interface& it, doubl
         cos1 = {c, 0.0};
         cos2 = cos_of_sin(it.c2 / it.c1 * sqrt(1.0 - c * c));
     }
+}
+
+// sigma = T12 phi at a point with unit normal (nx, ny, nz)
+__device__ __forceinline__ double2 transmit_point(const rsi_interface& it, double nx, double nz, double2 phi) {
+    Cplx cos1, cos2;
+    incidence_cosines(it, nx, nz, cos1, cos2);
     // T12 = 2 rho1 c2 cos a1 / (rho2 c2 cos a1 + rho1 c1 cos a2)
     Cplx num = {2.0 * it.rho1 * it.c2 * cos1.re, 2.0 * it.rho1 * it.c2 * cos1.im};
     Cplx den = {it.rho2 * it.c2 * cos1.re + it.rho1 * it.c1 * cos2.re,
                 it.rho2 * it.c2 * cos1.im + it.rho1 * it.c1 * cos2.im};
     Cplx T = cdiv(num, den);
     Cplx s = cmul(T, {phi.x, phi.y});
+    return make_double2(s.re, s.im);
+}
+
+// sigma = R12 phi at a point (Eq. reflection_coefficient), the reflected
+// field's value on the interface
+__device__ __forceinline__ double2 reflect_point(const rsi_interface& it, double nx, double nz, double2 phi) {
+    Cplx cos1, cos2;
+    incidence_cosines(it, nx, nz, cos1, cos2);
+    // R12 = (rho2 c2 cos a1 - rho1 c1 cos a2) / (rho2 c2 cos a1 + rho1 c1 cos a2)
+    const Cplx a = {it.rho2 * it.c2 * cos1.re, it.rho2 * it.c2 * cos1.im};
+    const Cplx b = {it.rho1 * it.c1 * cos2.re, it.rho1 * it.c1 * cos2.im};
+    const Cplx R = cdiv({a.re - b.re, a.im - b.im}, {a.re + b.re, a.im + b.im});
+    Cplx s = cmul(R, {phi.x, phi.y});
     return make_double2(s.re, s.im);
 }
 

@@ -124,7 +124,7 @@ int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p) {
         return rsi_fail(RSI_E_INVAL, "unknown stage kind %d", st.kind);
     if (st.precision != RSI_PREC_FP64 && st.precision != RSI_PREC_FP32C)
         return rsi_fail(RSI_E_INVAL, "unknown precision %d", st.precision);
-    if (st.kind == RSI_STAGE_RSI && st.normals != RSI_NORMALS_Z && st.normals != RSI_NORMALS_POINTS)
+    if (st.kind == RSI_STAGE_RSI && (st.normals < RSI_NORMALS_Z || st.normals > RSI_NORMALS_POINTS_NEG))
         return rsi_fail(RSI_E_INVAL, "unknown normals mode %d", st.normals);
     if (n_src < 1 || n_tgt < 1) return rsi_fail(RSI_E_INVAL, "empty source or target set");
     if (n_src > (int64_t(1) << 31) || n_tgt > (int64_t(1) << 31))
@@ -158,7 +158,8 @@ int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p) {
         p.variant = 0;
     }
     p.n_tiles = int((n_src + p.S - 1) / p.S);
-    p.tile_bytes = RSI_TILE_HDR_BYTES + size_t(p.S) * (fp32 ? fp32_record_bytes(st.kind, st.normals) : fp64_record_bytes());
+    p.tile_bytes = RSI_TILE_HDR_BYTES +
+                   size_t(p.S) * (fp32 ? fp32_record_bytes(st.kind, base_normals(st.normals)) : fp64_record_bytes());
     p.tiles_bytes = align256(size_t(p.n_tiles) * p.tile_bytes);
 
     const int threads = fp32 ? fp32_threads() : fp64_threads();
@@ -239,7 +240,7 @@ extern "C" int rsi_propagate_stage(const rsi_stage* st, const void* src_points, 
 
     StageArgs a = {};
     a.kind = st->kind;
-    a.normals = st->kind == RSI_STAGE_RSI ? st->normals : RSI_NORMALS_Z;
+    a.normals = st->kind == RSI_STAGE_RSI ? base_normals(st->normals) : RSI_NORMALS_Z;
     a.tpt = p.tpt;
     a.variant = p.variant;
     a.S = p.S;
@@ -310,7 +311,8 @@ extern "C" int rsi_autotune_stage(const rsi_stage* st, const void* src_points, i
         *best = base;
         return RSI_OK;
     }
-    const auto key = std::make_tuple(st->kind, st->kind == RSI_STAGE_RSI ? st->normals : 0, ceil_log2(n_src),
+    const auto key = std::make_tuple(st->kind, st->kind == RSI_STAGE_RSI ? base_normals(st->normals) : 0,
+                                     ceil_log2(n_src),
                                      ceil_log2(n_tgt));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);

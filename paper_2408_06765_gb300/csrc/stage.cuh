@@ -52,7 +52,14 @@ struct StageArgs {
 };
 
 size_t fp32_record_bytes(int kind, int normals);
-double stage_amp_scale(const rsi_stage& st);  // -v0/(2 pi) (piston) or -1/(2 pi) (RSI)
+double stage_amp_scale(const rsi_stage& st);  // -v0/(2 pi) (piston) or -+1/(2 pi) (RSI)
+// Reversed normals (RSI_NORMALS_NEG_Z, RSI_NORMALS_POINTS_NEG): cos(theta) is
+// linear in the normal, so the kernels run with the stored normals and the
+// sign goes into the source amplitudes (stage_amp_scale).
+inline int base_normals(int n) {
+    return n == RSI_NORMALS_NEG_Z ? RSI_NORMALS_Z : n == RSI_NORMALS_POINTS_NEG ? RSI_NORMALS_POINTS : n;
+}
+inline double normals_sign(int n) { return (n == RSI_NORMALS_NEG_Z || n == RSI_NORMALS_POINTS_NEG) ? -1.0 : 1.0; }
 size_t fp64_record_bytes();
 
 int launch_prep_fp32(const rsi_stage& st, const PointsView& src, int64_t n_src, const double2* sigma,

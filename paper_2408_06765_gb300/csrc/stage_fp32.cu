@@ -92,12 +92,13 @@ size_t fp32_record_bytes(int kind, int normals) {
 int fp32_threads() { return kThreads; }
 
 double stage_amp_scale(const rsi_stage& st) {
-    return (st.kind == RSI_STAGE_PISTON) ? -st.v0 / (2.0 * M_PI) : -1.0 / (2.0 * M_PI);
+    return (st.kind == RSI_STAGE_PISTON) ? -st.v0 / (2.0 * M_PI) : -normals_sign(st.normals) / (2.0 * M_PI);
 }
 
 int launch_prep_fp32(const rsi_stage& st, const PointsView& src, int64_t n_src, const double2* sigma, int S,
                      uint8_t* tiles, size_t tile_bytes, int n_tiles, cudaStream_t s) {
-    prep_fp32_kernel<<<n_tiles, S, 0, s>>>(st.kind, st.normals, n_src, src, sigma, stage_amp_scale(st), st.k, tiles,
+    const int normals = st.kind == RSI_STAGE_RSI ? base_normals(st.normals) : RSI_NORMALS_Z;
+    prep_fp32_kernel<<<n_tiles, S, 0, s>>>(st.kind, normals, n_src, src, sigma, stage_amp_scale(st), st.k, tiles,
                                            tile_bytes);
     RSI_CHECK_LAUNCH("prep_fp32_kernel");
     return RSI_OK;

@@ -189,12 +189,13 @@ int fp64_threads() { return kThreads; }
 
 int launch_prep_fp64(const rsi_stage& st, const PointsView& src, int64_t n_src, const double2* sigma, int S,
                      uint8_t* tiles, size_t tile_bytes, int n_tiles, cudaStream_t s) {
-    double amp_scale = (st.kind == RSI_STAGE_PISTON) ? -st.v0 / (2.0 * M_PI) : -1.0 / (2.0 * M_PI);
+    const double amp_scale = stage_amp_scale(st);
+    const int normals = st.kind == RSI_STAGE_RSI ? base_normals(st.normals) : RSI_NORMALS_Z;
     int64_t n_slots = int64_t(n_tiles) * S;
     int threads = 256;
     unsigned blocks = unsigned((n_slots + threads - 1) / threads);
-    prep_fp64_kernel<<<blocks, threads, 0, s>>>(st.kind, st.normals, n_src, src, sigma, amp_scale, tiles,
-                                                tile_bytes, n_slots);
+    prep_fp64_kernel<<<blocks, threads, 0, s>>>(st.kind, normals, n_src, src, sigma, amp_scale, tiles, tile_bytes,
+                                                n_slots);
     RSI_CHECK_LAUNCH("prep_fp64_kernel");
     return RSI_OK;
 }

@@ -29,14 +29,14 @@ PF_DTYPE = {**{k: torch.int32 for k in ("IDX", "SU", "SV")},
 SURF = {"disk": 0, "rect": 1, "cyl": 2}
 STAGE_PISTON, STAGE_RSI = 0, 1
 PREC = {"fp64": 0, "fp32c": 1}
-NORMALS_Z, NORMALS_POINTS = 0, 1
+NORMALS_Z, NORMALS_POINTS, NORMALS_NEG_Z, NORMALS_POINTS_NEG = 0, 1, 2, 3
 TMODE = {"global": 0, "local": 1}
 IMG = {"c128": 0, "c64": 1, "abs32": 2}
 
 SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes",
            "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points",
            "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_interface_transmit",
-           "rsi_field_image", "rsi_launch_count", "rsi_timing_enable", "rsi_timing_read",
+           "rsi_interface_reflect", "rsi_field_image", "rsi_field_image_sum", "rsi_launch_count", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
            "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier",
@@ -112,6 +112,9 @@ def load(path: str | None = None):
         L.rsi_interface_transmit.argtypes = [ctypes.POINTER(Interface), vp, i64, vp, vp, vp]
         L.rsi_field_image.argtypes = [ctypes.POINTER(Grid), vp, ctypes.c_double, ctypes.c_double,
                                       i32, vp, vp]
+        L.rsi_interface_reflect.argtypes = [ctypes.POINTER(Interface), vp, i64, vp, vp, vp]
+        L.rsi_field_image_sum.argtypes = [ctypes.POINTER(Grid), vp, vp, ctypes.c_double, ctypes.c_double,
+                                          i32, vp, vp]
         L.rsi_launch_count.restype = u64
         L.rsi_timing_enable.argtypes = [i32]
         L.rsi_timing_read.argtypes = [i32, ctypes.POINTER(ctypes.c_double),
@@ -279,14 +282,26 @@ def interface_transmit(pts: Points, phi, m_in: dict, m_out: dict, snell_C: float
     return out
 
 
+def interface_reflect(pts: Points, phi, m_in: dict, m_out: dict, snell_C: float,
+                      mode: str = "global", out=None, stream=None) -> torch.Tensor:
+    """sigma_r = R12 phi: the reflected field's source density (rsi_interface_reflect)."""
+    if out is None:
+        out = torch.empty_like(phi)
+    it = interface_struct(m_in, m_out, snell_C, mode)
+    _check(load().rsi_interface_reflect(ctypes.byref(it), pts.ptr(), pts.n, _ptr(phi), _ptr(out),
+                                        _stream(stream)), "rsi_interface_reflect")
+    return out
+
+
 def field_image(g: dict, field, k: float, v0: float = 1.0, fmt: str = "c128", out=None,
-                stream=None) -> torch.Tensor:
+                stream=None, field_b=None) -> torch.Tensor:
+    """(k / v0) (field + field_b) on the grid, [nz][nx]; field_b optional."""
     G = grid_struct(g)
     if out is None:
         dt = {"c128": torch.complex128, "c64": torch.complex64, "abs32": torch.float32}[fmt]
         out = torch.empty((G.nz, G.nx), dtype=dt, device=field.device)
-    _check(load().rsi_field_image(ctypes.byref(G), _ptr(field), float(k), float(v0), IMG[fmt],
-                                  _ptr(out), _stream(stream)), "rsi_field_image")
+    _check(load().rsi_field_image_sum(ctypes.byref(G), _ptr(field), _ptr(field_b), float(k), float(v0),
+                                      IMG[fmt], _ptr(out), _stream(stream)), "rsi_field_image_sum")
     return out
 
 
@@ -386,6 +401,63 @@ def run_chain(cfg: dict, precision: str | None = None, targets: Points | None = 
         k_last = wavenumber(freq, media[len(ifaces)]["c"])
         image = field_image(cfg["grid"], phi, k_last, v0, fmt, stream=stream)
     return ChainResult(image, phi, kept)
+
+
+class TwoMediumResult:
+    def __init__(self, image, parts):
+        self.image = image  # [nz_w + nz_s][nx], medium-1 rows first
+        self.parts = parts  # dict of the fields on the interface and the two windows
+
+
+def run_two_medium(cfg: dict, precision: str | None = None, fmt: str = "c128",
+                   workspace: Workspace | None = None, stage_opts: dict | None = None, stream=None,
+                   device="cuda") -> TwoMediumResult:
+    """Both media of a one-interface workload (Fig. rayleigh-sommerfeld_integral):
+    incident + reflected field in the medium-1 window cfg["grid_water"],
+    transmitted field in the medium-2 window cfg["grid_solid"], written into
+    one image (medium-1 rows first)."""
+    prec = precision or cfg.get("precision", "fp32c")
+    opts = stage_opts or {}
+    ws = workspace or Workspace(device)
+    seed = int(cfg.get("seed", 0))
+    freq, v0 = float(cfg["freq"]), float(cfg.get("v0", 1.0))
+    m = cfg["media"]
+    C = snell_invariant(cfg)
+    mode = cfg.get("tmode", "global")
+    k1, k2 = wavenumber(freq, m[0]["c"]), wavenumber(freq, m[1]["c"])
+    pc, it = cfg["piston"], cfg["interfaces"][0]
+    piston = make_qmc_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]),
+                             device=device, stream=stream)
+    iface = make_qmc_points(it, seed, int(it["set_id"]), int(it["n"]), device=device, stream=stream)
+    gw_cfg, gs_cfg = cfg["grid_water"], cfg["grid_solid"]
+    gw = grid_points(gw_cfg, device=device, stream=stream)
+    gs = grid_points(gs_cfg, device=device, stream=stream)
+    flat = it["kind"] == "rect"
+    st1 = stage_struct(STAGE_PISTON, prec, k1, v0, **opts)
+    phi_if = propagate_stage(st1, piston, None, iface, workspace=ws, stream=stream)
+    phi_inc = propagate_stage(st1, piston, None, gw, workspace=ws, stream=stream)
+    sig_r = interface_reflect(iface, phi_if, m[0], m[1], C, mode, stream=stream)
+    st_r = stage_struct(STAGE_RSI, prec, k1, 1.0, NORMALS_NEG_Z if flat else NORMALS_POINTS_NEG, **opts)
+    phi_ref = propagate_stage(st_r, iface, sig_r, gw, workspace=ws, stream=stream)
+    sig_t = interface_transmit(iface, phi_if, m[0], m[1], C, mode, stream=stream)
+    st_t = stage_struct(STAGE_RSI, prec, k2, 1.0, NORMALS_Z if flat else NORMALS_POINTS, **opts)
+    phi_tr = propagate_stage(st_t, iface, sig_t, gs, workspace=ws, stream=stream)
+    dt = {"c128": torch.complex128, "c64": torch.complex64, "abs32": torch.float32}[fmt]
+    nw, ns = int(gw_cfg["nz"]), int(gs_cfg["nz"])
+    image = torch.empty((nw + ns, int(gw_cfg["nx"])), dtype=dt, device=device)
+    field_image(gw_cfg, phi_inc, k1, v0, fmt, out=image[:nw], stream=stream, field_b=phi_ref)
+    field_image(gs_cfg, phi_tr, k2, v0, fmt, out=image[nw:], stream=stream)
+    parts = {"interface": phi_if, "incident": phi_inc, "reflected": phi_ref, "transmitted": phi_tr}
+    return TwoMediumResult(image, parts)
+
+
+def two_medium_pairs(cfg: dict) -> int:
+    """Pair terms of run_two_medium: piston -> interface, piston -> medium-1
+    window, interface -> medium-1 window, interface -> medium-2 window."""
+    n_p, n_i = int(cfg["piston"]["n"]), int(cfg["interfaces"][0]["n"])
+    n_w = int(cfg["grid_water"]["nx"]) * int(cfg["grid_water"]["nz"])
+    n_s = int(cfg["grid_solid"]["nx"]) * int(cfg["grid_solid"]["nz"])
+    return n_p * n_i + n_p * n_w + n_i * n_w + n_i * n_s
 
 
 # ---------------------------------------------------------------------------

@@ -81,7 +81,7 @@ def c2_all() -> list[dict]:
 
 def f1_two_medium(freq: float = 5.0 * MHZ, tilt_deg: float = 10.0, n_piston: int = 1 << 16,
                   n_iface: int = 1 << 18, nx: int = 512, nz_water: int = 256, nz_solid: int = 256,
-                  half_width: float = 40 * MM, depth: float = 30 * MM) -> dict:
+                  half_width: float = 40 * MM, depth: float = 30 * MM, patch: float = 80 * MM) -> dict:
     """Both sides of c2's interface: the 6.35 mm piston tilted by 10 degrees,
     water -> steel at z = 50 mm, 2^16 piston points and 2^18 points on an
     80 x 80 mm patch centred where the axis meets the interface; the image
@@ -97,7 +97,7 @@ def f1_two_medium(freq: float = 5.0 * MHZ, tilt_deg: float = 10.0, n_piston: int
         "piston": {"a": 6.35 * MM, "centre": (0.0, 0.0, 0.0), "tilt": tilt, "n": int(n_piston),
                    "set_id": 0},
         "media": [dict(WATER), dict(STEEL)],
-        "interfaces": [_rect((xc, 0.0, zi), 80 * MM, n_iface, 1)],
+        "interfaces": [_rect((xc, 0.0, zi), patch, n_iface, 1)],
         "tmode": "global",
         "grid_water": {"x0": -half_width, "x1": half_width, "nx": int(nx), "z0": zi - depth, "z1": zi,
                        "nz": int(nz_water), "y": 0.0},
@@ -107,10 +107,11 @@ def f1_two_medium(freq: float = 5.0 * MHZ, tilt_deg: float = 10.0, n_piston: int
 
 
 def f1_small() -> dict:
-    """f1 at sizes the oracle finishes in a second: ragged point counts and
-    an image of 48 x (20 + 24) pixels."""
-    return f1_two_medium(n_piston=3000, n_iface=5000, nx=48, nz_water=20, nz_solid=24,
-                         half_width=20 * MM, depth=10 * MM)
+    """f1 at sizes the oracle finishes in a second, still resolving the
+    water wavelength on the interface (2.25 MHz, 12 000 points on 40 mm):
+    ragged point counts and an image of 48 x (20 + 24) pixels."""
+    return f1_two_medium(freq=2.25 * MHZ, n_piston=3000, n_iface=12000, nx=48, nz_water=20, nz_solid=24,
+                         half_width=15 * MM, depth=10 * MM, patch=40 * MM)
 
 
 C3_TOP = 30 * MM

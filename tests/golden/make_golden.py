@@ -7,8 +7,10 @@ pixel indices and normalised values k phi / v0 as JSON text:
 
     python tests/golden/make_golden.py [name ...]
 
-Workloads: c2 at 2.25, 5 and 10 MHz (2^16 x 2^18 points, 512^2 image) and the
-multilayer c3 workload, flat and curved (9 interfaces of 2^16 points).
+Workloads: c2 at 2.25, 5 and 10 MHz (2^16 x 2^18 points, 512^2 image), the
+multilayer c3 workload, flat and curved (9 interfaces of 2^16 points), and the
+two-medium image f1 (incident + reflected field above the interface,
+transmitted field below, oracle.two_medium).
 """
 from __future__ import annotations
 
@@ -33,7 +35,23 @@ def cases():
     out = {f"c2_{f / 1e6:g}MHz": W.c2_full_image(f) for f in W.C2_FREQS}
     out["c3_flat"] = W.c3_multilayer(curved=False)
     out["c3_curved"] = W.c3_multilayer(curved=True)
+    out["f1_5MHz"] = W.f1_two_medium()
     return out
+
+
+def make_two_medium(name: str, cfg: dict):
+    gw, gs = cfg["grid_water"], cfg["grid_solid"]
+    n_pix = int(gw["nx"]) * (int(gw["nz"]) + int(gs["nz"]))
+    rng = np.random.default_rng(1234)
+    pix = np.sort(rng.choice(n_pix, N_PIXELS, replace=False))
+    t0 = time.time()
+    val = oracle.two_medium(cfg, pixels=pix)
+    rec = {"workload": name, "source": "oracle.two_medium (FP64 CPU oracle), tests/golden/make_golden.py",
+           "pixels": pix.tolist(), "re": val.real.tolist(), "im": val.imag.tolist(),
+           "oracle_seconds": time.time() - t0}
+    with open(os.path.join(HERE, f"{name}.json"), "w") as f:
+        json.dump(rec, f)
+    print(f"{name}: {time.time() - t0:.1f} s", flush=True)
 
 
 def make(name: str, cfg: dict):
@@ -59,4 +77,4 @@ if __name__ == "__main__":
     want = sys.argv[1:]
     for name, cfg in cases().items():
         if not want or name in want:
-            make(name, cfg)
+            (make_two_medium if "grid_water" in cfg else make)(name, cfg)
