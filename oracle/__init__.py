@@ -96,6 +96,11 @@ def lib():
                 f.argtypes = [ctypes.c_double] * 8 + [_D]
             L.orc_transmit.restype = None
             L.orc_transmit.argtypes = [_I64, ctypes.c_int] + [ctypes.c_double] * 5 + [_D] * 9
+            L.orc_ray_path.restype = None
+            L.orc_ray_path.argtypes = [ctypes.c_double] * 5 + [_D]
+            L.orc_raytrace_field.restype = None
+            L.orc_raytrace_field.argtypes = [_I64, _D, _D, _D, _D] + [ctypes.c_double] * 8 + \
+                [_I64, _D, _D, _D, _D, _D, ctypes.c_int]
             L.orc_reflect.restype = None
             L.orc_reflect.argtypes = [_I64, ctypes.c_int] + [ctypes.c_double] * 5 + [_D] * 9
             _lib = L
@@ -359,3 +364,50 @@ def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False, pixe
     top = (k1 / v0) * (phi_inc + phi_ref).reshape(int(w["nz"]), int(w["nx"]))
     bot = (k2 / v0) * phi_tr.reshape(int(sg["nz"]), int(sg["nx"]))
     return np.concatenate([top, bot], axis=0)
+
+
+# ---------------------------------------------------------------------------
+# Ray-tracing model (Sec. 2.2)
+# ---------------------------------------------------------------------------
+def ray_path(h1: float, h2: float, rho: float, c1: float, c2: float) -> dict:
+    """The refracted ray of Eq. ray_tracing: Snell's invariant C, path lengths
+    D1, D2 and the cosines of the two angles."""
+    out = np.empty(5, np.float64)
+    lib().orc_ray_path(float(h1), float(h2), float(rho), float(c1), float(c2), _p(out))
+    return {"C": out[0], "D1": out[1], "D2": out[2], "cos1": out[3], "cos2": out[4]}
+
+
+def raytrace_field(src: dict, tgt: dict, m1: dict, m2: dict, z_interface: float, k1: float, k2: float,
+                   v0: float = 1.0, nthreads: int | None = None):
+    """Eq. transmitted_ray_tracing over weighted transducer points (z < z_I)
+    onto targets in medium 2 (z > z_I); returns complex128."""
+    sx, sy, sz, sw = (_f64(src[key]) for key in ("x", "y", "z", "w"))
+    tx, ty, tz = (_f64(tgt[key]) for key in ("x", "y", "z"))
+    nt = tx.shape[0]
+    ore = np.empty(nt, np.float64)
+    oim = np.empty(nt, np.float64)
+    lib().orc_raytrace_field(sx.shape[0], _p(sx), _p(sy), _p(sz), _p(sw), float(v0), float(m1["rho"]),
+                             float(m1["c"]), float(m2["rho"]), float(m2["c"]), float(z_interface), float(k1),
+                             float(k2), nt, _p(tx), _p(ty), _p(tz), _p(ore), _p(oim),
+                             nthreads or default_threads())
+    return ore + 1j * oim
+
+
+def raytrace_image(cfg: dict, nthreads: int | None = None, pixels=None):
+    """Normalised image k2 phi_t / v0 of the ray-tracing model on a
+    one-interface workload's grid (the interface plane is its centre's z),
+    shape [nz][nx], or the values at flat pixel indices."""
+    seed = int(cfg.get("seed", 0))
+    freq, v0 = float(cfg["freq"]), float(cfg.get("v0", 1.0))
+    m = cfg["media"]
+    pc = cfg["piston"]
+    piston = make_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]))
+    zI = float(cfg["interfaces"][0]["centre"][2])
+    g = cfg["grid"]
+    tg = grid_points(g)
+    if pixels is not None:
+        tg = {key: tg[key][np.asarray(pixels)] for key in ("x", "y", "z")}
+    k1, k2 = wavenumber(freq, m[0]["c"]), wavenumber(freq, m[1]["c"])
+    phi = raytrace_field(piston, tg, m[0], m[1], zI, k1, k2, v0, nthreads)
+    val = (k2 / v0) * phi
+    return val if pixels is not None else val.reshape(int(g["nz"]), int(g["nx"]))

@@ -37,6 +37,13 @@
  *                      reflected field on the interface (Sec. 2.1, with
  *                      Eq. reflection_coefficient), same incidence angles as
  *                      orc_transmit.
+ *   orc_ray_path       the refracted ray between two points across a plane
+ *                      interface: Snell's invariant C of Eq. ray_tracing
+ *                      (Sec. 2.2, Eq. root_searching) by bisection, and the
+ *                      path lengths and angles it fixes.
+ *   orc_raytrace_field transmitted field of the ray-tracing model, Eq.
+ *                      transmitted_ray_tracing (Sec. 2.2), over weighted
+ *                      transducer points.
  *   orc_rsi_field      first Rayleigh-Sommerfeld solution, Eq. rayleigh_sommerfeld
  *                      (Sec. 2.1), over weighted source points; the sign of
  *                      its bracket is read as explained at rsi_range().
@@ -497,4 +504,116 @@ void orc_reflect(int64_t n, int mode, double rho1, double c1, double rho2, doubl
         if (R_im)
             R_im[i] = cimag(R);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ray-tracing model (Sec. 2.2)                                              */
+/* ------------------------------------------------------------------------ */
+/* The ray from a point at height h1 above a plane interface (in medium 1,
+ * speed c1) to a point at depth h2 below it (medium 2, speed c2), at
+ * horizontal distance rho, obeys Eq. ray_tracing:
+ *   rho = C h1 / sqrt(S1^2 - C^2) + C h2 / sqrt(S2^2 - C^2),  S = 1/c,
+ * whose right side increases from 0 to infinity as C goes from 0 to
+ * min(S1, S2), so the root is unique; it is found by bisection to the last
+ * representable C.  out = {C, D1, D2, cos a1, cos a2}, with sin a = c C
+ * (Eq. root_searching), D1 = h1 / cos a1, D2 = h2 / cos a2.               */
+void orc_ray_path(double h1, double h2, double rho, double c1, double c2, double *out)
+{
+    double S1 = 1.0 / c1, S2 = 1.0 / c2;
+    double lo = 0.0, hi = fmin(S1, S2);
+    for (int it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi)
+            break;
+        double f = mid * h1 / sqrt(S1 * S1 - mid * mid) + mid * h2 / sqrt(S2 * S2 - mid * mid) - rho;
+        if (f < 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    double C = 0.5 * (lo + hi);
+    double s1 = c1 * C, s2 = c2 * C;
+    double cos1 = sqrt(1.0 - s1 * s1), cos2 = sqrt(1.0 - s2 * s2);
+    out[0] = C;
+    out[1] = h1 / cos1;
+    out[2] = h2 / cos2;
+    out[3] = cos1;
+    out[4] = cos2;
+}
+
+typedef struct {
+    int64_t ns;
+    const double *sx, *sy, *sz, *sw;
+    double v0, rho1, c1, rho2, c2, zI, k1, k2;
+    const double *tx, *ty, *tz;
+    double *ore, *oim;
+} ray_job;
+
+typedef struct {
+    const ray_job *J;
+    int64_t t0, t1;
+} ray_range_arg;
+
+/* Eq. transmitted_ray_tracing: for every target,
+ *   phi_t = -(v0 / 2 pi) sum_i w_i T12 e^{i (k1 D1 + k2 D2)}
+ *           / sqrt((D1 + c2 cos^2 a1 / (c1 cos^2 a2) D2) (D1 + (c2 / c1) D2)),
+ * T12 of Eq. transmission_coefficient at the ray's angles.                  */
+static void *ray_range(void *argp)
+{
+    const ray_range_arg *a = (const ray_range_arg *)argp;
+    const ray_job *J = a->J;
+    const double pre = -J->v0 / (2.0 * M_PI);
+    for (int64_t j = a->t0; j < a->t1; ++j) {
+        double sre = 0.0, cre = 0.0, sim = 0.0, cim = 0.0;
+        double h2 = J->tz[j] - J->zI;
+        for (int64_t i = 0; i < J->ns; ++i) {
+            double h1 = J->zI - J->sz[i];
+            double rho = hypot(J->tx[j] - J->sx[i], J->ty[j] - J->sy[i]);
+            double path[5];
+            orc_ray_path(h1, h2, rho, J->c1, J->c2, path);
+            double D1 = path[1], D2 = path[2], cos1 = path[3], cos2 = path[4];
+            double complex T = orc_T12(J->rho1, J->c1, J->rho2, J->c2, cos1, cos2);
+            double spread = sqrt((D1 + J->c2 * cos1 * cos1 / (J->c1 * cos2 * cos2) * D2) *
+                                 (D1 + J->c2 / J->c1 * D2));
+            double complex term = pre * J->sw[i] * T * cexp(I * (J->k1 * D1 + J->k2 * D2)) / spread;
+            double v = creal(term), t = sre + v;
+            cre += (fabs(sre) >= fabs(v)) ? (sre - t) + v : (v - t) + sre;
+            sre = t;
+            v = cimag(term);
+            t = sim + v;
+            cim += (fabs(sim) >= fabs(v)) ? (sim - t) + v : (v - t) + sim;
+            sim = t;
+        }
+        J->ore[j] = sre + cre;
+        J->oim[j] = sim + cim;
+    }
+    return NULL;
+}
+
+void orc_raytrace_field(int64_t ns, const double *sx, const double *sy, const double *sz, const double *sw,
+                        double v0, double rho1, double c1, double rho2, double c2, double zI, double k1,
+                        double k2, int64_t nt, const double *tx, const double *ty, const double *tz,
+                        double *out_re, double *out_im, int nthreads)
+{
+    ray_job J = {ns, sx, sy, sz, sw, v0, rho1, c1, rho2, c2, zI, k1, k2, tx, ty, tz, out_re, out_im};
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > 256)
+        nthreads = 256;
+    pthread_t th[256];
+    ray_range_arg args[256];
+    int64_t per = (nt + nthreads - 1) / nthreads;
+    int used = 0;
+    for (int q = 0; q < nthreads; ++q) {
+        int64_t t0 = q * per, t1 = t0 + per < nt ? t0 + per : nt;
+        if (t0 >= t1)
+            break;
+        args[q].J = &J;
+        args[q].t0 = t0;
+        args[q].t1 = t1;
+        pthread_create(&th[q], NULL, ray_range, &args[q]);
+        ++used;
+    }
+    for (int q = 0; q < used; ++q)
+        pthread_join(th[q], NULL);
 }
