@@ -37,6 +37,10 @@ if ROOT not in sys.path:
 OPS = {
     "rsi": {"fp32": 23, "mufu": 3, "lds": 1.0},
     "piston": {"fp32": 13, "mufu": 3, "lds": 1.0},
+    # ray-tracing pair (Sec. 2.2): linear prediction of the crossing from the
+    # tile's reference ray, then 2 safeguarded Newton steps (~29 FP32 and 3
+    # MUFU each); ~88 FP32 and 11 MUFU around them
+    "raytrace": {"fp32": 146, "mufu": 17, "lds": 2.0},
 }
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "rsi_pair_terms_per_s"
@@ -59,7 +63,7 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
-    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5", "f1"], default="c2",
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5", "f1", "f2"], default="c2",
                     help="c4: the batched broadband scan (2048 instances in one CUDA graph); "
                          "c5: the learned surrogate (train on RSI fields, compare)")
     ap.add_argument("--fields", type=int, default=20000, help="c5: training fields")
@@ -642,6 +646,74 @@ def run_two_medium_f1(args):
     print(json.dumps(line), flush=True)
 
 
+def run_raytrace_f2(args):
+    """f2: the ray-tracing model (Sec. 2.2) on c2's geometry with a 10 degree
+    tilt at 5 MHz: 2^16 transducer points onto a 512^2 image in the steel;
+    error against the stored oracle pixels."""
+    import numpy as np
+    import torch
+    from paper_2408_06765_gb300 import build, rsi
+    from paper_2408_06765_gb300 import workloads as W
+    build.build()
+    rsi.load()
+    dev = torch.device("cuda", 0)
+    cfg = W.f2_ray_tracing()
+    g = cfg["grid"]
+    pixels = int(g["nx"]) * int(g["nz"])
+    pairs = int(cfg["piston"]["n"]) * pixels
+    ws = rsi.Workspace(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    step = lambda: rsi.run_raytrace(cfg, fmt="c64", workspace=ws, device=dev)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    rsi.sync_status()
+    clocks = ClockSampler(0)
+    clocks.start()
+    rsi.timing_enable(True)
+    n0 = rsi.launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        img = step()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = rsi.launch_count() - n0
+    clk = clocks.stop()
+    rt_ms, rt_n, rt_pairs = rsi.timing_read(rsi.TIMING_RAYTRACE)
+    rsi.timing_enable(False)
+    rsi.sync_status()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_hz = (clk["sm_mhz"] if clk and clk.get("sm_mhz") else 2070.0) * 1e6
+    peak, limiter = alu_roofline("raytrace", n_sm, clk_hz)
+    achieved = rt_pairs / (rt_ms * 1e-3)
+    err = None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "f2_5MHz.json")
+    if os.path.exists(path):
+        rec = json.load(open(path))
+        got = img.reshape(-1).cpu().numpy().astype(np.complex128)[np.asarray(rec["pixels"])]
+        want = np.asarray(rec["re"]) + 1j * np.asarray(rec["im"])
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    total_s = sum(ms) * 1e-3
+    line = {"metric": METRIC, "value": pairs * args.steps / total_s, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scrambled-Sobol points; workload parameters only)",
+            "config": {"workload": "f2 ray-tracing model: 6.35 mm piston tilted 10 deg, 2^16 points, 5 MHz, "
+                                   "water -> steel at 50 mm, 512^2 image over 80 x 60 mm in the steel",
+                       "pairs_per_step": pairs, "l2_flush": "256 MiB write before every step"},
+            "field_pts_per_s": pixels * args.steps / total_s,
+            "rel_l2_err": {"image_vs_stored_fp64_oracle_1024_pixels": err, "tolerance": 1e-4},
+            "roofline": {"bound": "alu", "kernel": "raytrace_kernel", "achieved": achieved / 1e9,
+                         "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+                         "limiter": limiter, "ops_per_pair": OPS["raytrace"], "launches": rt_n},
+            "clocks": clk, "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev)}
+    print(json.dumps(line), flush=True)
+
+
 def measured_peaks():
     """Copy bandwidth and bf16 GEMM throughput measured on this GPU model
     (MEASURED_PEAKS.json beside this file), else the fallback figures."""
@@ -785,6 +857,8 @@ def main():
         run_surrogate_c5(args)
     elif args.config == "f1" and args.impl == "ours":
         run_two_medium_f1(args)
+    elif args.config == "f2" and args.impl == "ours":
+        run_raytrace_f2(args)
     elif args.config == "c4" and args.impl == "ours" and args.case == "chain":
         run_batch_c4(args)
     elif args.case == "stage":

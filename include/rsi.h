@@ -226,6 +226,39 @@ int rsi_interface_transmit(const rsi_interface *it, const void *points, int64_t 
 int rsi_interface_reflect(const rsi_interface *it, const void *points, int64_t n,
                           const double *phi, double *sigma, void *stream);
 
+/* ---- ray-tracing model (Sec. 2.2) ------------------------------------------ */
+typedef struct rsi_raytrace {
+    double k1, k2;       /* wavenumbers of medium 1 (transducer side) and 2 (rad/m) */
+    double rho1, c1;     /* medium 1: density, sound speed                          */
+    double rho2, c2;     /* medium 2                                                */
+    double z_interface;  /* the plane interface z = z_interface (m)                 */
+    double v0;           /* piston normal velocity amplitude (m/s)                  */
+    int32_t tile;        /* transducer points per tile (32, 64, 128, 256); 0 = auto */
+    int32_t splits;      /* transducer-point splits (>= 1); 0 = auto                */
+    int32_t newton;      /* Newton steps per pair for the crossing point after a
+                            linear prediction from the tile's reference ray, before
+                            the convergence test (steps then continue, at most 12,
+                            until the crossing moves < 1 nm); 0 = 2              */
+    int32_t reserved;
+} rsi_raytrace;
+
+/* Workspace for rsi_raytrace_field (staged transducer tiles and split
+ * partial sums); 0 on invalid input.                                      */
+size_t rsi_raytrace_workspace_bytes(const rsi_raytrace *rt, int64_t n_src, int64_t n_tgt);
+
+/* Eq. transmitted_ray_tracing: for every target Q_j (in medium 2, z > z_I)
+ *   field[j] = -(v0 / 2 pi) sum_i w_i T12 e^{i (k1 D1 + k2 D2)}
+ *              / sqrt((D1 + c2 cos^2 a1 / (c1 cos^2 a2) D2) (D1 + (c2 / c1) D2))
+ * along the refracted ray from transducer point P_i (in medium 1, z < z_I)
+ * to Q_j (Snell's law, Eq. root_searching; D1, D2 the path lengths in the two
+ * media; T12 of Eq. transmission_coefficient at the ray's angles).  Points
+ * on the wrong side of the interface break the model: their sums come out
+ * non-finite (recorded in the status word).  Same conventions for point
+ * sets, field, workspace and stream as rsi_propagate_stage.                */
+int rsi_raytrace_field(const rsi_raytrace *rt, const void *src_points, int64_t n_src,
+                       const void *tgt_points, int64_t n_tgt, double *tgt_field,
+                       void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---- field image (step a7) ------------------------------------------------- */
 enum rsi_image_format {
     RSI_IMG_C128 = 0, /* complex double [nz][nx]                                */
@@ -360,12 +393,14 @@ int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window,
 uint64_t rsi_launch_count(void);
 
 /* Per-kernel timing of the source x target kernels.  While enabled, every
- * rsi_propagate_stage call brackets its main kernel with CUDA events recorded
- * on the call's stream.  rsi_timing_enable(1) clears the record and starts;
- * rsi_timing_enable(0) stops.  rsi_timing_read(kind, ...) synchronises with
- * the recorded events and returns, for the stages of that kind
- * (RSI_STAGE_PISTON or RSI_STAGE_RSI): the summed kernel time in ms, the
- * number of launches and the summed source x target pair count.            */
+ * rsi_propagate_stage and rsi_raytrace_field call brackets its main kernel
+ * with CUDA events recorded on the call's stream.  rsi_timing_enable(1)
+ * clears the record and starts; rsi_timing_enable(0) stops.
+ * rsi_timing_read(kind, ...) synchronises with the recorded events and
+ * returns, for the kernels of that kind (RSI_STAGE_PISTON, RSI_STAGE_RSI or
+ * RSI_TIMING_RAYTRACE): the summed kernel time in ms, the number of launches
+ * and the summed source x target pair count.                               */
+#define RSI_TIMING_RAYTRACE 2
 int rsi_timing_enable(int32_t on);
 int rsi_timing_read(int32_t kind, double *total_ms, int64_t *launches, double *pairs);
 

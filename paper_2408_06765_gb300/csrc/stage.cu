@@ -258,28 +258,38 @@ extern "C" int rsi_propagate_stage(const rsi_stage* st, const void* src_points, 
     double2* field = reinterpret_cast<double2*>(tgt_field);
     a.out = p.splits > 1 ? reinterpret_cast<double2*>(tiles + p.tiles_bytes) : field;
     a.status = status;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_tmu);
-        if (g_timing) {
-            ev0 = pooled_event();
-            ev1 = pooled_event();
-        }
-    }
-    if (ev0 && ev1) RSI_CUDA_TRY(cudaEventRecord(ev0, s), "cudaEventRecord");
+    TimingScope tsc = timing_begin(s);
     rc = fp32 ? launch_stage_fp32(a, s) : launch_stage_fp64(a, s);
     if (rc != RSI_OK) return rc;
-    if (ev0 && ev1) {
-        RSI_CUDA_TRY(cudaEventRecord(ev1, s), "cudaEventRecord");
+    timing_end(tsc, st->kind, double(n_src) * double(n_tgt), s);
+    if (p.splits > 1) return launch_reduce_partials(a.out, p.splits, n_tgt, field, status, s);
+    return RSI_OK;
+}
+
+TimingScope timing_begin(cudaStream_t s) {
+    TimingScope t;
+    {
         std::lock_guard<std::mutex> lk(g_tmu);
-        g_timed.push_back({ev0, ev1, st->kind, double(n_src) * double(n_tgt)});
+        if (!g_timing) return t;
+        t.a = pooled_event();
+        t.b = pooled_event();
     }
-    if (p.splits > 1) {
-        int threads = 256;
-        unsigned blocks = unsigned((n_tgt + threads - 1) / threads);
-        reduce_partials_kernel<<<blocks, threads, 0, s>>>(a.out, p.splits, n_tgt, field, status);
-        RSI_CHECK_LAUNCH("reduce_partials_kernel");
-    }
+    if (t.a && t.b && cudaEventRecord(t.a, s) != cudaSuccess) t.a = t.b = nullptr;
+    return t;
+}
+
+void timing_end(TimingScope& t, int kind, double pairs, cudaStream_t s) {
+    if (!t.a || !t.b) return;
+    if (cudaEventRecord(t.b, s) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timed.push_back({t.a, t.b, kind, pairs});
+}
+
+int launch_reduce_partials(const double2* part, int splits, int64_t n, double2* out, int* status, cudaStream_t s) {
+    int threads = 256;
+    unsigned blocks = unsigned((n + threads - 1) / threads);
+    reduce_partials_kernel<<<blocks, threads, 0, s>>>(part, splits, n, out, status);
+    RSI_CHECK_LAUNCH("reduce_partials_kernel");
     return RSI_OK;
 }
 

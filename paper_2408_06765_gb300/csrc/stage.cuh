@@ -73,3 +73,13 @@ int fp64_threads();
 // resident CTAs per SM of the kernel a launch would use (>= 1)
 int stage_occupancy_fp32(const StageArgs& a);
 int stage_occupancy_fp64(const StageArgs& a);
+
+// CUDA-event timing of a source x target kernel for rsi_timing_read: a no-op
+// unless timing is enabled.  `kind` is RSI_STAGE_* or RSI_TIMING_RAYTRACE.
+struct TimingScope {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+TimingScope timing_begin(cudaStream_t s);
+void timing_end(TimingScope& t, int kind, double pairs, cudaStream_t s);
+// out[j] = sum over splits of part[split][j] (Neumaier, split order)
+int launch_reduce_partials(const double2* part, int splits, int64_t n, double2* out, int* status, cudaStream_t s);

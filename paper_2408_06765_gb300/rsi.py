@@ -36,7 +36,8 @@ IMG = {"c128": 0, "c64": 1, "abs32": 2}
 SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes",
            "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points",
            "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_interface_transmit",
-           "rsi_interface_reflect", "rsi_field_image", "rsi_field_image_sum", "rsi_launch_count", "rsi_timing_enable", "rsi_timing_read",
+           "rsi_interface_reflect", "rsi_field_image", "rsi_field_image_sum", "rsi_launch_count",
+           "rsi_raytrace_workspace_bytes", "rsi_raytrace_field", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
            "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier",
@@ -70,6 +71,13 @@ class Interface(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rho1", ctypes.c_double),
                 ("c1", ctypes.c_double), ("rho2", ctypes.c_double), ("c2", ctypes.c_double),
                 ("snell_C", ctypes.c_double)]
+
+
+class Raytrace(ctypes.Structure):
+    _fields_ = [("k1", ctypes.c_double), ("k2", ctypes.c_double), ("rho1", ctypes.c_double),
+                ("c1", ctypes.c_double), ("rho2", ctypes.c_double), ("c2", ctypes.c_double),
+                ("z_interface", ctypes.c_double), ("v0", ctypes.c_double), ("tile", ctypes.c_int32),
+                ("splits", ctypes.c_int32), ("newton", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class BatchInstance(ctypes.Structure):
@@ -113,6 +121,9 @@ def load(path: str | None = None):
         L.rsi_field_image.argtypes = [ctypes.POINTER(Grid), vp, ctypes.c_double, ctypes.c_double,
                                       i32, vp, vp]
         L.rsi_interface_reflect.argtypes = [ctypes.POINTER(Interface), vp, i64, vp, vp, vp]
+        L.rsi_raytrace_workspace_bytes.restype = sz
+        L.rsi_raytrace_workspace_bytes.argtypes = [ctypes.POINTER(Raytrace), i64, i64]
+        L.rsi_raytrace_field.argtypes = [ctypes.POINTER(Raytrace), vp, i64, vp, i64, vp, vp, sz, vp]
         L.rsi_field_image_sum.argtypes = [ctypes.POINTER(Grid), vp, vp, ctypes.c_double, ctypes.c_double,
                                           i32, vp, vp]
         L.rsi_launch_count.restype = u64
@@ -401,6 +412,46 @@ def run_chain(cfg: dict, precision: str | None = None, targets: Points | None = 
         k_last = wavenumber(freq, media[len(ifaces)]["c"])
         image = field_image(cfg["grid"], phi, k_last, v0, fmt, stream=stream)
     return ChainResult(image, phi, kept)
+
+
+TIMING_RAYTRACE = 2
+
+
+def raytrace_struct(cfg: dict, tile: int = 0, splits: int = 0, newton: int = 0) -> Raytrace:
+    m = cfg["media"]
+    f = float(cfg["freq"])
+    return Raytrace(wavenumber(f, m[0]["c"]), wavenumber(f, m[1]["c"]), float(m[0]["rho"]), float(m[0]["c"]),
+                    float(m[1]["rho"]), float(m[1]["c"]), float(cfg["interfaces"][0]["centre"][2]),
+                    float(cfg.get("v0", 1.0)), int(tile), int(splits), int(newton), 0)
+
+
+def raytrace_field(rt: Raytrace, src: Points, tgt: Points, out=None, workspace: Workspace | None = None,
+                   stream=None) -> torch.Tensor:
+    """Eq. transmitted_ray_tracing from transducer points onto targets in medium 2."""
+    L = load()
+    if out is None:
+        out = torch.empty(tgt.n, dtype=torch.complex128, device=tgt.buf.device)
+    nb = int(L.rsi_raytrace_workspace_bytes(ctypes.byref(rt), src.n, tgt.n))
+    if nb == 0:
+        raise RSIError("rsi_raytrace_workspace_bytes", -1, L.rsi_last_error().decode(errors="replace"))
+    ws = (workspace or Workspace(tgt.buf.device)).get(nb)
+    _check(L.rsi_raytrace_field(ctypes.byref(rt), src.ptr(), src.n, tgt.ptr(), tgt.n, _ptr(out), _ptr(ws), nb,
+                                _stream(stream)), "rsi_raytrace_field")
+    return out
+
+
+def run_raytrace(cfg: dict, fmt: str = "c128", workspace: Workspace | None = None, stream=None,
+                 device="cuda", **shape) -> torch.Tensor:
+    """Image k2 phi_t / v0 of the ray-tracing model (Sec. 2.2) on cfg["grid"]
+    (medium 2, below the plane interface at the interface centre's z)."""
+    seed = int(cfg.get("seed", 0))
+    pc = cfg["piston"]
+    piston = make_qmc_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]),
+                             device=device, stream=stream)
+    tgt = grid_points(cfg["grid"], device=device, stream=stream)
+    rt = raytrace_struct(cfg, **shape)
+    phi = raytrace_field(rt, piston, tgt, workspace=workspace, stream=stream)
+    return field_image(cfg["grid"], phi, rt.k2, float(cfg.get("v0", 1.0)), fmt, stream=stream)
 
 
 class TwoMediumResult:

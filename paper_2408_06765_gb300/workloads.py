@@ -106,6 +106,31 @@ def f1_two_medium(freq: float = 5.0 * MHZ, tilt_deg: float = 10.0, n_piston: int
     }
 
 
+def f2_ray_tracing(freq: float = 5.0 * MHZ, tilt_deg: float = 10.0, n_piston: int = 1 << 16,
+                   nx: int = 512, nz: int = 512) -> dict:
+    """The ray-tracing model (Sec. 2.2) on c2's geometry: the 6.35 mm piston
+    tilted by 10 degrees with 2^16 points, water -> steel at z = 50 mm, a
+    512 x 512 image over x in [-40, 40] mm, z in (50, 110] mm in the steel."""
+    tilt = math.radians(tilt_deg)
+    zi = 50 * MM
+    return {
+        "name": f"f2_ray_tracing_{freq / MHZ:g}MHz", "freq": float(freq), "v0": 1.0, "seed": 0,
+        "piston": {"a": 6.35 * MM, "centre": (0.0, 0.0, 0.0), "tilt": tilt, "n": int(n_piston), "set_id": 0},
+        "media": [dict(WATER), dict(STEEL)],
+        "interfaces": [_rect((zi * math.tan(tilt), 0.0, zi), 80 * MM, 0, 1)],  # the plane z = 50 mm
+        "grid": {"x0": -40 * MM, "x1": 40 * MM, "nx": int(nx), "z0": zi, "z1": zi + 60 * MM, "nz": int(nz),
+                 "y": 0.0},
+    }
+
+
+def f2_small() -> dict:
+    """f2 at sizes the oracle finishes in a second: 3001 piston points (ragged
+    tiles) onto 37 x 29 pixels reaching out to 75 degrees in the steel."""
+    cfg = f2_ray_tracing(n_piston=3001, nx=37, nz=29)
+    cfg["grid"].update({"x0": -30 * MM, "x1": 30 * MM, "z1": 50 * MM + 20 * MM})
+    return cfg
+
+
 def f1_small() -> dict:
     """f1 at sizes the oracle finishes in a second, still resolving the
     water wavelength on the interface (2.25 MHz, 12 000 points on 40 mm):

@@ -10,7 +10,8 @@ pixel indices and normalised values k phi / v0 as JSON text:
 Workloads: c2 at 2.25, 5 and 10 MHz (2^16 x 2^18 points, 512^2 image), the
 multilayer c3 workload, flat and curved (9 interfaces of 2^16 points), and the
 two-medium image f1 (incident + reflected field above the interface,
-transmitted field below, oracle.two_medium).
+transmitted field below, oracle.two_medium) and the ray-tracing model f2
+(oracle.raytrace_image).
 """
 from __future__ import annotations
 
@@ -36,7 +37,23 @@ def cases():
     out["c3_flat"] = W.c3_multilayer(curved=False)
     out["c3_curved"] = W.c3_multilayer(curved=True)
     out["f1_5MHz"] = W.f1_two_medium()
+    out["f2_5MHz"] = W.f2_ray_tracing()
     return out
+
+
+def make_ray(name: str, cfg: dict):
+    g = cfg["grid"]
+    n_pix = int(g["nx"]) * int(g["nz"])
+    rng = np.random.default_rng(1234)
+    pix = np.sort(rng.choice(n_pix, N_PIXELS, replace=False))
+    t0 = time.time()
+    val = oracle.raytrace_image(cfg, pixels=pix)
+    rec = {"workload": name, "source": "oracle.raytrace_image (FP64 CPU oracle), tests/golden/make_golden.py",
+           "pixels": pix.tolist(), "re": val.real.tolist(), "im": val.imag.tolist(),
+           "oracle_seconds": time.time() - t0}
+    with open(os.path.join(HERE, f"{name}.json"), "w") as f:
+        json.dump(rec, f)
+    print(f"{name}: {time.time() - t0:.1f} s", flush=True)
 
 
 def make_two_medium(name: str, cfg: dict):
@@ -77,4 +94,9 @@ if __name__ == "__main__":
     want = sys.argv[1:]
     for name, cfg in cases().items():
         if not want or name in want:
-            (make_two_medium if "grid_water" in cfg else make)(name, cfg)
+            if "grid_water" in cfg:
+                make_two_medium(name, cfg)
+            elif name.startswith("f2"):
+                make_ray(name, cfg)
+            else:
+                make(name, cfg)
