@@ -74,10 +74,13 @@ def lib():
             L.orc_sobol.restype = None
             L.orc_sobol.argtypes = [ctypes.c_uint64, ctypes.c_uint32, _I64, _I64,
                                     ctypes.c_int, _U32, _U32]
-            for name, extra in (("orc_map_disk", 5), ("orc_map_rect", 5), ("orc_map_cyl", 6)):
+            L.orc_halton.restype = None
+            L.orc_halton.argtypes = [_I64, _I64, _U32, _U32]
+            for name, extra in (("orc_map_disk", 6), ("orc_map_rect", 5), ("orc_map_cyl", 6),
+                                ("orc_map_cap", 7)):
                 f = getattr(L, name)
                 f.restype = None
-                f.argtypes = [_I64, _U32, _U32] + [ctypes.c_double] * extra + [_D] * 7
+                f.argtypes = [_I64, ctypes.c_int, _U32, _U32] + [ctypes.c_double] * extra + [_D] * 7
             L.orc_grid_points.restype = None
             L.orc_grid_points.argtypes = [ctypes.c_double, ctypes.c_double, _I64,
                                           ctypes.c_double, ctypes.c_double, _I64,
@@ -142,9 +145,23 @@ def sobol(seed: int, set_id: int, n: int, first: int = 0, scrambled: bool = True
     return su, sv
 
 
+def halton(n: int, first: int = 0):
+    """Integer Halton coordinates of points first+1 .. first+n (bases 2, 3):
+    the base-2 radical inverse as a 32-bit fraction, the base-3 one as a
+    fraction of 3^20."""
+    su = np.empty(n, np.uint32)
+    sv = np.empty(n, np.uint32)
+    lib().orc_halton(first, n, _p(su, _U32), _p(sv, _U32))
+    return su, sv
+
+
+SEQUENCES = {"sobol": 0, "halton": 1}
+
+
 def map_points(surface: dict, su, sv) -> dict:
     """Map integer QMC coordinates onto a surface (Eqs. circle_sampling,
-    square_sampling; cylinder variant).  Returns x, y, z, nx, ny, nz, w."""
+    square_sampling; cylinder and spherical-cap variants; optional Gaussian
+    apodisation of the disk and cap).  Returns x, y, z, nx, ny, nz, w."""
     su = np.ascontiguousarray(su, np.uint32)
     sv = np.ascontiguousarray(sv, np.uint32)
     n = su.shape[0]
@@ -152,23 +169,33 @@ def map_points(surface: dict, su, sv) -> dict:
     ptrs = [_p(out[k]) for k in ("x", "y", "z", "nx", "ny", "nz", "w")]
     c = [float(v) for v in surface["centre"]]
     kind = surface["kind"]
+    seq = SEQUENCES[surface.get("sequence", "sobol")]
+    apod = float(surface.get("apod", 0.0))
     L = lib()
     if kind == "disk":
-        L.orc_map_disk(n, _p(su, _U32), _p(sv, _U32), *c, float(surface.get("tilt", 0.0)),
-                       float(surface["a"]), *ptrs)
+        L.orc_map_disk(n, seq, _p(su, _U32), _p(sv, _U32), *c, float(surface.get("tilt", 0.0)),
+                       float(surface["a"]), apod, *ptrs)
     elif kind == "rect":
-        L.orc_map_rect(n, _p(su, _U32), _p(sv, _U32), *c, float(surface["wx"]),
+        L.orc_map_rect(n, seq, _p(su, _U32), _p(sv, _U32), *c, float(surface["wx"]),
                        float(surface["wy"]), *ptrs)
     elif kind == "cyl":
-        L.orc_map_cyl(n, _p(su, _U32), _p(sv, _U32), *c, float(surface["wx"]),
+        L.orc_map_cyl(n, seq, _p(su, _U32), _p(sv, _U32), *c, float(surface["wx"]),
                       float(surface["wy"]), float(surface["R"]), *ptrs)
+    elif kind == "cap":
+        L.orc_map_cap(n, seq, _p(su, _U32), _p(sv, _U32), *c, float(surface.get("tilt", 0.0)),
+                      float(surface["a"]), float(surface["R"]), apod, *ptrs)
     else:
         raise ValueError(f"unknown surface kind {kind!r}")
     return out
 
 
 def make_points(surface: dict, seed: int, set_id: int, n: int, scrambled: bool = True) -> dict:
-    su, sv = sobol(seed, set_id, n, 0, scrambled)
+    """Points of a surface in index order: scrambled Sobol (seed, set_id) or,
+    with surface["sequence"] == "halton", the Halton points 1..n."""
+    if surface.get("sequence", "sobol") == "halton":
+        su, sv = halton(n)
+    else:
+        su, sv = sobol(seed, set_id, n, 0, scrambled)
     pts = map_points(surface, su, sv)
     pts["su"], pts["sv"] = su, sv
     return pts

@@ -21,7 +21,15 @@
  *                      construction), optionally with a nested (Owen 1995)
  *                      bit scramble keyed by a SplitMix64 stream (Steele, Lea
  *                      & Flood 2014; output mixer = Stafford 2011 "Mix13").
- *   orc_map_disk       piston face sampling, Eq. circle_sampling (Sec. 2.3).
+ *   orc_halton         the paper's own QMC points, the Halton sequence in
+ *                      bases 2 and 3 (Sec. 2.3), as exact integer radical
+ *                      inverses (index 0, the origin of every base, skipped).
+ *   orc_map_disk       piston face sampling, Eq. circle_sampling (Sec. 2.3),
+ *                      optionally with a Gaussian amplitude profile (the
+ *                      apodised face Sec. 4 mentions).
+ *   orc_map_cap        focused transducer: a spherical cap (Sec. 3.3, Fig.
+ *                      transducer_system b), projected-disk sampling lifted
+ *                      onto the sphere with the surface Jacobian.
  *   orc_map_rect       square interface sampling, Eq. square_sampling, with
  *                      the side length given explicitly.
  *   orc_map_cyl        cylindrical interface (projected-area sampling with the
@@ -137,22 +145,53 @@ void orc_sobol(uint64_t seed, uint32_t set_id, int64_t first, int64_t n,
     }
 }
 
-/* unit value of a 32-bit QMC coordinate: (x + 1/2) 2^-32, exact in FP64 */
-static double unit(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+/* Halton points first+1 .. first+n (Halton 1960): su = the base-2 radical
+ * inverse of the index as a 32-bit fraction (its bits reversed), sv = the
+ * base-3 radical inverse as a fraction of 3^20 (its 20 base-3 digits
+ * reversed).  Indices stay below 2^31 < 3^20, so both are exact.          */
+void orc_halton(int64_t first, int64_t n, uint32_t *su, uint32_t *sv)
+{
+    for (int64_t q = 0; q < n; ++q) {
+        uint64_t i = (uint64_t)(first + q + 1);
+        uint32_t r2 = 0;
+        for (int b = 0; b < 32; ++b)
+            if ((i >> b) & 1u)
+                r2 |= 1u << (31 - b);
+        uint64_t r3 = 0, k = i;
+        for (int d = 0; d < 20; ++d) {
+            r3 = 3 * r3 + k % 3;
+            k /= 3;
+        }
+        su[q] = r2;
+        sv[q] = (uint32_t)r3;
+    }
+}
+
+/* unit value of a QMC coordinate.  seq 0 (Sobol): (x + 1/2) 2^-32.  seq 1
+ * (Halton): dimension 0 is x 2^-32, dimension 1 is x / 3^20 -- the radical
+ * inverses themselves.                                                     */
+static double unit_of(int seq, int dim, uint32_t x)
+{
+    if (seq == 0)
+        return ((double)x + 0.5) * (1.0 / 4294967296.0);
+    if (dim == 0)
+        return (double)x * (1.0 / 4294967296.0);
+    return (double)x / 3486784401.0;
+}
 
 /* Piston face, Eq. circle_sampling: r = a sqrt(H), theta = 2 pi H (first
  * dimension radial, second angular).  The face is centred at c and tilted by
  * `tilt` radians about +y: in-plane axes e1 = (cos t, 0, -sin t), e2 = +y,
  * normal (sin t, 0, cos t).  Weight = face area / n (Eq. monte_carlo).    */
-void orc_map_disk(int64_t n, const uint32_t *su, const uint32_t *sv,
-                  double cx, double cy, double cz, double tilt, double a,
+void orc_map_disk(int64_t n, int seq, const uint32_t *su, const uint32_t *sv,
+                  double cx, double cy, double cz, double tilt, double a, double apod,
                   double *x, double *y, double *z,
                   double *nx, double *ny, double *nz, double *w)
 {
     double ct = cos(tilt), st = sin(tilt);
     for (int64_t i = 0; i < n; ++i) {
-        double r = a * sqrt(unit(su[i]));
-        double th = 2.0 * M_PI * unit(sv[i]);
+        double r = a * sqrt(unit_of(seq, 0, su[i]));
+        double th = 2.0 * M_PI * unit_of(seq, 1, sv[i]);
         double l1 = r * cos(th), l2 = r * sin(th);
         x[i] = cx + l1 * ct;
         y[i] = cy + l2;
@@ -161,19 +200,21 @@ void orc_map_disk(int64_t n, const uint32_t *su, const uint32_t *sv,
         ny[i] = 0.0;
         nz[i] = ct;
         w[i] = M_PI * a * a / (double)n;
+        if (apod > 0.0) /* Gaussian velocity profile v0 exp(-(r / apod)^2) */
+            w[i] *= exp(-(r / apod) * (r / apod));
     }
 }
 
 /* Flat interface patch, Eq. square_sampling with sides wx, wy centred on c;
  * the interface normal is +z, toward the observation side (Sec. 2.1).    */
-void orc_map_rect(int64_t n, const uint32_t *su, const uint32_t *sv,
+void orc_map_rect(int64_t n, int seq, const uint32_t *su, const uint32_t *sv,
                   double cx, double cy, double cz, double wx, double wy,
                   double *x, double *y, double *z,
                   double *nx, double *ny, double *nz, double *w)
 {
     for (int64_t i = 0; i < n; ++i) {
-        x[i] = cx + wx * (unit(su[i]) - 0.5);
-        y[i] = cy + wy * (unit(sv[i]) - 0.5);
+        x[i] = cx + wx * (unit_of(seq, 0, su[i]) - 0.5);
+        y[i] = cy + wy * (unit_of(seq, 1, sv[i]) - 0.5);
         z[i] = cz;
         nx[i] = 0.0;
         ny[i] = 0.0;
@@ -186,21 +227,54 @@ void orc_map_rect(int64_t n, const uint32_t *su, const uint32_t *sv,
  * z = cz + R - sqrt(R^2 - xi^2), xi = x - cx.  Points are uniform in the
  * projected (x, y) rectangle; the weight carries the surface Jacobian
  * R / sqrt(R^2 - xi^2).  The normal points toward the axis (+z side).     */
-void orc_map_cyl(int64_t n, const uint32_t *su, const uint32_t *sv,
+void orc_map_cyl(int64_t n, int seq, const uint32_t *su, const uint32_t *sv,
                  double cx, double cy, double cz, double wx, double wy, double R,
                  double *x, double *y, double *z,
                  double *nx, double *ny, double *nz, double *w)
 {
     for (int64_t i = 0; i < n; ++i) {
-        double xi = wx * (unit(su[i]) - 0.5);
+        double xi = wx * (unit_of(seq, 0, su[i]) - 0.5);
         double s = sqrt(R * R - xi * xi);
         x[i] = cx + xi;
-        y[i] = cy + wy * (unit(sv[i]) - 0.5);
+        y[i] = cy + wy * (unit_of(seq, 1, sv[i]) - 0.5);
         z[i] = cz + R - s;
         nx[i] = -xi / R;
         ny[i] = 0.0;
         nz[i] = s / R;
         w[i] = wx * wy / (double)n * (R / s);
+    }
+}
+
+/* Focused transducer: the spherical cap of radius of curvature R over an
+ * aperture of radius a, apex at c, centre of curvature R along the axis.
+ * Points are uniform in the projected aperture (r = a sqrt(u), theta = 2 pi v,
+ * as Eq. circle_sampling), lifted to the sphere at height
+ * R - sqrt(R^2 - r^2); the weight carries the Jacobian R / sqrt(R^2 - r^2)
+ * and the normal points to the centre of curvature.  The cap is tilted like
+ * the disk: local (l1, l2, h) -> (l1 cos t + h sin t, l2, -l1 sin t + h cos t).
+ * apod > 0 multiplies the weight by exp(-(r / apod)^2).                     */
+void orc_map_cap(int64_t n, int seq, const uint32_t *su, const uint32_t *sv,
+                 double cx, double cy, double cz, double tilt, double a, double R, double apod,
+                 double *x, double *y, double *z,
+                 double *nx, double *ny, double *nz, double *w)
+{
+    double ct = cos(tilt), st = sin(tilt);
+    for (int64_t i = 0; i < n; ++i) {
+        double r = a * sqrt(unit_of(seq, 0, su[i]));
+        double th = 2.0 * M_PI * unit_of(seq, 1, sv[i]);
+        double l1 = r * cos(th), l2 = r * sin(th);
+        double q = sqrt(R * R - r * r);
+        double h = R - q;
+        x[i] = cx + l1 * ct + h * st;
+        y[i] = cy + l2;
+        z[i] = cz - l1 * st + h * ct;
+        double m1 = -l1 / R, m2 = -l2 / R, m3 = q / R; /* toward the centre of curvature */
+        nx[i] = m1 * ct + m3 * st;
+        ny[i] = m2;
+        nz[i] = -m1 * st + m3 * ct;
+        w[i] = M_PI * a * a / (double)n * (R / q);
+        if (apod > 0.0)
+            w[i] *= exp(-(r / apod) * (r / apod));
     }
 }
 
