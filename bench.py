@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
-    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5", "f1", "f2"], default="c2",
+    ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5", "f1", "f2", "f3", "f4"], default="c2",
                     help="c4: the batched broadband scan (2048 instances in one CUDA graph); "
                          "c5: the learned surrogate (train on RSI fields, compare)")
     ap.add_argument("--fields", type=int, default=20000, help="c5: training fields")
@@ -714,6 +714,128 @@ def run_raytrace_f2(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sequences_f3(args):
+    """f3: Halton (the paper's points) against scrambled Sobol, side by side:
+    on-axis error of the flat piston (closed form) and of the focused cap
+    (O'Neil's closed form) for N = 2^8 .. 2^18 points, FP64 stage so that
+    only the QMC error shows, the fitted convergence slopes, and the point
+    generation rate of both sequences."""
+    import numpy as np
+    import torch
+    from paper_2408_06765_gb300 import build, rsi
+    build.build()
+    rsi.load()
+    mm, f, c = 1e-3, 2.5e6, 1480.0
+    k = 2 * math.pi * f / c
+    a, R = 6.35 * mm, 33 * mm
+    z = np.linspace(5 * mm, 60 * mm, 56)
+    flat = 1.0 / (1j * k) * (np.exp(1j * k * z) - np.exp(1j * k * np.sqrt(z * z + a * a)))
+    zc = np.linspace(3 * mm, 45 * mm, 43)
+    zc = zc[np.abs(zc - R) > 0.5 * mm]
+    r_rim = np.sqrt(R * R + (R - zc) ** 2 - 2 * R * (R - zc) * math.sqrt(1 - (a / R) ** 2))
+    cap = -(R / (1j * k * (R - zc))) * (np.exp(1j * k * r_rim) - np.exp(1j * k * zc))
+    surfaces = {"flat": ({"kind": "disk", "centre": (0.0, 0.0, 0.0), "a": a}, z, flat),
+                "cap": ({"kind": "cap", "centre": (0.0, 0.0, 0.0), "a": a, "R": R}, zc, cap)}
+    ws = rsi.Workspace()
+    st = rsi.stage_struct(rsi.STAGE_PISTON, "fp64", k, 1.0)
+    out = {}
+    for sname, (surf, zs, exact) in surfaces.items():
+        tgt = rsi.Points(len(zs))
+        for key, vals in (("X", 0 * zs), ("Y", 0 * zs), ("Z", zs)):
+            tgt.field(key).copy_(torch.tensor(vals, dtype=torch.float64))
+        for key, vals in (("XH", 0 * zs), ("XL", 0 * zs), ("YH", 0 * zs), ("YL", 0 * zs)):
+            tgt.field(key).copy_(torch.tensor(vals, dtype=torch.float32))
+        tgt.field("ZH").copy_(torch.tensor(zs, dtype=torch.float32))
+        tgt.field("ZL").copy_(torch.tensor(zs - zs.astype(np.float32).astype(np.float64), dtype=torch.float32))
+        for seq in ("sobol", "halton"):
+            rows = []
+            for m in range(8, 19):
+                src = rsi.make_qmc_points(dict(surf, sequence=seq), 0, 0, 1 << m)
+                phi = rsi.propagate_stage(st, src, None, tgt, workspace=ws).cpu().numpy()
+                rows.append([1 << m, float(np.linalg.norm(phi - exact) / np.linalg.norm(exact))])
+            n = np.log([r[0] for r in rows])
+            e = np.log([r[1] for r in rows])
+            out[f"{sname}_{seq}"] = {"n_and_rel_l2": rows, "slope": float(np.polyfit(n, e, 1)[0])}
+    # generation rate: 2^24 points of each sequence on the piston
+    rates = {}
+    for seq in ("sobol", "halton"):
+        pts = rsi.Points(1 << 24)
+        surf = {"kind": "disk", "centre": (0.0, 0.0, 0.0), "a": a, "sequence": seq}
+        for _ in range(3):
+            rsi.make_qmc_points(surf, 0, 0, 1 << 24, out=pts)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            rsi.make_qmc_points(surf, 0, 0, 1 << 24, out=pts)
+        e1.record()
+        e1.synchronize()
+        rates[seq] = 10 * (1 << 24) / (e0.elapsed_time(e1) * 1e-3)
+    rsi.sync_status()
+    line = {"config": {"workload": "f3 QMC point sets: on-axis field of a 6.35 mm flat piston and of the "
+                                   "focused cap (R = 33 mm) at 2.5 MHz in water against their closed forms, "
+                                   "N = 2^8 .. 2^18 points, FP64 stage",
+                       "scrambled_sobol_seed": 0},
+            "convergence": out, "points_per_s": rates, "gpu": torch.cuda.get_device_name(0)}
+    print(json.dumps(line), flush=True)
+
+
+def run_focused_f4(args):
+    """f4: the focused transducer through both models (RSI chain and ray
+    tracing) at full size; errors against the stored oracle pixels."""
+    import numpy as np
+    import torch
+    from paper_2408_06765_gb300 import build, rsi
+    from paper_2408_06765_gb300 import workloads as W
+    build.build()
+    rsi.load()
+    dev = torch.device("cuda", 0)
+    cfg = W.f4_focused()
+    g = cfg["grid"]
+    pixels = int(g["nx"]) * int(g["nz"])
+    ws = rsi.Workspace(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    models = {"rsi_chain": (lambda: rsi.run_chain(cfg, fmt="c64", workspace=ws, device=dev).image, W.pairs_of(cfg)),
+              "ray_tracing": (lambda: rsi.run_raytrace(cfg, fmt="c64", workspace=ws, device=dev),
+                              int(cfg["piston"]["n"]) * pixels)}
+    res = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, (step, pairs) in models.items():
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            img = step()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        err = None
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                            ("f4_chain" if name == "rsi_chain" else "f4_ray") + "_2.5MHz.json")
+        if os.path.exists(path):
+            rec = json.load(open(path))
+            got = img.reshape(-1).cpu().numpy().astype(np.complex128)[np.asarray(rec["pixels"])]
+            want = np.asarray(rec["re"]) + 1j * np.asarray(rec["im"])
+            err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        t = sum(ms) * 1e-3
+        res[name] = {"pair_terms_per_s": pairs * args.steps / t, "ms_per_image": t * 1e3 / args.steps,
+                     "pairs": pairs, "field_pts_per_s": pixels * args.steps / t,
+                     "rel_l2_vs_stored_oracle_1024_pixels": err}
+    clk = clocks.stop()
+    rsi.sync_status()
+    line = {"config": {"workload": "f4 focused transducer: spherical cap a = 6.35 mm, R = 33 mm, 2^16 points, "
+                                   "2.5 MHz, 10 mm water -> steel, 2^18 interface points on 40 mm, 512^2 image "
+                                   "over 20 x 30 mm of steel around the focus",
+                       "l2_flush": "256 MiB write before every step"},
+            "steps": args.steps, "warmup": max(3, args.warmup), "models": res, "clocks": clk,
+            "gpu": torch.cuda.get_device_name(dev)}
+    print(json.dumps(line), flush=True)
+
+
 def measured_peaks():
     """Copy bandwidth and bf16 GEMM throughput measured on this GPU model
     (MEASURED_PEAKS.json beside this file), else the fallback figures."""
@@ -859,6 +981,10 @@ def main():
         run_two_medium_f1(args)
     elif args.config == "f2" and args.impl == "ours":
         run_raytrace_f2(args)
+    elif args.config == "f3" and args.impl == "ours":
+        run_sequences_f3(args)
+    elif args.config == "f4" and args.impl == "ours":
+        run_focused_f4(args)
     elif args.config == "c4" and args.impl == "ours" and args.case == "chain":
         run_batch_c4(args)
     elif args.case == "stage":

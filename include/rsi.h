@@ -74,17 +74,28 @@ int64_t rsi_points_offset(int32_t field, int64_t n); /* -1 for an unknown field 
 enum rsi_surface_kind {
     RSI_SURF_DISK = 0, /* piston face: radius a, centre, tilt about +y          */
     RSI_SURF_RECT = 1, /* flat interface patch wx x wy at z = centre[2], normal +z */
-    RSI_SURF_CYL = 2   /* cylinder, axis parallel to y through (cx, ., cz + R)  */
+    RSI_SURF_CYL = 2,  /* cylinder, axis parallel to y through (cx, ., cz + R)  */
+    RSI_SURF_CAP = 3   /* focused transducer: spherical cap of aperture radius a
+                          and radius of curvature R > a, apex at centre, centre
+                          of curvature R along the (tilted) axis (Sec. 3.3)   */
+};
+enum rsi_sequence {
+    RSI_SEQ_SOBOL = 0, /* scrambled (or plain) Sobol dimensions 1-2             */
+    RSI_SEQ_HALTON = 1 /* the Halton points 1..n in bases 2 and 3 (Sec. 2.3)    */
 };
 
 typedef struct rsi_surface {
     int32_t kind;     /* enum rsi_surface_kind                                  */
     int32_t scramble; /* 1: nested bit scramble of the Sobol digits; 0: plain   */
-    double centre[3]; /* DISK: face centre; RECT: patch centre; CYL: apex point */
-    double tilt;      /* DISK: rotation about +y (rad), normal (sin t, 0, cos t)*/
-    double a;         /* DISK: radius (m)                                       */
+    double centre[3]; /* DISK: face centre; RECT: patch centre; CYL, CAP: apex  */
+    double tilt;      /* DISK, CAP: rotation about +y (rad), axis (sin t, 0, cos t) */
+    double a;         /* DISK: radius; CAP: aperture radius (m)                 */
     double wx, wy;    /* RECT, CYL: side lengths of the (projected) patch (m)   */
-    double R;         /* CYL: radius of curvature (m), R > wx / 2               */
+    double R;         /* CYL, CAP: radius of curvature (m); CYL R > wx/2, CAP R > a */
+    int32_t sequence; /* enum rsi_sequence (HALTON needs scramble = 0)          */
+    int32_t reserved;
+    double apod;      /* DISK, CAP: Gaussian profile radius g: weights times
+                         exp(-(r/g)^2), r the radius in the aperture; 0 = uniform */
 } rsi_surface;
 
 /* Steps a1-a2.  Sobol points 0..n-1 of the set (seed, set_id), dimensions 1
@@ -93,7 +104,12 @@ typedef struct rsi_surface {
  * the surface: DISK r = a sqrt(u), theta = 2 pi v (Eq. circle_sampling);
  * RECT x = cx + wx (u - 1/2), y = cy + wy (v - 1/2) (Eq. square_sampling);
  * CYL the same (x, y) with z = cz + R - sqrt(R^2 - (x - cx)^2) and Jacobian
- * R / sqrt(R^2 - (x - cx)^2) in the weight; u = (su + 1/2) 2^-32.
+ * R / sqrt(R^2 - (x - cx)^2) in the weight; CAP the disk's (r, theta) lifted
+ * onto the sphere (height R - sqrt(R^2 - r^2), Jacobian R / sqrt(R^2 - r^2),
+ * normal to the centre of curvature); u = (su + 1/2) 2^-32.  HALTON sets
+ * hold points 1..n: su = the base-2 radical inverse as a 32-bit fraction,
+ * sv = the base-3 one as a fraction of 3^20 (u = su 2^-32, v = sv / 3^20),
+ * stored in index order (slot i = point i + 1).
  * Layout: points are stored in CELL ORDER, not index order: n is split into
  * aligned power-of-two blocks (its binary digits, largest first); within a
  * block of 2^m points, point i goes to slot block_start + morton(cx, cy) with

@@ -322,7 +322,7 @@ def chain(cfg: dict, targets: dict | None = None, nthreads: int | None = None,
     C = snell_invariant(cfg)
     mode = cfg.get("tmode", "global")
     pc = cfg["piston"]
-    piston = make_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]))
+    piston = make_points(dict({"kind": "disk"}, **pc), seed, int(pc.get("set_id", 0)), int(pc["n"]))
     ifaces = []
     for it in cfg["interfaces"]:
         ifaces.append(make_points(it, seed, int(it["set_id"]), int(it["n"])))
@@ -368,7 +368,7 @@ def two_medium(cfg: dict, nthreads: int | None = None, parts: bool = False, pixe
     mode = cfg.get("tmode", "global")
     k1, k2 = wavenumber(freq, m[0]["c"]), wavenumber(freq, m[1]["c"])
     pc, it = cfg["piston"], cfg["interfaces"][0]
-    piston = make_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]))
+    piston = make_points(dict({"kind": "disk"}, **pc), seed, int(pc.get("set_id", 0)), int(pc["n"]))
     iface = make_points(it, seed, int(it["set_id"]), int(it["n"]))
     gw, gs = grid_points(cfg["grid_water"]), grid_points(cfg["grid_solid"])
     n_w = int(cfg["grid_water"]["nx"]) * int(cfg["grid_water"]["nz"])
@@ -428,7 +428,7 @@ def raytrace_image(cfg: dict, nthreads: int | None = None, pixels=None):
     freq, v0 = float(cfg["freq"]), float(cfg.get("v0", 1.0))
     m = cfg["media"]
     pc = cfg["piston"]
-    piston = make_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]))
+    piston = make_points(dict({"kind": "disk"}, **pc), seed, int(pc.get("set_id", 0)), int(pc["n"]))
     zI = float(cfg["interfaces"][0]["centre"][2])
     g = cfg["grid"]
     tg = grid_points(g)

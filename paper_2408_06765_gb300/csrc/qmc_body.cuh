@@ -52,8 +52,8 @@ __device__ __forceinline__ uint32_t nested_scramble(uint32_t x, uint64_t key) {
 }
 
 struct SurfaceDev {
-    int kind;
-    double cx, cy, cz, tilt_c, tilt_s, a, wx, wy, R;
+    int kind, seq;
+    double cx, cy, cz, tilt_c, tilt_s, a, wx, wy, R, apod;
 };
 
 inline SurfaceDev surface_dev(const rsi_surface& s) {
@@ -68,11 +68,17 @@ inline SurfaceDev surface_dev(const rsi_surface& s) {
     d.wx = s.wx;
     d.wy = s.wy;
     d.R = s.R;
+    d.seq = s.sequence;
+    d.apod = s.apod;
     return d;
 }
 
 // host-side check of a surface description; RSI_OK or an RSI_E_INVAL message
 inline int check_surface(const rsi_surface& s) {
+    if (s.sequence != RSI_SEQ_SOBOL && s.sequence != RSI_SEQ_HALTON)
+        return rsi_fail(RSI_E_INVAL, "unknown point sequence %d", s.sequence);
+    if (s.sequence == RSI_SEQ_HALTON && s.scramble) return rsi_fail(RSI_E_INVAL, "Halton points are not scrambled");
+    if (!(s.apod >= 0.0) || !isfinite(s.apod)) return rsi_fail(RSI_E_INVAL, "apodisation radius must be >= 0");
     switch (s.kind) {
         case RSI_SURF_DISK:
             if (!(s.a > 0)) return rsi_fail(RSI_E_INVAL, "disk radius must be > 0");
@@ -83,6 +89,9 @@ inline int check_surface(const rsi_surface& s) {
         case RSI_SURF_CYL:
             if (!(s.wx > 0 && s.wy > 0 && s.R > 0.5 * s.wx))
                 return rsi_fail(RSI_E_INVAL, "cylinder needs wx, wy > 0 and R > wx/2");
+            return RSI_OK;
+        case RSI_SURF_CAP:
+            if (!(s.a > 0 && s.R > s.a)) return rsi_fail(RSI_E_INVAL, "spherical cap needs a > 0 and R > a");
             return RSI_OK;
         default:
             return rsi_fail(RSI_E_INVAL, "unknown surface kind %d", s.kind);
@@ -108,34 +117,70 @@ __device__ __forceinline__ uint64_t cell_slot(uint64_t i, uint64_t n, uint32_t s
     return start + pos;
 }
 
-// point i (0 <= i < n) of a set, written to its cell-order slot
+// base-3 radical inverse of i < 3^20 as a fraction of 3^20 (digits reversed)
+__device__ __forceinline__ uint32_t radical_inverse3(uint32_t i) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int d = 0; d < 20; ++d) {
+        const uint32_t q = i / 3u;
+        r = 3u * r + (i - 3u * q);
+        i = q;
+    }
+    return r;
+}
+
+// point i (0 <= i < n) of a set, written to its slot (cell order for Sobol,
+// index order for Halton)
 __device__ __forceinline__ void make_point(const SurfaceDev& s, const SobolDirs& dirs, uint64_t k0, uint64_t k1,
                                            int scramble, int64_t i, int64_t n, const PointsView& out) {
     uint32_t ix = uint32_t(i);
-    uint32_t x = __brev(ix);  // v_j = 2^(32-j): bit j-1 of i -> bit 32-j of x
-    uint32_t y = 0;
+    uint32_t x, y;
+    double u, v;
+    if (s.seq == RSI_SEQ_HALTON) {  // Halton point i + 1
+        ix = uint32_t(i + 1);
+        x = __brev(ix);
+        y = radical_inverse3(ix);
+        u = double(x) * (1.0 / 4294967296.0);
+        v = double(y) / 3486784401.0;
+    } else {
+        x = __brev(ix);  // v_j = 2^(32-j): bit j-1 of i -> bit 32-j of x
+        y = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
-        if ((ix >> j) & 1u) y ^= dirs.v1[j];
-    if (scramble) {
-        x = nested_scramble(x, k0);
-        y = nested_scramble(y, k1);
+        for (int j = 0; j < 32; ++j)
+            if ((ix >> j) & 1u) y ^= dirs.v1[j];
+        if (scramble) {
+            x = nested_scramble(x, k0);
+            y = nested_scramble(y, k1);
+        }
+        u = (double(x) + 0.5) * (1.0 / 4294967296.0);
+        v = (double(y) + 0.5) * (1.0 / 4294967296.0);
     }
-    const double u = (double(x) + 0.5) * (1.0 / 4294967296.0);
-    const double v = (double(y) + 0.5) * (1.0 / 4294967296.0);
     double px, py, pz, nx, ny, nz, w;
-    if (s.kind == RSI_SURF_DISK) {
+    if (s.kind == RSI_SURF_DISK || s.kind == RSI_SURF_CAP) {
         double r = s.a * sqrt(u);
         double sn, cs;
         sincospi(2.0 * v, &sn, &cs);
         double l1 = r * cs, l2 = r * sn;
-        px = s.cx + l1 * s.tilt_c;
-        py = s.cy + l2;
-        pz = s.cz - l1 * s.tilt_s;
-        nx = s.tilt_s;
-        ny = 0.0;
-        nz = s.tilt_c;
         w = M_PI * s.a * s.a / double(n);
+        if (s.kind == RSI_SURF_DISK) {
+            px = s.cx + l1 * s.tilt_c;
+            py = s.cy + l2;
+            pz = s.cz - l1 * s.tilt_s;
+            nx = s.tilt_s;
+            ny = 0.0;
+            nz = s.tilt_c;
+        } else {  // lifted onto the sphere; normal to the centre of curvature
+            const double q = sqrt(s.R * s.R - r * r), h = s.R - q;
+            px = s.cx + l1 * s.tilt_c + h * s.tilt_s;
+            py = s.cy + l2;
+            pz = s.cz - l1 * s.tilt_s + h * s.tilt_c;
+            const double m1 = -l1 / s.R, m2 = -l2 / s.R, m3 = q / s.R;
+            nx = m1 * s.tilt_c + m3 * s.tilt_s;
+            ny = m2;
+            nz = -m1 * s.tilt_s + m3 * s.tilt_c;
+            w *= s.R / q;
+        }
+        if (s.apod > 0.0) w *= exp(-(r / s.apod) * (r / s.apod));
     } else {
         double xi = s.wx * (u - 0.5);
         px = s.cx + xi;
@@ -155,7 +200,7 @@ __device__ __forceinline__ void make_point(const SurfaceDev& s, const SobolDirs&
             w = s.wx * s.wy / double(n);
         }
     }
-    uint64_t slot = cell_slot(uint64_t(i), uint64_t(n), x, y);
+    const uint64_t slot = s.seq == RSI_SEQ_HALTON ? uint64_t(i) : cell_slot(uint64_t(i), uint64_t(n), x, y);
     out.idx[slot] = ix;
     out.su[slot] = x;
     out.sv[slot] = y;

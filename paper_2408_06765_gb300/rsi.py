@@ -26,7 +26,8 @@ PF = dict(IDX=0, SU=1, SV=2, X=3, Y=4, Z=5, NX=6, NY=7, NZ=8, W=9,
 PF_DTYPE = {**{k: torch.int32 for k in ("IDX", "SU", "SV")},
             **{k: torch.float64 for k in ("X", "Y", "Z", "NX", "NY", "NZ", "W")},
             **{k: torch.float32 for k in ("XH", "XL", "YH", "YL", "ZH", "ZL")}}
-SURF = {"disk": 0, "rect": 1, "cyl": 2}
+SURF = {"disk": 0, "rect": 1, "cyl": 2, "cap": 3}
+SEQ = {"sobol": 0, "halton": 1}
 STAGE_PISTON, STAGE_RSI = 0, 1
 PREC = {"fp64": 0, "fp32c": 1}
 NORMALS_Z, NORMALS_POINTS, NORMALS_NEG_Z, NORMALS_POINTS_NEG = 0, 1, 2, 3
@@ -51,7 +52,8 @@ class Surface(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("scramble", ctypes.c_int32),
                 ("centre", ctypes.c_double * 3), ("tilt", ctypes.c_double),
                 ("a", ctypes.c_double), ("wx", ctypes.c_double), ("wy", ctypes.c_double),
-                ("R", ctypes.c_double)]
+                ("R", ctypes.c_double), ("sequence", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("apod", ctypes.c_double)]
 
 
 class Grid(ctypes.Structure):
@@ -201,6 +203,10 @@ def surface_struct(surf: dict, scramble: bool = True) -> Surface:
     s.wx = float(surf.get("wx", 0.0))
     s.wy = float(surf.get("wy", 0.0))
     s.R = float(surf.get("R", 0.0))
+    s.sequence = SEQ[surf.get("sequence", "sobol")]
+    if s.sequence == SEQ["halton"]:
+        s.scramble = 0
+    s.apod = float(surf.get("apod", 0.0))
     return s
 
 
@@ -388,7 +394,7 @@ def run_chain(cfg: dict, precision: str | None = None, targets: Points | None = 
     C = snell_invariant(cfg)
     mode = cfg.get("tmode", "global")
     pc = cfg["piston"]
-    piston = make_qmc_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]),
+    piston = make_qmc_points(dict({"kind": "disk"}, **pc), seed, int(pc.get("set_id", 0)), int(pc["n"]),
                              device=device, stream=stream)
     ifaces = [make_qmc_points(it, seed, int(it["set_id"]), int(it["n"]), device=device, stream=stream)
               for it in cfg["interfaces"]]
@@ -446,7 +452,7 @@ def run_raytrace(cfg: dict, fmt: str = "c128", workspace: Workspace | None = Non
     (medium 2, below the plane interface at the interface centre's z)."""
     seed = int(cfg.get("seed", 0))
     pc = cfg["piston"]
-    piston = make_qmc_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]),
+    piston = make_qmc_points(dict({"kind": "disk"}, **pc), seed, int(pc.get("set_id", 0)), int(pc["n"]),
                              device=device, stream=stream)
     tgt = grid_points(cfg["grid"], device=device, stream=stream)
     rt = raytrace_struct(cfg, **shape)
@@ -477,7 +483,7 @@ def run_two_medium(cfg: dict, precision: str | None = None, fmt: str = "c128",
     mode = cfg.get("tmode", "global")
     k1, k2 = wavenumber(freq, m[0]["c"]), wavenumber(freq, m[1]["c"])
     pc, it = cfg["piston"], cfg["interfaces"][0]
-    piston = make_qmc_points(dict(pc, kind="disk"), seed, int(pc.get("set_id", 0)), int(pc["n"]),
+    piston = make_qmc_points(dict({"kind": "disk"}, **pc), seed, int(pc.get("set_id", 0)), int(pc["n"]),
                              device=device, stream=stream)
     iface = make_qmc_points(it, seed, int(it["set_id"]), int(it["n"]), device=device, stream=stream)
     gw_cfg, gs_cfg = cfg["grid_water"], cfg["grid_solid"]
@@ -520,7 +526,7 @@ def batch_instance(cfg: dict) -> BatchInstance:
         raise ValueError("batched chains have exactly one interface")
     b = BatchInstance()
     pc, it = cfg["piston"], cfg["interfaces"][0]
-    b.piston = surface_struct(dict(pc, kind="disk"))
+    b.piston = surface_struct(dict({"kind": "disk"}, **pc))
     b.iface = surface_struct(it)
     b.n_piston, b.n_iface = int(pc["n"]), int(it["n"])
     b.piston_set, b.iface_set = int(pc.get("set_id", 0)), int(it["set_id"])

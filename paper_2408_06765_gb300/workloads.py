@@ -131,6 +131,47 @@ def f2_small() -> dict:
     return cfg
 
 
+def f3_halton(apod: float = 0.0) -> dict:
+    """c1 with the paper's own point sets: Halton points 1..4096 on the
+    piston and on the 60 x 60 mm patch (Sec. 2.3), FP32C; apod > 0 gives the
+    piston a Gaussian velocity profile of that radius (Sec. 4)."""
+    cfg = c1_plain_fp64()
+    cfg["name"] = "f3_halton" + ("_apodised" if apod else "")
+    cfg["precision"] = "fp32c"
+    cfg["piston"].update({"sequence": "halton", "apod": float(apod)})
+    cfg["interfaces"][0]["sequence"] = "halton"
+    return cfg
+
+
+F4_R = 33 * MM  # radius of curvature: focal length 14 mm in steel behind 10 mm of water (Sec. 3.3)
+
+
+def f4_focused(freq: float = 2.5 * MHZ, n_piston: int = 1 << 16, n_iface: int = 1 << 18, nx: int = 512,
+               nz: int = 512, patch: float = 40 * MM, half_width: float = 10 * MM, depth: float = 30 * MM) -> dict:
+    """Focused transducer (Sec. 3.3, Fig. transducer_system b): a spherical
+    cap of aperture radius 6.35 mm and radius of curvature 33 mm, 10 mm of
+    water to the steel, 2.5 MHz; 2^16 points on the cap, 2^18 on a 40 x 40 mm
+    patch (about three transducer diameters, Eq. square_sampling), 512 x 512
+    image over x in [-10, 10] mm, z in (10, 40] mm of steel around the focus."""
+    zi = 10 * MM
+    return {
+        "name": f"f4_focused_{freq / MHZ:g}MHz", "freq": float(freq), "v0": 1.0, "seed": 0, "precision": "fp32c",
+        "piston": {"kind": "cap", "a": 6.35 * MM, "R": F4_R, "centre": (0.0, 0.0, 0.0), "tilt": 0.0,
+                   "n": int(n_piston), "set_id": 0},
+        "media": [dict(WATER), dict(STEEL)],
+        "interfaces": [_rect((0.0, 0.0, zi), patch, n_iface, 1)],
+        "tmode": "global",
+        "grid": {"x0": -half_width, "x1": half_width, "nx": int(nx), "z0": zi, "z1": zi + depth, "nz": int(nz),
+                 "y": 0.0},
+    }
+
+
+def f4_small() -> dict:
+    """f4 at sizes the oracle finishes in a second (ragged counts)."""
+    return f4_focused(n_piston=3001, n_iface=6000, nx=37, nz=29, patch=20 * MM, half_width=5 * MM,
+                      depth=15 * MM)
+
+
 def f1_small() -> dict:
     """f1 at sizes the oracle finishes in a second, still resolving the
     water wavelength on the interface (2.25 MHz, 12 000 points on 40 mm):

@@ -11,7 +11,7 @@ Workloads: c2 at 2.25, 5 and 10 MHz (2^16 x 2^18 points, 512^2 image), the
 multilayer c3 workload, flat and curved (9 interfaces of 2^16 points), and the
 two-medium image f1 (incident + reflected field above the interface,
 transmitted field below, oracle.two_medium) and the ray-tracing model f2
-(oracle.raytrace_image).
+(oracle.raytrace_image); the focused transducer f4 through both models.
 """
 from __future__ import annotations
 
@@ -38,6 +38,8 @@ def cases():
     out["c3_curved"] = W.c3_multilayer(curved=True)
     out["f1_5MHz"] = W.f1_two_medium()
     out["f2_5MHz"] = W.f2_ray_tracing()
+    out["f4_chain_2.5MHz"] = W.f4_focused()
+    out["f4_ray_2.5MHz"] = W.f4_focused()
     return out
 
 
@@ -96,7 +98,7 @@ if __name__ == "__main__":
         if not want or name in want:
             if "grid_water" in cfg:
                 make_two_medium(name, cfg)
-            elif name.startswith("f2"):
+            elif name.startswith("f2") or name.startswith("f4_ray"):
                 make_ray(name, cfg)
             else:
                 make(name, cfg)
