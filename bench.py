@@ -35,8 +35,12 @@ if ROOT not in sys.path:
 # operations, and shared-memory loads per pair at 2 targets per thread (two
 # 16-byte records per source shared by the thread's 2 targets).
 OPS = {
-    "rsi": {"fp32": 23, "mufu": 3, "lds": 1.0},
-    "piston": {"fp32": 13, "mufu": 3, "lds": 1.0},
+    # FP32-pipe warp instructions, MUFU operations and shared loads per pair of
+    # the default kernel (two sources per packed f32x2 instruction): RSI 22
+    # packed per two pairs plus one scalar scaling of the sincos argument per
+    # pair; piston 14 packed per two pairs plus the same scaling
+    "rsi": {"fp32": 12, "mufu": 3, "lds": 1.0},
+    "piston": {"fp32": 8, "mufu": 3, "lds": 1.0},
     # ray-tracing pair (Sec. 2.2): linear prediction of the crossing from the
     # tile's reference ray, then 2 safeguarded Newton steps (~29 FP32 and 3
     # MUFU each); ~88 FP32 and 11 MUFU around them
@@ -57,7 +61,9 @@ def parse():
                     help="target duration of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--case", choices=["chain", "stage"], default="chain",
+    ap.add_argument("--small", action="store_true",
+                    help="f2: 2^14 transducer points onto 256^2 pixels (a profiling case)")
+    ap.add_argument("--case", choices=["chain", "stage", "gemm"], default="chain",
                     help="stage: only the RSI interface -> image kernel of the 10 MHz c2 chain "
                          "on a 256 x 256 image (small case for profiler captures)")
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
@@ -303,8 +309,10 @@ def run_ours(args):
     ws = rsi.Workspace(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    opts = {"variant": args.variant} if args.variant else None
+
     def step():
-        return [rsi.run_chain(c, fmt="c64", workspace=ws, device=dev).image for c in cfgs]
+        return [rsi.run_chain(c, fmt="c64", workspace=ws, device=dev, stage_opts=opts).image for c in cfgs]
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -350,7 +358,7 @@ def run_ours(args):
             "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
             "limiter": limiter,
             "ops_per_pair": OPS["rsi"],
-            "peak_source": "unit counts (128 issue lanes, 16 MUFU lanes per SM per clock) x "
+            "peak_source": "unit counts (4 issue slots of 32 lanes and 16 MUFU lanes per SM per clock) x "
                            f"{n_sm} SMs x the median SM clock of the timed region "
                            f"({clk_hz / 1e6:.0f} MHz)",
             "probe_rates_tops": {k: v / 1e12 for k, v in rates.items()},
@@ -473,7 +481,7 @@ def run_stage_case(args):
     ws = rsi.Workspace()
     shapes = [(args.tile, args.tpt, args.variant)]
     if args.sweep:
-        shapes = [(t, q, v) for t in (64, 128, 256, 512) for q in (2, 4) for v in (1, 2)]
+        shapes = [(t, q, v) for t in (64, 128, 256, 512) for q in (2, 4) for v in (1, 2, 3)]
     for tile, tpt, variant in shapes:
         st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", rsi.wavenumber(cfg["freq"], 5900.0),
                               normals=rsi.NORMALS_Z, tile=tile, tpt=tpt, variant=variant)
@@ -657,7 +665,7 @@ def run_raytrace_f2(args):
     build.build()
     rsi.load()
     dev = torch.device("cuda", 0)
-    cfg = W.f2_ray_tracing()
+    cfg = W.f2_ray_tracing(n_piston=1 << 14, nx=256, nz=256) if args.small else W.f2_ray_tracing()
     g = cfg["grid"]
     pixels = int(g["nx"]) * int(g["nz"])
     pairs = int(cfg["piston"]["n"]) * pixels
@@ -692,7 +700,7 @@ def run_raytrace_f2(args):
     achieved = rt_pairs / (rt_ms * 1e-3)
     err = None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "f2_5MHz.json")
-    if os.path.exists(path):
+    if os.path.exists(path) and not args.small:
         rec = json.load(open(path))
         got = img.reshape(-1).cpu().numpy().astype(np.complex128)[np.asarray(rec["pixels"])]
         want = np.asarray(rec["re"]) + 1j * np.asarray(rec["im"])
@@ -712,6 +720,35 @@ def run_raytrace_f2(args):
                          "limiter": limiter, "ops_per_pair": OPS["raytrace"], "launches": rt_n},
             "clocks": clk, "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev)}
     print(json.dumps(line), flush=True)
+
+
+def run_gemm_case(args):
+    """The surrogate's dominant kernel alone: the output-layer GEMM of batch-1024
+    inference, [1024 x 512] x [512 x 32768] + bias with an f32 output, `steps`
+    times on random BF16 operands (the GEMM engine of --engine)."""
+    import torch
+    from paper_2408_06765_gb300 import build, rsi
+    build.build()
+    rsi.load()
+    g = torch.Generator(device="cuda").manual_seed(0)
+    M, N, K = 1024, 32768, 512
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    out = torch.empty(M, N, device="cuda")
+    times = []
+    for _ in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rsi.nn_gemm("f32", A, B, out_f32=out, bias=bias, engine=args.engine)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    rsi.sync_status()
+    ms = min(times[args.warmup:])
+    nbytes = 2.0 * (A.numel() + B.numel()) + 4.0 * (out.numel() + bias.numel())
+    print(json.dumps({"case": "gemm", "engine": args.engine, "M": M, "N": N, "K": K, "ms": ms,
+                      "tflops": 2.0 * M * N * K / ms / 1e9, "gbytes_per_s": nbytes / ms / 1e6}), flush=True)
 
 
 def run_sequences_f3(args):
@@ -989,6 +1026,8 @@ def main():
         run_batch_c4(args)
     elif args.case == "stage":
         run_stage_case(args)
+    elif args.case == "gemm":
+        run_gemm_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -165,7 +165,8 @@ typedef struct rsi_stage {
     int32_t tile;      /* sources per shared-memory tile (64, 128, 256); 0 = auto */
     int32_t tpt;       /* targets per thread (FP32C: 2 or 4; FP64: 1); 0 = auto   */
     int32_t splits;    /* source splits (>= 1); 0 = auto                          */
-    int32_t variant;   /* FP32C distance update: 0 = auto, 1 = reciprocal, 2 = Newton */
+    int32_t variant;   /* FP32C distance update: 0 = auto, 1 = reciprocal, 2 = Newton,
+                          3 = Newton on two sources per packed f32x2 instruction */
     int32_t reserved;
 } rsi_stage;
 

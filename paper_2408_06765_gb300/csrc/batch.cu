@@ -112,14 +112,14 @@ __global__ void batch_grid_kernel(const BGrid* __restrict__ grids, const BSeg* _
     if (q < int64_t(G.g.nx) * G.g.nz) rsi_qmc::make_grid_point(G.g, q, G.out);
 }
 
-__global__ void batch_prep_kernel(const BPrep* __restrict__ preps, const BPrepTile* __restrict__ tiles) {
+__global__ void batch_prep_kernel(const BPrep* __restrict__ preps, const BPrepTile* __restrict__ tiles, int packed) {
     __shared__ double red[32];
     const BPrepTile t = tiles[blockIdx.x];
     const BPrep& p = preps[t.inst];
     // all instances share the CTA size; tiles of smaller instances use fewer
     // threads, and the extra threads take part only in the reductions
     rsi_fp32::prep_tile(p.kind, p.normals, p.S, p.n_src, p.src, p.sigma, p.amp_scale, p.k, p.tiles,
-                        p.tile_bytes, t.tile, red);
+                        p.tile_bytes, t.tile, red, packed != 0);
 }
 
 template <int KIND, int NORM, int TPT, int VAR>
@@ -215,7 +215,7 @@ void append_segments(std::vector<BSeg>& segs, int32_t set, int64_t n) {
 // ---------------------------------------------------------------------------
 struct rsi_batch_plan {
     int n_inst = 0;
-    int S_max = 256, tpt = 2, variant = 2, normals2 = RSI_NORMALS_Z;
+    int S_max = 256, tpt = 2, variant = 3, normals2 = RSI_NORMALS_Z;
     size_t ws_bytes = 0, img_elems = 0, max_tile1 = 0, max_tile2 = 0;
     std::vector<uint8_t> blob;  // device tables, uploaded to workspace offset 0
     // table offsets (bytes) in the blob / workspace
@@ -463,10 +463,14 @@ int launch_batch_stage_v(const rsi_batch_plan& P, uint8_t* ws, size_t o_st, size
     if (P.tpt == 4) {
         if (P.variant == 1)
             return launch_batch_stage<KIND, NORM, 4, 1>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
+        if (P.variant == 3)
+            return launch_batch_stage<KIND, NORM, 4, 3>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
         return launch_batch_stage<KIND, NORM, 4, 2>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
     }
     if (P.variant == 1)
         return launch_batch_stage<KIND, NORM, 2, 1>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
+    if (P.variant == 3)
+        return launch_batch_stage<KIND, NORM, 2, 3>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
     return launch_batch_stage<KIND, NORM, 2, 2>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
 }
 
@@ -486,7 +490,8 @@ int enqueue(rsi_batch_plan& P, uint8_t* ws, int* status, cudaStream_t s) {
         RSI_CHECK_LAUNCH("batch_grid_kernel");
     }
     batch_prep_kernel<<<unsigned(P.n_pt1), P.S_max, 0, s>>>(reinterpret_cast<const BPrep*>(ws + P.o_prep1),
-                                                            reinterpret_cast<const BPrepTile*>(ws + P.o_pt1));
+                                                            reinterpret_cast<const BPrepTile*>(ws + P.o_pt1),
+                                                            P.variant == 3 ? 1 : 0);
     RSI_CHECK_LAUNCH("batch_prep_kernel");
     int rc = launch_batch_stage_v<RSI_STAGE_PISTON, RSI_NORMALS_Z>(P, ws, P.o_st1, P.o_it1, P.n_it1, P.max_tile1,
                                                                    ctr, status, s);
@@ -500,7 +505,8 @@ int enqueue(rsi_batch_plan& P, uint8_t* ws, int* status, cudaStream_t s) {
                                                             reinterpret_cast<const BSeg*>(ws + P.o_ts));
     RSI_CHECK_LAUNCH("batch_transmit_kernel");
     batch_prep_kernel<<<unsigned(P.n_pt2), P.S_max, 0, s>>>(reinterpret_cast<const BPrep*>(ws + P.o_prep2),
-                                                            reinterpret_cast<const BPrepTile*>(ws + P.o_pt2));
+                                                            reinterpret_cast<const BPrepTile*>(ws + P.o_pt2),
+                                                            P.variant == 3 ? 1 : 0);
     RSI_CHECK_LAUNCH("batch_prep_kernel");
     if (P.normals2 == RSI_NORMALS_POINTS)
         rc = launch_batch_stage_v<RSI_STAGE_RSI, RSI_NORMALS_POINTS>(P, ws, P.o_st2, P.o_it2, P.n_it2, P.max_tile2,
@@ -542,7 +548,7 @@ extern "C" int rsi_batch_create(const rsi_batch_instance* inst, int32_t n_inst, 
         if (shape->variant) P->variant = shape->variant;
     }
     if (!(P->S_max == 32 || P->S_max == 64 || P->S_max == 128 || P->S_max == 256 || P->S_max == 512) ||
-        (P->tpt != 2 && P->tpt != 4) || (P->variant != 1 && P->variant != 2)) {
+        (P->tpt != 2 && P->tpt != 4) || (P->variant < 1 || P->variant > 3)) {
         delete P;
         return rsi_fail(RSI_E_INVAL, "rsi_batch_create: bad tile / targets per thread / variant");
     }

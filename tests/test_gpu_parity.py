@@ -168,6 +168,9 @@ def test_multilayer_reduced_counts(curved):
     {"tile": 64, "tpt": 4, "splits": 3, "variant": 2},
     {"tile": 128, "tpt": 2, "splits": 0, "variant": 2},
     {"tile": 512, "tpt": 4, "splits": 2, "variant": 1},
+    {"tile": 32, "tpt": 2, "splits": 1, "variant": 3},
+    {"tile": 256, "tpt": 4, "splits": 0, "variant": 3},
+    {"tile": 128, "tpt": 2, "splits": 5, "variant": 3},
 ])
 def test_launch_shapes_agree(opts):
     cfg = W.small_ragged("fp32c", freq=7.5e6)
@@ -176,7 +179,14 @@ def test_launch_shapes_agree(opts):
     assert rel_l2(res.image.cpu().numpy(), base.cpu().numpy()) < 2e-5
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32c"])
+@pytest.mark.parametrize("curved", [False, True])
+def test_packed_variant_multilayer(curved):
+    # two sources per f32x2 instruction, with per-point normals on the curved stack
+    cfg = W.c3_multilayer(curved=curved, n_per_surface=1 << 11)
+    chain_parity(cfg, TOL["fp32c"], stage_opts={"variant": 3})
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32c", "fp32c_packed"])
 def test_coincident_targets_contribute_nothing(prec):
     # a surface propagated onto its own points: every target coincides with one
     # source, whose term is dropped (both sides)
@@ -187,14 +197,16 @@ def test_coincident_targets_contribute_nothing(prec):
     # flat patch: every chord lies in the plane, cos(theta) = 0, the RSI field is 0
     flat = rsi.make_qmc_points({"kind": "rect", "centre": (0.0, 0.0, 0.02), "wx": 0.02, "wy": 0.02},
                                0, 1, 700)
-    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_RSI, prec, k, normals=rsi.NORMALS_Z),
+    var = 3 if prec == "fp32c_packed" else 0
+    prec = "fp32c" if prec == "fp32c_packed" else prec
+    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_RSI, prec, k, normals=rsi.NORMALS_Z, variant=var),
                               flat, sig_d, flat)
     rsi.sync_status()
     hp = host_points(flat)
     src = {"x": hp["X"], "y": hp["Y"], "z": hp["Z"], "nx": hp["NX"], "ny": hp["NY"], "nz": hp["NZ"],
            "w": hp["W"]}
     assert np.all(out.cpu().numpy() == 0) and np.all(oracle.rsi_field(src, sig, src, k) == 0)
-    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_PISTON, prec, k), flat, None, flat)
+    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_PISTON, prec, k, variant=var), flat, None, flat)
     rsi.sync_status()
     ref = oracle.piston_field(src, src, k)
     assert np.all(np.isfinite(out.cpu().numpy()))
@@ -202,7 +214,7 @@ def test_coincident_targets_contribute_nothing(prec):
     # curved surface: chords are not normal to the surface normals
     cyl = rsi.make_qmc_points({"kind": "cyl", "centre": (0.0, 0.0, 0.02), "wx": 0.03, "wy": 0.03,
                                "R": 0.02}, 0, 2, 700)
-    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_RSI, prec, k, normals=rsi.NORMALS_POINTS),
+    out = rsi.propagate_stage(rsi.stage_struct(rsi.STAGE_RSI, prec, k, normals=rsi.NORMALS_POINTS, variant=var),
                               cyl, sig_d, cyl)
     rsi.sync_status()
     hp = host_points(cyl)
