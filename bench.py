@@ -249,9 +249,12 @@ def oracle_sample(cfg, seconds: float, seed: int = 0):
         dt = time.perf_counter() - t0
         return dt, pc["n"] * len(s1) + last["n"] * len(s2), s1, phi1
 
-    dt, pairs, _, _ = run(32, 8)
+    # rate probe with enough targets to keep every thread busy, then size the
+    # sample for `seconds` of work at that rate
+    m0 = 4 * oracle.default_threads()
+    dt, pairs, _, _ = run(m0, m0)
     rate = pairs / dt
-    m = max(16, int(seconds * rate / (pc["n"] + last["n"]) / 2))
+    m = max(16, int(seconds * rate / (pc["n"] + last["n"])))
     dt, pairs, s1, phi1 = run(m, m)
     return {"seconds": dt, "pairs": pairs, "rate": pairs / dt, "m": m,
             "iface_slots_natural": s1, "phi1": phi1, "threads": oracle.default_threads()}
