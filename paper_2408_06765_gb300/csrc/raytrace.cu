@@ -55,6 +55,8 @@ struct RayRef {
     float D1, D2;      // path lengths of the reference ray
     float tau;         // k1 D1 + k2 D2 mod 2 pi
     float a_r, a_h;    // linear response of the crossing to the foot distance and the source height
+    float s2h22;       // s2 H2^2 (Snell residual slope, medium-2 term)
+    float ih22;        // 1 / H2^2
 };
 
 __device__ __forceinline__ float rsqrt_ap(float x) {
@@ -79,13 +81,13 @@ __device__ __forceinline__ void df_sqrt(float sh, float sl, float& rh, float& rl
 
 // Snell's residual of a crossing at horizontal distance t from the source
 // foot (b = rho - t beyond it): G = s1 sin a1 - s2 sin a2, and its slope
-__device__ __forceinline__ void snell_residual(float t, float b, float h1, float h2, float s1, float s2, float& G,
-                                               float& dG) {
-    float r1 = rsqrt_ap(fmaf(t, t, h1 * h1));
-    float r2 = rsqrt_ap(fmaf(b, b, h2 * h2));
+// dG = s1 h1^2 / D1^3 + s2 h2^2 / D2^3 (h1q = h1^2, s1h = s1 h1^2, s2h = s2 h2^2)
+__device__ __forceinline__ void snell_residual(float t, float b, float h1q, float h2q, float s1, float s2, float s1h,
+                                               float s2h, float& G, float& dG) {
+    const float r1 = rsqrt_ap(fmaf(t, t, h1q));
+    const float r2 = rsqrt_ap(fmaf(b, b, h2q));
     G = fmaf(s1 * t, r1, -(s2 * b) * r2);
-    float r13 = r1 * r1 * r1, r23 = r2 * r2 * r2;
-    dG = fmaf(s1 * h1 * h1, r13, s2 * h2 * h2 * r23);
+    dG = fmaf(s1h, r1 * r1 * r1, s2h * (r2 * r2 * r2));
 }
 
 __device__ __forceinline__ RayRef ray_reference(float qxh, float qxl, float qyh, float qyl, float qzh, float qzl,
@@ -113,10 +115,11 @@ __device__ __forceinline__ RayRef ray_reference(float qxh, float qxl, float qyh,
     // from the small-angle guess t = rho h1 / (h1 + (c2/c1) h2)
     float lo = 0.0f, hi = rh;
     float t = rh * __fdividef(h1h, fmaf(a.c21, h2h, h1h));
+    const float h1q = h1h * h1h, h2q = h2h * h2h;
 #pragma unroll 1
     for (int it = 0; it < 24; ++it) {
         float G, dG;
-        snell_residual(t, rh - t, h1h, h2h, a.s1, a.s2, G, dG);
+        snell_residual(t, rh - t, h1q, h2q, a.s1, a.s2, a.s1 * h1q, a.s2 * h2q, G, dG);
         if (G > 0.0f)
             hi = t;
         else
@@ -154,6 +157,8 @@ __device__ __forceinline__ RayRef ray_reference(float qxh, float qxl, float qyh,
         R.a_r = gr * ig;
         R.a_h = a.s1 * t * h1h * i13 * ig;
     }
+    R.s2h22 = a.s2 * h2q;
+    R.ih22 = 1.0f / h2q;
     // k1 D1 + k2 D2 as a double-float, reduced modulo 2 pi (Cody & Waite)
     float ph, pl, eh, el;
     two_prod(a.k1h, D1h, ph, pl);
@@ -197,34 +202,43 @@ __device__ __forceinline__ void ray_pair(const RayRef& R, const float4& rec, flo
         wy = uy - R.uy;
     }
     const float h1 = R.H1 - pz, h2 = R.H2;
+    const float h1q = h1 * h1, h2q = h2 * h2, s1h = a.s1 * h1q;
     // crossing offset dt = t - t_c along u; the legs are t_c + dt and b_c - drho - dt
     const float bfix = R.bc - drho;
-    float lo = -R.tc, hi = bfix;
+    const float lo0 = -R.tc, hi0 = bfix;
     float dt = -fmaf(R.a_r, drho, R.a_h * pz);  // linear prediction from the reference ray
-    dt = fminf(fmaxf(dt, lo), hi);
+    dt = fminf(fmaxf(dt, lo0), hi0);
     float step = INFINITY;
-    auto newton_step = [&]() {
-        float G, dG;
-        snell_residual(R.tc + dt, bfix - dt, h1, h2, a.s1, a.s2, G, dG);
-        if (G > 0.0f)
-            hi = dt;
-        else
-            lo = dt;
-        const float dn = dt - __fdividef(G, dG);
-        const float nt = (dn >= lo && dn <= hi) ? dn : 0.5f * (lo + hi);
-        step = nt - dt;
-        dt = nt;
-    };
+    // plain Newton steps (kept inside the segment) from the prediction
     const int nw = NW ? NW : a.newton;
 #pragma unroll
     for (int it = 0; it < (NW ? NW : 16); ++it) {
         if (!NW && it >= nw) break;
-        newton_step();
+        float G, dG;
+        snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG);
+        const float nt = fminf(fmaxf(dt - __fdividef(G, dG), lo0), hi0);
+        step = nt - dt;
+        dt = nt;
     }
-    // then until the crossing moves by less than kCrossTol (rays that graze
-    // the interface near the target converge more slowly)
+    // then, for the rays still moving by more than kCrossTol (those that graze
+    // the interface near the target converge more slowly), safeguarded steps:
+    // Newton inside a bracket of the monotone residual, bisection otherwise
+    if (fabsf(step) > kCrossTol) {
+        float lo = lo0, hi = hi0;
 #pragma unroll 1
-    for (int it = 0; it < kCrossExtra && fabsf(step) > kCrossTol; ++it) newton_step();
+        for (int it = 0; it < kCrossExtra && fabsf(step) > kCrossTol; ++it) {
+            float G, dG;
+            snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG);
+            if (G > 0.0f)
+                hi = dt;
+            else
+                lo = dt;
+            const float dn = dt - __fdividef(G, dG);
+            const float nt = (dn >= lo && dn <= hi) ? dn : 0.5f * (lo + hi);
+            step = nt - dt;
+            dt = nt;
+        }
+    }
     // e1 = (X - P) - (X_c - c) = (dt u + t_c (u - u_c), -p_z); e2 = -(p_h + e1_h, 0)
     const float e1x = fmaf(dt, ux, R.tc * wx), e1y = fmaf(dt, uy, R.tc * wy), e1z = -pz;
     const float e2x = -(px + e1x), e2y = -(py + e1y);
@@ -239,8 +253,8 @@ __device__ __forceinline__ void ray_pair(const RayRef& R, const float4& rec, flo
     // angles of the ray, T12 (Eq. transmission_coefficient) and the spreading
     const float cos1 = h1 * ir1, cos2 = h2 * ir2;
     const float T = __fdividef(a.Tn * cos1, fmaf(a.Td1, cos1, a.Td2 * cos2));
-    const float g = __fdividef(cos1 * cos1, cos2 * cos2);
-    const float den = fmaf(a.c21 * g, D2, D1) * fmaf(a.c21, D2, D1);
+    // cos^2 a1 / cos^2 a2 D2 = cos^2 a1 D2^3 / h2^2
+    const float den = fmaf(a.c21 * cos1 * cos1 * R.ih22, D2 * q2, D1) * fmaf(a.c21, D2, D1);
     const float amp = A * T * rsqrt_ap(den);
     float s, c;
     __sincosf(u, &s, &c);

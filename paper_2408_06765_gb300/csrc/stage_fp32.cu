@@ -8,7 +8,7 @@ namespace {
 using namespace rsi_fp32;
 
 template <int KIND, int NORM, int TPT, int VAR>
-__global__ void __launch_bounds__(kThreads, TPT == 2 ? RSI_FP32_MIN_BLOCKS : 2)
+__global__ void __launch_bounds__(kThreads, (min_blocks<KIND, TPT, VAR>()))
     stage_fp32_kernel(StageArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RSI_PIPE_STAGES * a.tile_bytes);

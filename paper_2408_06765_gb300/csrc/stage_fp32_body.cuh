@@ -32,11 +32,27 @@
 #ifndef RSI_FP32_UNROLL
 #define RSI_FP32_UNROLL 2  // unrolling of the loop over a tile's sources
 #endif
+// the packed RSI kernel (variant 3) measured best with its own settings
+#ifndef RSI_FP32_PACKED_RSI_MIN_BLOCKS
+#define RSI_FP32_PACKED_RSI_MIN_BLOCKS 2
+#endif
+#ifndef RSI_FP32_PACKED_RSI_UNROLL
+#define RSI_FP32_PACKED_RSI_UNROLL 2
+#endif
 
 namespace rsi_fp32 {
 
 constexpr int kThreads = 256;
 constexpr int kUnroll = RSI_FP32_UNROLL;
+// resident CTAs asked of the compiler, and the unrolling of the packed loop
+template <int KIND, int TPT, int VAR>
+constexpr int min_blocks() {
+    return TPT != 2 ? 2 : (KIND == RSI_STAGE_RSI && VAR == 3) ? RSI_FP32_PACKED_RSI_MIN_BLOCKS : RSI_FP32_MIN_BLOCKS;
+}
+template <int KIND>
+constexpr int packed_unroll() {
+    return KIND == RSI_STAGE_RSI ? RSI_FP32_PACKED_RSI_UNROLL : RSI_FP32_UNROLL;
+}
 
 struct TgtRef {
     float Dx, Dy, Dz, mx, my, mz, R, R2, tau;
@@ -329,7 +345,7 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
                     a1[q] = a2[q] = b1[q] = b2[q] = make_float2(0.f, 0.f);
                 }
                 const float2 k2 = make_float2(k, k);
-#pragma unroll kUnroll
+#pragma unroll packed_unroll<KIND>()
                 for (int i = 0; i < w.S / 2; ++i) {
                     const float4* pr = rec + i * 2 * rec_f4;
                     const float4 v0 = pr[0], v1 = pr[1], v2 = pr[2], v3 = pr[3];
