@@ -4,7 +4,9 @@
 
 Each .cu file is compiled by nvcc in parallel for sm_103a only, then linked
 into paper_2408_06765_gb300/_build/librsi.so (static CUDA runtime).  ptxas
-resource usage (-Xptxas -v) is kept in _build/ptxas.log.
+resource usage (-Xptxas -v) is kept in _build/ptxas.log.  RSI_BUILD_DEFINES
+(-D flags for the kernels' tuning knobs) builds into _build_<hash> instead,
+and the binding loads that library.
 """
 from __future__ import annotations
 
@@ -17,7 +19,28 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
+
+
+def extra_defines() -> list:
+    """Build-time tuning defines from RSI_BUILD_DEFINES (e.g.
+    "-DRSI_FP32_PACKED_RSI_MIN_BLOCKS=3"); only -D flags are accepted."""
+    toks = os.environ.get("RSI_BUILD_DEFINES", "").split()
+    for t in toks:
+        if not t.startswith("-D"):
+            raise ValueError(f"RSI_BUILD_DEFINES takes -D flags only, got {t!r}")
+    return toks
+
+
+def build_dir() -> str:
+    """_build, or _build_<hash> for a build with extra defines."""
+    d = extra_defines()
+    if not d:
+        return os.path.join(HERE, "_build")
+    import hashlib
+    return os.path.join(HERE, "_build_" + hashlib.sha256(" ".join(d).encode()).hexdigest()[:12])
+
+
+BUILD = build_dir()
 LIB = os.path.join(BUILD, "librsi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
@@ -52,7 +75,7 @@ def _compile(src: str, force: bool):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
     if not force and not _stale(obj, src):
         return obj, ""
-    cmd = [nvcc()] + ARCH + CFLAGS + ["-c", src, "-o", obj + ".tmp"]
+    cmd = [nvcc()] + ARCH + CFLAGS + extra_defines() + ["-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")

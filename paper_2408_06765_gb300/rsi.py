@@ -16,6 +16,11 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "librsi.so")
+
+
+def _lib_path() -> str:
+    from paper_2408_06765_gb300 import build as _build  # the same rule as the build (RSI_BUILD_DEFINES)
+    return os.path.join(_build.build_dir(), "librsi.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -101,7 +106,7 @@ def load(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        p = path or _lib_path()
         if not os.path.exists(p):
             raise RuntimeError(f"librsi.so not built ({p}); run paper_2408_06765_gb300.build")
         L = ctypes.CDLL(p)
