@@ -74,7 +74,7 @@ def parse():
                          "c5: the learned surrogate (train on RSI fields, compare)")
     ap.add_argument("--fields", type=int, default=20000, help="c5: training fields")
     ap.add_argument("--instances", type=int, default=0, help="c4: first N instances only (0 = all)")
-    ap.add_argument("--epochs", type=int, default=300, help="c5: training epochs")
+    ap.add_argument("--epochs", type=int, default=1500, help="c5: training epochs")
     ap.add_argument("--sigma-b", type=float, default=0.25, help="c5: Fourier feature scale")
     ap.add_argument("--lr", type=float, default=1e-3, help="c5: peak learning rate")
     ap.add_argument("--engine", choices=["tcgen05", "mma_sync"], default="tcgen05", help="c5: GEMM engine")
@@ -995,6 +995,8 @@ def run_surrogate_c5(args):
             "held_out_median_pre_critical": float(np.median(errs[~post])) if (~post).any() else None,
             "held_out_median_post_critical": float(np.median(errs[post])) if post.any() else None,
             "reaches_1e-3": bool(np.median(errs) <= 1e-3),
+            "held_out_fraction_below": {"1e-2": float(np.mean(errs <= 1e-2)), "3e-2": float(np.mean(errs <= 3e-2)),
+                                        "1e-1": float(np.mean(errs <= 1e-1))},
             "surrogate_fields_per_s_batch1024": nn_fields_s,
             "engine": args.engine, "train_step_ms_batch256": step_ms,
             # the f32 output (134 MB) dominates the bytes: HBM-write-bound;
