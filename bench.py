@@ -61,6 +61,8 @@ def parse():
                     help="target duration of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="run frequencies that share their points one by one instead of together")
     ap.add_argument("--small", action="store_true",
                     help="f2: 2^14 transducer points onto 256^2 pixels (a profiling case)")
     ap.add_argument("--case", choices=["chain", "stage", "gemm"], default="chain",
@@ -167,20 +169,23 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # throughput probes -> ALU roofline
 # ---------------------------------------------------------------------------
-def recorded_traffic():
-    """DRAM bytes per RSI-stage launch from the committed ncu summary, if the
-    kernel source is still the one the counters were taken on; else None."""
+def recorded_traffic(kernel: str = "stage_fp32_kernel"):
+    """DRAM bytes per RSI-stage launch of `kernel` from the committed ncu
+    summary, if the kernel source is still the one the counters were taken
+    on; else None."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", "traffic_stage_fp32_rsi_c2.md")
+    name, srcs = {"stage_fp32_kernel": ("traffic_stage_fp32_rsi_c2.md", ("stage_fp32_body.cuh", "stage_fp32.cu")),
+                  "stage_multi_kernel": ("traffic_stage_multi_rsi_c2.md", ("stage_fp32_body.cuh", "stage_multi.cu"))}[
+        kernel]
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
-    m = re.search(r"stage_fp32_kernel_rsi_dram_bytes_per_launch (\d+) source_sha256_16 (\w+)",
-                  open(path).read())
+    m = re.search(kernel + r"_rsi_dram_bytes_per_launch (\d+) source_sha256_16 (\w+)", open(path).read())
     if not m:
         return None
     h = hashlib.sha256()
-    for f in ("stage_fp32_body.cuh", "stage_fp32.cu"):
+    for f in srcs:
         h.update(open(os.path.join(ROOT, "paper_2408_06765_gb300", "csrc", f), "rb").read())
     return int(m.group(1)) if h.hexdigest()[:16] == m.group(2) else None
 
@@ -209,10 +214,20 @@ def measure_unit_rates(rsi, torch):
 ISSUE_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
 
 
-def alu_roofline(kind: str, n_sm: int, clock_hz: float):
+def multi_ops(kind: str, nf: int) -> dict:
+    """Per pair-term counts of the multi-frequency stage kernel (nf frequencies
+    on shared points, scalar arithmetic): the shared geometry once per pair,
+    phase, sincos and epilogue per frequency; the source record (1 + nf float4
+    for RSI, 2 for the piston) is read once per two targets."""
+    if kind == "rsi":  # shared: r - R (10), obliquity and cos/r (3); per f: 10 + the sincos scaling
+        return {"fp32": 13.0 / nf + 11.0, "mufu": 2.0 + 1.0 / nf, "lds": (1.0 + nf) / (2.0 * nf)}
+    return {"fp32": 11.0 / nf + 4.0, "mufu": 2.0 + 1.0 / nf, "lds": 1.0 / nf}
+
+
+def alu_roofline(kind: str, n_sm: int, clock_hz: float, ops: dict | None = None):
     """Peak pairs/s of a stage kernel at `clock_hz`: the tighter of the issue
     limit (one warp instruction per scheduler per clock) and the MUFU limit."""
-    o = OPS[kind]
+    o = ops or OPS[kind]
     issue = (o["fp32"] + o["mufu"] + o["lds"]) / (ISSUE_LANES_PER_SM * n_sm * clock_hz)
     mufu = o["mufu"] / (MUFU_LANES_PER_SM * n_sm * clock_hz)
     return 1.0 / max(issue, mufu), ("mufu" if mufu >= issue else "issue")
@@ -313,8 +328,12 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     opts = {"variant": args.variant} if args.variant else None
+    multi = (not args.no_multi and not args.variant and rsi.same_geometry(cfgs) and len(cfgs) <= 4
+             and cfgs[0].get("precision", "fp32c") == "fp32c")
 
     def step():
+        if multi:  # the frequencies share every point: one pass over the pair geometry
+            return rsi.run_chain_multi(cfgs, fmt="c64", workspace=ws, device=dev)
         return [rsi.run_chain(c, fmt="c64", workspace=ws, device=dev, stage_opts=opts).image for c in cfgs]
 
     for _ in range(max(3, args.warmup)):
@@ -354,13 +373,17 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_hz = (clk["sm_mhz"] if clk and clk.get("sm_mhz") else
               rates["ffma"] / (ISSUE_LANES_PER_SM * n_sm) / 1e6) * 1e6
-    peak, limiter = alu_roofline("rsi", n_sm, clk_hz)
+    nf = len(cfgs) if multi else 1
+    rsi_ops = multi_ops("rsi", nf) if multi else OPS["rsi"]
+    pis_ops = multi_ops("piston", nf) if multi else OPS["piston"]
+    peak, limiter = alu_roofline("rsi", n_sm, clk_hz, rsi_ops)
     pis_avg = pis_ms * 1e-3 / max(1, pis_n)
-    pis_peak, _ = alu_roofline("piston", n_sm, clk_hz)
-    roof = {"bound": "alu", "kernel": "stage_fp32_kernel<RSI>", "achieved": achieved / 1e9,
+    pis_peak, _ = alu_roofline("piston", n_sm, clk_hz, pis_ops)
+    roof = {"bound": "alu", "kernel": f"stage_multi_kernel<RSI, nf={nf}>" if multi else "stage_fp32_kernel<RSI>",
+            "achieved": achieved / 1e9,
             "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
             "limiter": limiter,
-            "ops_per_pair": OPS["rsi"],
+            "ops_per_pair": rsi_ops,
             "peak_source": "unit counts (4 issue slots of 32 lanes and 16 MUFU lanes per SM per clock) x "
                            f"{n_sm} SMs x the median SM clock of the timed region "
                            f"({clk_hz / 1e6:.0f} MHz)",
@@ -377,7 +400,7 @@ def run_ours(args):
                         "no FP64 roofline is modelled",
                 "avg_launch_ms": avg_s * 1e3, "launches": rsi_n}
     if cfgs[0]["precision"] != "fp64" and args.config == "c2":
-        roof["traffic"] = recorded_traffic()
+        roof["traffic"] = recorded_traffic("stage_multi_kernel" if multi else "stage_fp32_kernel")
 
     e2e = None
     if not args.no_e2e:

@@ -188,6 +188,24 @@ int rsi_propagate_stage(const rsi_stage *st,
                         const void *tgt_points, int64_t n_tgt, double *tgt_field,
                         void *workspace, size_t workspace_bytes, void *stream);
 
+/* Steps a3/a5 (+a6) for nf frequencies at once on the same point sets: a
+ * broadband field is the superposition of single-frequency fields (Sec. 4),
+ * and frequencies that share the transducer and the interfaces share every
+ * point.  The pair geometry (r - R, 1/r, the obliquity) is formed once per
+ * pair and used by the nf sums; each frequency adds its phase, its sincos
+ * and its source amplitude.  ks: the nf wavenumbers (st->k is not used);
+ * src_sigma: complex [nf][n_src] (RSI; NULL for PISTON, whose amplitude does
+ * not depend on the frequency); tgt_field: complex [nf][n_tgt], overwritten.
+ * FP32C only (st->variant is not used), 2 <= nf <= 4.  Each frequency's
+ * result equals a single-frequency rsi_propagate_stage to rounding; other
+ * conventions as rsi_propagate_stage.  The workspace size depends on nf.     */
+size_t rsi_stage_multi_workspace_bytes(const rsi_stage *st, int32_t nf, const double *ks, int64_t n_src,
+                                       int64_t n_tgt);
+int rsi_propagate_stage_multi(const rsi_stage *st, int32_t nf, const double *ks,
+                              const void *src_points, int64_t n_src, const double *src_sigma,
+                              const void *tgt_points, int64_t n_tgt, double *tgt_field,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot give the library device memory for scratch (a latency-bound
  * acquisition loop that must not call cudaMalloc, a plug-in whose host owns

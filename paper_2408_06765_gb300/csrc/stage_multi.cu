@@ -1,0 +1,541 @@
+// stage_multi.cu -- rsi_propagate_stage_multi: the FP32C stage sum (steps a3,
+// a5, a6) for nf frequencies at once on the same point sets.  A broadband
+// field is the superposition of single-frequency fields (Sec. 4), and the
+// frequencies of one transducer and one interface share every point, so per
+// pair the geometry -- r - R (Newton update), 1/r and the obliquity -- is
+// formed once; each frequency adds only its phase k_f (r - R) + tau_f, its
+// sincos and its source amplitude.  MUFU work per pair-term falls from 3 to
+// 2 + 1/nf.  Each frequency's arithmetic is that of the single-frequency
+// kernel (stage_fp32_body.cuh), so the results agree with nf separate stages
+// to rounding.
+#include <math.h>
+
+#include "stage_fp32_body.cuh"
+
+namespace {
+
+using namespace rsi_fp32;
+
+constexpr int kMaxNF = 4;
+constexpr int kMTpt = 2;
+
+struct MultiArgs {
+    int kind, normals, nf, S, n_tiles, tiles_per_split, splits;
+    int64_t n_tgt;
+    size_t tile_bytes;
+    const uint8_t* tiles;
+    TgtView tgt;
+    float kh[kMaxNF], kl[kMaxNF];
+    TwoPiSplit tp;
+    double2* out;  // [splits][nf][n_tgt] partial sums, or the fields [nf][n_tgt]
+    int* status;
+};
+
+// Tile records (float4 units): [p.x, p.y, p.z, |p|^2], then
+//   PISTON  [A, 0, 0, 0]                   (A = -v0 w / 2 pi, frequency independent)
+//   RSI     nf x [B.re, B.im, C.re, C.im]  (B = -w sigma_f / 2 pi, C = i k_f B)
+//           [+ (nx, ny, nz, n.p)]
+template <int KIND, int NORM, int NF>
+constexpr int mrec_f4() {
+    return KIND == RSI_STAGE_PISTON ? 2 : 1 + NF + (NORM == RSI_NORMALS_POINTS ? 1 : 0);
+}
+__host__ __device__ inline int mrec_f4_rt(int kind, int normals, int nf) {
+    return kind == RSI_STAGE_PISTON ? 2 : 1 + nf + (normals == RSI_NORMALS_POINTS ? 1 : 0);
+}
+
+struct MRef {
+    float Dx, Dy, Dz, mx, my, mz, R, R2;
+    float tau[kMaxNF];
+};
+
+// double-float reference of one target against one tile centre: D, R and the
+// phase k_f R mod 2 pi of every frequency
+template <int NF>
+__device__ __forceinline__ MRef multi_reference(float qxh, float qxl, float qyh, float qyl, float qzh, float qzl,
+                                                const float* c, const MultiArgs& a) {
+    float dxh, dxl, dyh, dyl, dzh, dzl;
+    df_diff(qxh, qxl, c[0], c[1], dxh, dxl);
+    df_diff(qyh, qyl, c[2], c[3], dyh, dyl);
+    df_diff(qzh, qzl, c[4], c[5], dzh, dzl);
+    float ax, axl, ay, ayl, az, azl, sh, sl;
+    df_sqr(dxh, dxl, ax, axl);
+    df_sqr(dyh, dyl, ay, ayl);
+    df_sqr(dzh, dzl, az, azl);
+    df_add_pos(ax, axl, ay, ayl, sh, sl);
+    df_add_pos(sh, sl, az, azl, sh, sl);
+    float Rh = 0.0f, Rl = 0.0f;
+    if (sh > 0.0f) {
+        float y = rsqrtf(sh);
+        float r0 = __fmul_rn(sh, y);
+        float p, pe;
+        two_prod(r0, r0, p, pe);
+        float e = __fadd_rn(__fsub_rn(__fsub_rn(sh, p), pe), sl);
+        fast_two_sum(r0, __fmul_rn(e, __fmul_rn(0.5f, y)), Rh, Rl);
+    }
+    MRef t;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        float ph, pl;
+        two_prod(a.kh[f], Rh, ph, pl);
+        pl = __fmaf_rn(a.kh[f], Rl, __fmaf_rn(a.kl[f], Rh, pl));
+        float n = rintf(__fmul_rn(ph, a.tp.inv));
+        float x = __fmaf_rn(-n, a.tp.p1, ph);
+        x = __fmaf_rn(-n, a.tp.p2, x);
+        x = __fmaf_rn(-n, a.tp.p3, x);
+        t.tau[f] = __fadd_rn(x, pl);
+    }
+    t.Dx = dxh;
+    t.Dy = dyh;
+    t.Dz = dzh;
+    t.mx = -2.0f * dxh;
+    t.my = -2.0f * dyh;
+    t.mz = -2.0f * dzh;
+    t.R = Rh;
+    t.R2 = Rh * Rh;
+    return t;
+}
+
+// the terms of one pair for every frequency once r - R, 1/r and the obliquity are known
+template <int KIND, int NORM, int NF>
+__device__ __forceinline__ void mterms(const MRef& t, const float4* r, float dr, float ir, float nd, const float* kv,
+                                       float (&ar)[NF], float (&ai)[NF]) {
+    if (KIND == RSI_STAGE_PISTON) {
+        const float amp = r[1].x * ir;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            float s, c;
+            __sincosf(fmaf(kv[f], dr, t.tau[f]), &s, &c);
+            ar[f] = fmaf(amp, c, ar[f]);
+            ai[f] = fmaf(amp, s, ai[f]);
+        }
+    } else {
+        const float h = nd * (ir * ir);  // cos(theta) / r
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const float4 b = r[1 + f];
+            float s, c;
+            __sincosf(fmaf(kv[f], dr, t.tau[f]), &s, &c);
+            const float vr = fmaf(-ir, b.x, b.z), vi = fmaf(-ir, b.y, b.w);  // B (ik - 1/r)
+            ar[f] = fmaf(h, fmaf(vr, c, -vi * s), ar[f]);
+            ai[f] = fmaf(h, fmaf(vr, s, vi * c), ai[f]);
+        }
+    }
+}
+
+// far path: R > 2 (tile radius)
+template <int KIND, int NORM, int NF>
+__device__ __forceinline__ void mpair_far(const MRef& t, const float4* r, const float* kv, float (&ar)[NF],
+                                          float (&ai)[NF]) {
+    const float4 a = r[0];
+    const float tt = fmaf(t.mx, a.x, fmaf(t.my, a.y, fmaf(t.mz, a.z, a.w)));  // r^2 - R^2
+    const float r2 = t.R2 + tt;
+    const float ir = rsqrt_approx(r2);
+    const float r0 = r2 * ir;
+    const float am = r0 - t.R;
+    const float e = fmaf(-am, t.R + r0, tt);
+    const float dr = fmaf(e, 0.5f * ir, am);
+    float nd = 0.0f;
+    if (KIND == RSI_STAGE_RSI) {
+        if (NORM == RSI_NORMALS_Z) {
+            nd = t.Dz - a.z;
+        } else {
+            const float4 n = r[1 + NF];
+            nd = fmaf(n.x, t.Dx, fmaf(n.y, t.Dy, fmaf(n.z, t.Dz, -n.w)));
+        }
+    }
+    mterms<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
+}
+
+// near path: r^2 from the FP32 offsets; pairs closer than 1e-12 m contribute nothing
+template <int KIND, int NORM, int NF>
+__device__ __forceinline__ void mpair_near(const MRef& t, const float4* r, const float* kv, float (&ar)[NF],
+                                           float (&ai)[NF]) {
+    const float4 a = r[0];
+    const float dx = t.Dx - a.x, dy = t.Dy - a.y, dz = t.Dz - a.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float tt = fmaf(t.mx, a.x, fmaf(t.my, a.y, fmaf(t.mz, a.z, a.w)));
+    float ir = rsqrt_approx(r2);
+    ir = r2 > 1e-24f ? ir : 0.0f;
+    const float r0 = r2 * ir;
+    const float am = t.R - r0;
+    const float e = fmaf(am, t.R + r0, tt);
+    const float dr = fmaf(e, 0.5f * ir, -am);
+    float nd = 0.0f;
+    if (KIND == RSI_STAGE_RSI) {
+        if (NORM == RSI_NORMALS_Z) {
+            nd = dz;
+        } else {
+            const float4 n = r[1 + NF];
+            nd = fmaf(n.x, dx, fmaf(n.y, dy, n.z * dz));
+        }
+    }
+    mterms<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
+}
+
+template <int KIND, int NORM, int NF>
+__global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RSI_PIPE_STAGES * a.tile_bytes);
+    init_barriers(bars);
+    constexpr int RF4 = mrec_f4<KIND, NORM, NF>();
+    const int tid = threadIdx.x;
+    const int split = blockIdx.y;
+    const int t_begin = split * a.tiles_per_split;
+    const int ntile = max(0, min(a.n_tiles, t_begin + a.tiles_per_split) - t_begin);
+    const uint32_t tb = uint32_t(a.tile_bytes);
+    int64_t jt[kMTpt];
+#pragma unroll
+    for (int q = 0; q < kMTpt; ++q) {
+        const int64_t j = int64_t(blockIdx.x) * kMTpt * kThreads + int64_t(q) * kThreads + tid;
+        jt[q] = j < a.n_tgt ? j : a.n_tgt - 1;
+    }
+    if (tid == 0)
+        for (int s = 0; s < RSI_PIPE_STAGES && s < ntile; ++s) {
+            const uint32_t bar = smem_u32(&bars[s]);
+            mbar_expect_tx(bar, tb);
+            bulk_g2s(smem_u32(smem + s * tb), a.tiles + size_t(t_begin + s) * tb, tb, bar);
+        }
+    float kv[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) kv[f] = a.kh[f];
+    float hr[kMTpt][NF], lr[kMTpt][NF], hi[kMTpt][NF], li[kMTpt][NF];
+#pragma unroll
+    for (int q = 0; q < kMTpt; ++q)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) hr[q][f] = lr[q][f] = hi[q][f] = li[q][f] = 0.0f;
+    int failed_at = -1;
+    for (int it = 0; it < ntile; ++it) {
+        const int buf = it % RSI_PIPE_STAGES;
+        const bool ok = mbar_wait_bounded(smem_u32(&bars[buf]), uint32_t(it / RSI_PIPE_STAGES) & 1u);
+        if (__syncthreads_or(!ok)) {
+            failed_at = it;
+            break;
+        }
+        const uint8_t* tile = smem + buf * tb;
+        const float* hdr = reinterpret_cast<const float*>(tile);
+        const float4* rec = reinterpret_cast<const float4*>(tile + RSI_TILE_HDR_BYTES);
+        MRef ref[kMTpt];
+        float ar[kMTpt][NF], ai[kMTpt][NF];
+        const float far_min = 2.0f * hdr[6];
+        bool far_lane = true;
+#pragma unroll
+        for (int q = 0; q < kMTpt; ++q) {
+            const int64_t j = jt[q];
+            ref[q] = multi_reference<NF>(__ldg(a.tgt.xh + j), __ldg(a.tgt.xl + j), __ldg(a.tgt.yh + j),
+                                         __ldg(a.tgt.yl + j), __ldg(a.tgt.zh + j), __ldg(a.tgt.zl + j), hdr, a);
+            far_lane = far_lane && ref[q].R > far_min && ref[q].R > 0.0f;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) ar[q][f] = ai[q][f] = 0.0f;
+        }
+        if (__all_sync(0xffffffffu, far_lane)) {
+#pragma unroll 1
+            for (int i = 0; i < a.S; ++i) {
+                float4 r[RF4];
+#pragma unroll
+                for (int m = 0; m < RF4; ++m) r[m] = rec[i * RF4 + m];
+#pragma unroll
+                for (int q = 0; q < kMTpt; ++q) mpair_far<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
+            }
+        } else {
+#pragma unroll 1
+            for (int i = 0; i < a.S; ++i) {
+                float4 r[RF4];
+#pragma unroll
+                for (int m = 0; m < RF4; ++m) r[m] = rec[i * RF4 + m];
+#pragma unroll
+                for (int q = 0; q < kMTpt; ++q) mpair_near<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kMTpt; ++q)
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                float s, e;
+                two_sum(hr[q][f], ar[q][f], s, e);
+                hr[q][f] = s;
+                lr[q][f] = __fadd_rn(lr[q][f], e);
+                two_sum(hi[q][f], ai[q][f], s, e);
+                hi[q][f] = s;
+                li[q][f] = __fadd_rn(li[q][f], e);
+            }
+        __syncthreads();
+        if (tid == 0 && it + RSI_PIPE_STAGES < ntile) {
+            const uint32_t bar = smem_u32(&bars[buf]);
+            mbar_expect_tx(bar, tb);
+            bulk_g2s(smem_u32(smem + buf * tb), a.tiles + size_t(t_begin + it + RSI_PIPE_STAGES) * tb, tb, bar);
+        }
+    }
+    if (failed_at >= 0) {
+        if (tid == 0) {
+            atomicExch(a.status, RSI_DEV_TIMEOUT);
+            for (int it = failed_at; it < ntile && it < failed_at + RSI_PIPE_STAGES; ++it)
+                mbar_wait_bounded(smem_u32(&bars[it % RSI_PIPE_STAGES]), uint32_t(it / RSI_PIPE_STAGES) & 1u);
+        }
+        return;
+    }
+    double2* out = a.out + (a.splits > 1 ? size_t(split) * size_t(NF) * size_t(a.n_tgt) : 0);
+#pragma unroll
+    for (int q = 0; q < kMTpt; ++q) {
+        const int64_t j = int64_t(blockIdx.x) * kMTpt * kThreads + int64_t(q) * kThreads + tid;
+        if (j < a.n_tgt)
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const double re = double(hr[q][f]) + double(lr[q][f]);
+                const double im = double(hi[q][f]) + double(li[q][f]);
+                if (!isfinite(re) || !isfinite(im)) atomicExch(a.status, RSI_DEV_NONFINITE);
+                out[size_t(f) * size_t(a.n_tgt) + size_t(j)] = make_double2(re, im);
+            }
+    }
+}
+
+// one CTA per tile: the geometry of stage_fp32_body.cuh's prep_tile, and one
+// amplitude block per frequency
+__global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, PointsView src,
+                             const double2* __restrict__ sigma, double amp_scale, MultiArgs a, uint8_t* tiles,
+                             size_t tile_bytes) {
+    __shared__ double red[32];
+    const int S = blockDim.x;
+    const int64_t tile = blockIdx.x;
+    const int64_t i = tile * S + threadIdx.x;
+    const bool valid = i < n_src;
+    double c[3];
+    const double* coord[3] = {src.x, src.y, src.z};
+    for (int d = 0; d < 3; ++d) {
+        const double v = valid ? coord[d][i] : 0.0;
+        const double lo = block_reduce(valid ? v : INFINITY, false, red);
+        const double hi = block_reduce(valid ? v : -INFINITY, true, red);
+        c[d] = 0.5 * (lo + hi);
+    }
+    float ch[3], cl[3];
+    for (int d = 0; d < 3; ++d) {
+        ch[d] = __double2float_rn(c[d]);
+        cl[d] = __double2float_rn(c[d] - double(ch[d]));
+    }
+    const int rf = 4 * mrec_f4_rt(kind, normals, nf);
+    float* rec = reinterpret_cast<float*>(tiles + size_t(tile) * tile_bytes + RSI_TILE_HDR_BYTES) +
+                 size_t(threadIdx.x) * rf;
+    float px = 4.0f, py = 4.0f, pz = 4.0f;
+    if (valid) {
+        float h, l;
+        df_diff(src.xh[i], src.xl[i], ch[0], cl[0], h, l);
+        px = h;
+        df_diff(src.yh[i], src.yl[i], ch[1], cl[1], h, l);
+        py = h;
+        df_diff(src.zh[i], src.zl[i], ch[2], cl[2], h, l);
+        pz = h;
+    }
+    rec[0] = px;
+    rec[1] = py;
+    rec[2] = pz;
+    rec[3] = fmaf(px, px, fmaf(py, py, pz * pz));
+    if (kind == RSI_STAGE_PISTON) {
+        rec[4] = valid ? float(amp_scale * src.w[i]) : 0.0f;
+        rec[5] = rec[6] = rec[7] = 0.0f;
+    } else {
+        for (int f = 0; f < nf; ++f) {
+            float* b = rec + 4 + 4 * f;
+            if (valid) {
+                const double k = double(a.kh[f]) + double(a.kl[f]);
+                const double2 sg = sigma[size_t(f) * size_t(n_src) + size_t(i)];
+                const double br = amp_scale * src.w[i] * sg.x, bi = amp_scale * src.w[i] * sg.y;
+                b[0] = float(br);
+                b[1] = float(bi);
+                b[2] = float(-k * bi);
+                b[3] = float(k * br);
+            } else {
+                b[0] = b[1] = b[2] = b[3] = 0.0f;
+            }
+        }
+        if (normals == RSI_NORMALS_POINTS) {
+            float* n = rec + 4 + 4 * nf;
+            const float nx = valid ? float(src.nx[i]) : 0.0f, ny = valid ? float(src.ny[i]) : 0.0f,
+                        nz = valid ? float(src.nz[i]) : 1.0f;
+            n[0] = nx;
+            n[1] = ny;
+            n[2] = nz;
+            n[3] = fmaf(nx, px, fmaf(ny, py, nz * pz));
+        }
+    }
+    const double rad = block_reduce(valid ? double(px * px + py * py + pz * pz) : 0.0, true, red);
+    if (threadIdx.x == 0) {
+        float* hdr = reinterpret_cast<float*>(tiles + size_t(tile) * tile_bytes);
+        hdr[0] = ch[0];
+        hdr[1] = cl[0];
+        hdr[2] = ch[1];
+        hdr[3] = cl[1];
+        hdr[4] = ch[2];
+        hdr[5] = cl[2];
+        hdr[6] = sqrtf(float(rad));
+        hdr[7] = 0.0f;
+    }
+}
+
+size_t msmem(size_t tile_bytes) { return RSI_PIPE_STAGES * tile_bytes + RSI_PIPE_STAGES * sizeof(uint64_t); }
+
+template <int KIND, int NORM, int NF>
+int mlaunch(const MultiArgs& a, cudaStream_t s, bool occ, int* occ_out) {
+    auto kern = stage_multi_kernel<KIND, NORM, NF>;
+    static bool attr = false;
+    if (!attr) {
+        RSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
+                     "cudaFuncSetAttribute(stage_multi)");
+        attr = true;
+    }
+    if (occ) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, msmem(a.tile_bytes)) != cudaSuccess)
+            b = 1;
+        *occ_out = b > 0 ? b : 1;
+        return RSI_OK;
+    }
+    const int64_t per_block = int64_t(kThreads) * kMTpt;
+    dim3 grid(unsigned((a.n_tgt + per_block - 1) / per_block), unsigned(a.splits));
+    kern<<<grid, kThreads, msmem(a.tile_bytes), s>>>(a);
+    RSI_CHECK_LAUNCH("stage_multi_kernel");
+    return RSI_OK;
+}
+
+template <int KIND, int NORM>
+int mdispatch_nf(const MultiArgs& a, cudaStream_t s, bool occ, int* o) {
+    switch (a.nf) {
+        case 2: return mlaunch<KIND, NORM, 2>(a, s, occ, o);
+        case 3: return mlaunch<KIND, NORM, 3>(a, s, occ, o);
+        default: return mlaunch<KIND, NORM, 4>(a, s, occ, o);
+    }
+}
+
+int mdispatch(const MultiArgs& a, cudaStream_t s, bool occ, int* o) {
+    if (a.kind == RSI_STAGE_PISTON) return mdispatch_nf<RSI_STAGE_PISTON, RSI_NORMALS_Z>(a, s, occ, o);
+    if (a.normals == RSI_NORMALS_POINTS) return mdispatch_nf<RSI_STAGE_RSI, RSI_NORMALS_POINTS>(a, s, occ, o);
+    return mdispatch_nf<RSI_STAGE_RSI, RSI_NORMALS_Z>(a, s, occ, o);
+}
+
+struct MPlan {
+    int S, n_tiles, tiles_per_split, splits;
+    size_t tile_bytes, tiles_bytes, partial_bytes;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int mplan(const rsi_stage& st, int nf, const double* ks, int64_t n_src, int64_t n_tgt, MPlan& p, MultiArgs& a) {
+    if (st.kind != RSI_STAGE_PISTON && st.kind != RSI_STAGE_RSI)
+        return rsi_fail(RSI_E_INVAL, "unknown stage kind %d", st.kind);
+    if (st.precision != RSI_PREC_FP32C) return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi is FP32C only");
+    if (nf < 2 || nf > kMaxNF) return rsi_fail(RSI_E_INVAL, "nf must be in 2..%d (got %d)", kMaxNF, nf);
+    if (st.kind == RSI_STAGE_RSI && (st.normals < RSI_NORMALS_Z || st.normals > RSI_NORMALS_POINTS_NEG))
+        return rsi_fail(RSI_E_INVAL, "unknown normals mode %d", st.normals);
+    if (n_src < 1 || n_tgt < 1) return rsi_fail(RSI_E_INVAL, "empty source or target set");
+    if (n_src > (int64_t(1) << 31) || n_tgt > (int64_t(1) << 31))
+        return rsi_fail(RSI_E_INVAL, "more than 2^31 sources or targets");
+    for (int f = 0; f < nf; ++f)
+        if (!(ks[f] > 0) || !isfinite(ks[f])) return rsi_fail(RSI_E_INVAL, "wavenumbers must be finite and > 0");
+    const int normals = st.kind == RSI_STAGE_RSI ? base_normals(st.normals) : RSI_NORMALS_Z;
+    if (st.tile) {
+        p.S = st.tile;
+        if (p.S != 32 && p.S != 64 && p.S != 128 && p.S != 256)
+            return rsi_fail(RSI_E_INVAL, "tile must be 32, 64, 128 or 256");
+    } else {
+        const int64_t cap = n_src / 64;
+        p.S = 256;
+        while (p.S > 32 && p.S > cap) p.S >>= 1;
+    }
+    p.n_tiles = int((n_src + p.S - 1) / p.S);
+    p.tile_bytes = RSI_TILE_HDR_BYTES + size_t(p.S) * 16 * size_t(mrec_f4_rt(st.kind, normals, nf));
+    p.tiles_bytes = align256(size_t(p.n_tiles) * p.tile_bytes);
+    a.kind = st.kind;
+    a.normals = normals;
+    a.nf = nf;
+    a.S = p.S;
+    a.n_tiles = p.n_tiles;
+    a.n_tgt = n_tgt;
+    a.tile_bytes = p.tile_bytes;
+    for (int f = 0; f < kMaxNF; ++f) {
+        const double k = f < nf ? ks[f] : ks[0];
+        a.kh[f] = float(k);
+        a.kl[f] = float(k - double(a.kh[f]));
+    }
+    a.tp = two_pi_split();
+    const int64_t blocks = (n_tgt + int64_t(kThreads) * kMTpt - 1) / (int64_t(kThreads) * kMTpt);
+    int splits = st.splits;
+    if (splits < 0) return rsi_fail(RSI_E_INVAL, "splits must be >= 0");
+    if (splits == 0) {
+        int occ = 1;
+        mdispatch(a, nullptr, true, &occ);
+        const int64_t slots = int64_t(rsi_num_sms()) * occ;
+        int64_t best = INT64_MAX;
+        splits = 1;
+        for (int s = 1; s <= 128 && s <= p.n_tiles; ++s) {
+            const int64_t tps = (p.n_tiles + s - 1) / s, s_act = (p.n_tiles + tps - 1) / tps;
+            const int64_t cost = ((blocks * s_act + slots - 1) / slots) * tps;
+            if (cost < best) {
+                best = cost;
+                splits = int(s_act);
+            }
+        }
+    }
+    if (splits > p.n_tiles) splits = p.n_tiles;
+    if (splits > 65535) return rsi_fail(RSI_E_INVAL, "too many splits");
+    p.tiles_per_split = (p.n_tiles + splits - 1) / splits;
+    p.splits = (p.n_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
+    p.partial_bytes =
+        p.splits > 1 ? align256(size_t(p.splits) * size_t(nf) * size_t(n_tgt) * sizeof(double2)) : 0;
+    a.tiles_per_split = p.tiles_per_split;
+    a.splits = p.splits;
+    return RSI_OK;
+}
+
+}  // namespace
+
+extern "C" size_t rsi_stage_multi_workspace_bytes(const rsi_stage* st, int32_t nf, const double* ks, int64_t n_src,
+                                                  int64_t n_tgt) {
+    if (!st || !ks) return 0;
+    MPlan p;
+    MultiArgs a = {};
+    if (mplan(*st, nf, ks, n_src, n_tgt, p, a) != RSI_OK) return 0;
+    return p.tiles_bytes + p.partial_bytes;
+}
+
+extern "C" int rsi_propagate_stage_multi(const rsi_stage* st, int32_t nf, const double* ks, const void* src_points,
+                                         int64_t n_src, const double* src_sigma, const void* tgt_points,
+                                         int64_t n_tgt, double* tgt_field, void* workspace, size_t workspace_bytes,
+                                         void* stream) {
+    if (!st || !ks || !src_points || !tgt_points || !tgt_field || !workspace)
+        return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi: null argument");
+    if (st->kind == RSI_STAGE_RSI && !src_sigma)
+        return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi: RSI stage needs source densities");
+    if (st->kind == RSI_STAGE_PISTON && !isfinite(st->v0))
+        return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi: v0 must be finite");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 || reinterpret_cast<uintptr_t>(src_points) % 256 ||
+        reinterpret_cast<uintptr_t>(tgt_points) % 256 || reinterpret_cast<uintptr_t>(tgt_field) % 16 ||
+        (src_sigma && reinterpret_cast<uintptr_t>(src_sigma) % 16))
+        return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi: misaligned pointer");
+    MPlan p;
+    MultiArgs a = {};
+    int rc = mplan(*st, nf, ks, n_src, n_tgt, p, a);
+    if (rc != RSI_OK) return rc;
+    if (workspace_bytes < p.tiles_bytes + p.partial_bytes)
+        return rsi_fail(RSI_E_NOMEM, "rsi_propagate_stage_multi: workspace %zu < %zu bytes", workspace_bytes,
+                        p.tiles_bytes + p.partial_bytes);
+    int* status = rsi_status_ptr();
+    if (!status) return RSI_E_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PointsView src = rsi_points_view(const_cast<void*>(src_points), n_src);
+    PointsView tgt = rsi_points_view(const_cast<void*>(tgt_points), n_tgt);
+    uint8_t* tiles = static_cast<uint8_t*>(workspace);
+    mprep_kernel<<<p.n_tiles, p.S, 0, s>>>(a.kind, a.normals, nf, n_src, src,
+                                           reinterpret_cast<const double2*>(src_sigma), stage_amp_scale(*st), a,
+                                           tiles, p.tile_bytes);
+    RSI_CHECK_LAUNCH("mprep_kernel");
+    a.tiles = tiles;
+    a.tgt = {tgt.xh, tgt.xl, tgt.yh, tgt.yl, tgt.zh, tgt.zl, tgt.x, tgt.y, tgt.z};
+    double2* field = reinterpret_cast<double2*>(tgt_field);
+    a.out = p.splits > 1 ? reinterpret_cast<double2*>(tiles + p.tiles_bytes) : field;
+    a.status = status;
+    TimingScope tsc = timing_begin(s);
+    int o = 0;
+    rc = mdispatch(a, s, false, &o);
+    if (rc != RSI_OK) return rc;
+    timing_end(tsc, st->kind, double(nf) * double(n_src) * double(n_tgt), s);
+    if (p.splits > 1) return launch_reduce_partials(a.out, p.splits, int64_t(nf) * n_tgt, field, status, s);
+    return RSI_OK;
+}

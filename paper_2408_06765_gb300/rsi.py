@@ -43,7 +43,8 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points",
            "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_interface_transmit",
            "rsi_interface_reflect", "rsi_field_image", "rsi_field_image_sum", "rsi_launch_count",
-           "rsi_raytrace_workspace_bytes", "rsi_raytrace_field", "rsi_timing_enable", "rsi_timing_read",
+           "rsi_raytrace_workspace_bytes", "rsi_raytrace_field", "rsi_stage_multi_workspace_bytes",
+           "rsi_propagate_stage_multi", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
            "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier",
@@ -128,6 +129,10 @@ def load(path: str | None = None):
         L.rsi_field_image.argtypes = [ctypes.POINTER(Grid), vp, ctypes.c_double, ctypes.c_double,
                                       i32, vp, vp]
         L.rsi_interface_reflect.argtypes = [ctypes.POINTER(Interface), vp, i64, vp, vp, vp]
+        L.rsi_stage_multi_workspace_bytes.restype = sz
+        L.rsi_stage_multi_workspace_bytes.argtypes = [ctypes.POINTER(Stage), i32, vp, i64, i64]
+        L.rsi_propagate_stage_multi.argtypes = [ctypes.POINTER(Stage), i32, vp, vp, i64, vp, vp, i64, vp, vp, sz,
+                                                vp]
         L.rsi_raytrace_workspace_bytes.restype = sz
         L.rsi_raytrace_workspace_bytes.argtypes = [ctypes.POINTER(Raytrace), i64, i64]
         L.rsi_raytrace_field.argtypes = [ctypes.POINTER(Raytrace), vp, i64, vp, i64, vp, vp, sz, vp]
@@ -282,6 +287,24 @@ def propagate_stage(st: Stage, src: Points, sigma, tgt: Points, out=None,
     _check(load().rsi_propagate_stage(ctypes.byref(st), src.ptr(), src.n, _ptr(sigma), tgt.ptr(),
                                       tgt.n, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
            "rsi_propagate_stage")
+    return out
+
+
+def propagate_stage_multi(st: Stage, ks, src: Points, sigma, tgt: Points, out=None,
+                          workspace: Workspace | None = None, stream=None) -> torch.Tensor:
+    """nf frequencies of one stage on shared points (rsi_propagate_stage_multi):
+    sigma complex [nf, n_src] (RSI) or None, returns complex [nf, n_tgt]."""
+    L = load()
+    nf = len(ks)
+    kd = (ctypes.c_double * nf)(*[float(k) for k in ks])
+    if out is None:
+        out = torch.empty((nf, tgt.n), dtype=torch.complex128, device=tgt.buf.device)
+    nb = int(L.rsi_stage_multi_workspace_bytes(ctypes.byref(st), nf, kd, src.n, tgt.n))
+    if nb == 0:
+        raise RSIError("rsi_stage_multi_workspace_bytes", -1, L.rsi_last_error().decode(errors="replace"))
+    ws = (workspace or Workspace(tgt.buf.device)).get(nb)
+    _check(L.rsi_propagate_stage_multi(ctypes.byref(st), nf, kd, src.ptr(), src.n, _ptr(sigma), tgt.ptr(), tgt.n,
+                                       _ptr(out), _ptr(ws), nb, _stream(stream)), "rsi_propagate_stage_multi")
     return out
 
 
@@ -520,6 +543,55 @@ def two_medium_pairs(cfg: dict) -> int:
     n_w = int(cfg["grid_water"]["nx"]) * int(cfg["grid_water"]["nz"])
     n_s = int(cfg["grid_solid"]["nx"]) * int(cfg["grid_solid"]["nz"])
     return n_p * n_i + n_p * n_w + n_i * n_w + n_i * n_s
+
+
+def same_geometry(cfgs) -> bool:
+    """True when workloads differ only in frequency (same seed, points, media
+    and image grid), so their stages can share every pair's geometry."""
+    strip = lambda c: {k: v for k, v in c.items() if k not in ("freq", "name")}
+    return len(cfgs) > 1 and all(strip(c) == strip(cfgs[0]) for c in cfgs[1:])
+
+
+def run_chain_multi(cfgs: list, fmt: str = "c128", workspace: Workspace | None = None,
+                    stage_opts: dict | None = None, stream=None, device="cuda") -> list:
+    """The chains of 2-4 workloads that differ only in frequency, every stage
+    evaluated for all frequencies at once (rsi_propagate_stage_multi).
+    Returns one image per workload, as run_chain would."""
+    if not same_geometry(cfgs) or not 2 <= len(cfgs) <= 4:
+        raise ValueError("run_chain_multi needs 2-4 workloads that differ only in frequency")
+    cfg = cfgs[0]
+    if cfg.get("precision", "fp32c") != "fp32c":
+        raise ValueError("run_chain_multi is FP32C only")
+    opts = {k: v for k, v in (stage_opts or {}).items() if k != "variant"}
+    ws = workspace or Workspace(device)
+    seed = int(cfg.get("seed", 0))
+    v0 = float(cfg.get("v0", 1.0))
+    media = cfg["media"]
+    C = snell_invariant(cfg)
+    mode = cfg.get("tmode", "global")
+    freqs = [float(c["freq"]) for c in cfgs]
+    nf = len(freqs)
+    pc = cfg["piston"]
+    piston = make_qmc_points(dict({"kind": "disk"}, **pc), seed, int(pc.get("set_id", 0)), int(pc["n"]),
+                             device=device, stream=stream)
+    ifaces = [make_qmc_points(it, seed, int(it["set_id"]), int(it["n"]), device=device, stream=stream)
+              for it in cfg["interfaces"]]
+    targets = grid_points(cfg["grid"], device=device, stream=stream)
+    first_tgt = ifaces[0] if ifaces else targets
+    ks = [wavenumber(f, media[0]["c"]) for f in freqs]
+    st = stage_struct(STAGE_PISTON, "fp32c", ks[0], v0, **opts)
+    phi = propagate_stage_multi(st, ks, piston, None, first_tgt, workspace=ws, stream=stream)
+    for s, pts in enumerate(ifaces):
+        sigma = torch.empty_like(phi)
+        for f in range(nf):
+            interface_transmit(pts, phi[f], media[s], media[s + 1], C, mode, out=sigma[f], stream=stream)
+        nxt = ifaces[s + 1] if s + 1 < len(ifaces) else targets
+        normals = NORMALS_POINTS if cfg["interfaces"][s]["kind"] != "rect" else NORMALS_Z
+        ks = [wavenumber(f, media[s + 1]["c"]) for f in freqs]
+        st = stage_struct(STAGE_RSI, "fp32c", ks[0], 1.0, normals, **opts)
+        phi = propagate_stage_multi(st, ks, pts, sigma, nxt, workspace=ws, stream=stream)
+    k_last = [wavenumber(f, media[len(ifaces)]["c"]) for f in freqs]
+    return [field_image(cfg["grid"], phi[f], k_last[f], v0, fmt, stream=stream) for f in range(nf)]
 
 
 # ---------------------------------------------------------------------------
