@@ -61,6 +61,8 @@ def parse():
                     help="target duration of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nf", type=int, default=1,
+                    help="--case stage: frequencies per stage (2-4: the multi-frequency stage at 10, 5, 2.25, 1 MHz)")
     ap.add_argument("--no-multi", action="store_true",
                     help="run frequencies that share their points one by one instead of together")
     ap.add_argument("--small", action="store_true",
@@ -508,6 +510,11 @@ def run_stage_case(args):
     shapes = [(args.tile, args.tpt, args.variant)]
     if args.sweep:
         shapes = [(t, q, v) for t in (64, 128, 256, 512) for q in (2, 4) for v in (1, 2, 3)]
+    nf = args.nf
+    if nf > 1:
+        shapes = [(args.tile, 2, 0)]
+        ks = [rsi.wavenumber(f, 5900.0) for f in (10e6, 5e6, 2.25e6, 1e6)[:nf]]
+        sigma = torch.ones((nf, it["n"]), dtype=torch.complex128, device="cuda")
     for tile, tpt, variant in shapes:
         st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", rsi.wavenumber(cfg["freq"], 5900.0),
                               normals=rsi.NORMALS_Z, tile=tile, tpt=tpt, variant=variant)
@@ -516,14 +523,17 @@ def run_stage_case(args):
         for _ in range(args.warmup + args.steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            out = rsi.propagate_stage(st, pts, sigma, grid, workspace=ws)
+            if nf > 1:
+                out = rsi.propagate_stage_multi(st, ks, pts, sigma, grid, workspace=ws)
+            else:
+                out = rsi.propagate_stage(st, pts, sigma, grid, workspace=ws)
             e1.record()
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         rsi.sync_status()
         ms = min(times[args.warmup:])
-        pairs = it["n"] * grid.n
-        print(json.dumps({"case": "stage", "ms": ms, "gpair_per_s": pairs / ms / 1e6,
+        pairs = it["n"] * grid.n * nf
+        print(json.dumps({"case": "stage", "nf": nf, "ms": ms, "gpair_per_s": pairs / ms / 1e6,
                           "variant": variant, "tile": tile, "tpt": tpt,
                           "checksum": float(out.abs().sum().item())}), flush=True)
 
