@@ -196,9 +196,10 @@ int rsi_propagate_stage(const rsi_stage *st,
  * and its source amplitude.  ks: the nf wavenumbers (st->k is not used);
  * src_sigma: complex [nf][n_src] (RSI; NULL for PISTON, whose amplitude does
  * not depend on the frequency); tgt_field: complex [nf][n_tgt], overwritten.
- * FP32C only (st->variant is not used), 2 <= nf <= 4.  Each frequency's
- * result equals a single-frequency rsi_propagate_stage to rounding; other
- * conventions as rsi_propagate_stage.  The workspace size depends on nf.     */
+ * FP32C only, 2 <= nf <= 4; st->variant 0 or 3: two sources per packed
+ * f32x2 instruction, 2: scalar.  Each frequency's result equals a
+ * single-frequency rsi_propagate_stage to rounding; other conventions as
+ * rsi_propagate_stage.  The workspace size depends on nf and the variant.   */
 size_t rsi_stage_multi_workspace_bytes(const rsi_stage *st, int32_t nf, const double *ks, int64_t n_src,
                                        int64_t n_tgt);
 int rsi_propagate_stage_multi(const rsi_stage *st, int32_t nf, const double *ks,

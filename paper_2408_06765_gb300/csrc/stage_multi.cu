@@ -20,7 +20,7 @@ constexpr int kMaxNF = 4;
 constexpr int kMTpt = 2;
 
 struct MultiArgs {
-    int kind, normals, nf, S, n_tiles, tiles_per_split, splits;
+    int kind, normals, nf, packed, S, n_tiles, tiles_per_split, splits;
     int64_t n_tgt;
     size_t tile_bytes;
     const uint8_t* tiles;
@@ -172,21 +172,131 @@ __device__ __forceinline__ void mpair_near(const MRef& t, const float4* r, const
     mterms<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
 }
 
+// ---------------------------------------------------------------------------
+// Packed form: two sources per f32x2 instruction, records pair-interleaved
+// with the signs and the factor 1/2 of the single-frequency packed kernel
+// (field f of source 2i+L at float (2i) rf + 2f + L):
+//   [px, py, -pz, |p|^2/2], then RSI nf x [-B.re, -B.im, C.re, C.im] or
+//   PISTON [A, 0, 0, 0], then [nx, ny, nz, -n.p] for per-point normals.
+// ---------------------------------------------------------------------------
+struct MRef2 {
+    float2 mx, my, mz, R2, nR, pR, Dx, Dy, Dz;
+    float2 tau[kMaxNF];
+};
+template <int NF>
+__device__ __forceinline__ MRef2 packed_mref(const MRef& t) {
+    MRef2 r;
+    r.mx = make_float2(-t.Dx, -t.Dx);
+    r.my = make_float2(-t.Dy, -t.Dy);
+    r.mz = make_float2(t.Dz, t.Dz);
+    r.R2 = make_float2(t.R2, t.R2);
+    r.nR = make_float2(-t.R, -t.R);
+    r.pR = make_float2(t.R, t.R);
+    r.Dx = make_float2(t.Dx, t.Dx);
+    r.Dy = make_float2(t.Dy, t.Dy);
+    r.Dz = make_float2(t.Dz, t.Dz);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) r.tau[f] = make_float2(t.tau[f], t.tau[f]);
+    return r;
+}
+
+// two sources (records pr[0..RF4*2-1], packed) onto one target, far path;
+// acc[f] = (sum h vr c, sum h vi s, sum h vr s, sum h vi c) for RSI or
+// (sum A c / r, -, sum A s / r, -) for the piston
 template <int KIND, int NORM, int NF>
+__device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, const float2* kv,
+                                           float2 (&acc)[NF][4]) {
+    const float4 v0 = pr[0], v1 = pr[1];
+    const float2 px = make_float2(v0.x, v0.y), py = make_float2(v0.z, v0.w);
+    const float2 pzn = make_float2(v1.x, v1.y), pwh = make_float2(v1.z, v1.w);
+    const float2 th = __ffma2_rn(t.mx, px, __ffma2_rn(t.my, py, __ffma2_rn(t.mz, pzn, pwh)));
+    const float2 r2 = __ffma2_rn(th, make_float2(2.0f, 2.0f), t.R2);
+    float2 ir;
+    ir.x = rsqrt_approx(r2.x);
+    ir.y = rsqrt_approx(r2.y);
+    const float2 r0 = __fmul2_rn(r2, ir);
+    const float2 am = __fadd2_rn(r0, t.nR);
+    const float2 q = __fmul2_rn(am, __fadd2_rn(r0, t.pR));
+    const float2 eh = __ffma2_rn(q, make_float2(-0.5f, -0.5f), th);
+    const float2 dr = __ffma2_rn(eh, ir, am);
+    if (KIND == RSI_STAGE_PISTON) {
+        const float4 va = pr[2];
+        const float2 amp = __fmul2_rn(make_float2(va.x, va.y), ir);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
+            float2 sn, cs;
+            __sincosf(u.x, &sn.x, &cs.x);
+            __sincosf(u.y, &sn.y, &cs.y);
+            acc[f][0] = __ffma2_rn(amp, cs, acc[f][0]);
+            acc[f][2] = __ffma2_rn(amp, sn, acc[f][2]);
+        }
+    } else {
+        float2 nd;
+        if (NORM == RSI_NORMALS_Z) {
+            nd = __fadd2_rn(t.Dz, pzn);
+        } else {
+            const float4 n0 = pr[2 + 2 * NF], n1 = pr[3 + 2 * NF];
+            nd = __ffma2_rn(make_float2(n0.x, n0.y), t.Dx,
+                            __ffma2_rn(make_float2(n0.z, n0.w), t.Dy,
+                                       __ffma2_rn(make_float2(n1.x, n1.y), t.Dz, make_float2(n1.z, n1.w))));
+        }
+        const float2 h = __fmul2_rn(nd, __fmul2_rn(ir, ir));
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const float4 b0 = pr[2 + 2 * f], b1 = pr[3 + 2 * f];
+            const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
+            float2 sn, cs;
+            __sincosf(u.x, &sn.x, &cs.x);
+            __sincosf(u.y, &sn.y, &cs.y);
+            const float2 vr = __ffma2_rn(ir, make_float2(b0.x, b0.y), make_float2(b1.x, b1.y));
+            const float2 vi = __ffma2_rn(ir, make_float2(b0.z, b0.w), make_float2(b1.z, b1.w));
+            const float2 hv = __fmul2_rn(h, vr), hw = __fmul2_rn(h, vi);
+            acc[f][0] = __ffma2_rn(hv, cs, acc[f][0]);
+            acc[f][1] = __ffma2_rn(hw, sn, acc[f][1]);
+            acc[f][2] = __ffma2_rn(hv, sn, acc[f][2]);
+            acc[f][3] = __ffma2_rn(hw, cs, acc[f][3]);
+        }
+    }
+}
+
+// one source of a packed tile, unpacked into the scalar record format
+template <int KIND, int NORM, int NF>
+__device__ __forceinline__ void munpack(const float* tile_rec, int i, float4* r) {
+    constexpr int rf = 4 * mrec_f4<KIND, NORM, NF>();
+    const float* q = tile_rec + (i >> 1) * 2 * rf + (i & 1);
+    r[0] = make_float4(q[0], q[2], -q[4], 2.0f * q[6]);
+    if (KIND == RSI_STAGE_PISTON) {
+        r[1] = make_float4(q[8], 0.f, 0.f, 0.f);
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const float* b = q + 8 + 8 * f;
+            r[1 + f] = make_float4(-b[0], -b[2], b[4], b[6]);
+        }
+        if (NORM == RSI_NORMALS_POINTS) {
+            const float* n = q + 8 + 8 * NF;
+            r[1 + NF] = make_float4(n[0], n[2], n[4], -n[6]);
+        }
+    }
+}
+
+template <int KIND, int NORM, int NF, int PK>
 __global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RSI_PIPE_STAGES * a.tile_bytes);
     init_barriers(bars);
     constexpr int RF4 = mrec_f4<KIND, NORM, NF>();
+    constexpr int TPT = PK ? 1 : kMTpt;
     const int tid = threadIdx.x;
     const int split = blockIdx.y;
     const int t_begin = split * a.tiles_per_split;
     const int ntile = max(0, min(a.n_tiles, t_begin + a.tiles_per_split) - t_begin);
     const uint32_t tb = uint32_t(a.tile_bytes);
-    int64_t jt[kMTpt];
+    int64_t jt[TPT];
 #pragma unroll
-    for (int q = 0; q < kMTpt; ++q) {
-        const int64_t j = int64_t(blockIdx.x) * kMTpt * kThreads + int64_t(q) * kThreads + tid;
+    for (int q = 0; q < TPT; ++q) {
+        const int64_t j = int64_t(blockIdx.x) * TPT * kThreads + int64_t(q) * kThreads + tid;
         jt[q] = j < a.n_tgt ? j : a.n_tgt - 1;
     }
     if (tid == 0)
@@ -198,9 +308,9 @@ __global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
     float kv[NF];
 #pragma unroll
     for (int f = 0; f < NF; ++f) kv[f] = a.kh[f];
-    float hr[kMTpt][NF], lr[kMTpt][NF], hi[kMTpt][NF], li[kMTpt][NF];
+    float hr[TPT][NF], lr[TPT][NF], hi[TPT][NF], li[TPT][NF];
 #pragma unroll
-    for (int q = 0; q < kMTpt; ++q)
+    for (int q = 0; q < TPT; ++q)
 #pragma unroll
         for (int f = 0; f < NF; ++f) hr[q][f] = lr[q][f] = hi[q][f] = li[q][f] = 0.0f;
     int failed_at = -1;
@@ -214,12 +324,12 @@ __global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
         const uint8_t* tile = smem + buf * tb;
         const float* hdr = reinterpret_cast<const float*>(tile);
         const float4* rec = reinterpret_cast<const float4*>(tile + RSI_TILE_HDR_BYTES);
-        MRef ref[kMTpt];
-        float ar[kMTpt][NF], ai[kMTpt][NF];
+        MRef ref[TPT];
+        float ar[TPT][NF], ai[TPT][NF];
         const float far_min = 2.0f * hdr[6];
         bool far_lane = true;
 #pragma unroll
-        for (int q = 0; q < kMTpt; ++q) {
+        for (int q = 0; q < TPT; ++q) {
             const int64_t j = jt[q];
             ref[q] = multi_reference<NF>(__ldg(a.tgt.xh + j), __ldg(a.tgt.xl + j), __ldg(a.tgt.yh + j),
                                          __ldg(a.tgt.yl + j), __ldg(a.tgt.zh + j), __ldg(a.tgt.zl + j), hdr, a);
@@ -227,14 +337,46 @@ __global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
 #pragma unroll
             for (int f = 0; f < NF; ++f) ar[q][f] = ai[q][f] = 0.0f;
         }
-        if (__all_sync(0xffffffffu, far_lane)) {
+        if (PK && __all_sync(0xffffffffu, far_lane)) {
+            float2 k2[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) k2[f] = make_float2(kv[f], kv[f]);
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+                const MRef2 r2 = packed_mref<NF>(ref[q]);
+                float2 acc[NF][4];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = make_float2(0.f, 0.f);
+#pragma unroll 1
+                for (int i = 0; i < a.S / 2; ++i) {
+                    float4 pr[2 * RF4];
+#pragma unroll
+                    for (int m = 0; m < 2 * RF4; ++m) pr[m] = rec[i * 2 * RF4 + m];
+                    mpair_far2<KIND, NORM, NF>(r2, pr, k2, acc);
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    ar[q][f] = (acc[f][0].x + acc[f][0].y) - (acc[f][1].x + acc[f][1].y);
+                    ai[q][f] = (acc[f][2].x + acc[f][2].y) + (acc[f][3].x + acc[f][3].y);
+                }
+            }
+        } else if (PK) {
+            const float* tf = reinterpret_cast<const float*>(rec);
+#pragma unroll 1
+            for (int i = 0; i < a.S; ++i) {
+                float4 r[RF4];
+                munpack<KIND, NORM, NF>(tf, i, r);
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) mpair_near<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
+            }
+        } else if (__all_sync(0xffffffffu, far_lane)) {
 #pragma unroll 1
             for (int i = 0; i < a.S; ++i) {
                 float4 r[RF4];
 #pragma unroll
                 for (int m = 0; m < RF4; ++m) r[m] = rec[i * RF4 + m];
 #pragma unroll
-                for (int q = 0; q < kMTpt; ++q) mpair_far<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
+                for (int q = 0; q < TPT; ++q) mpair_far<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
             }
         } else {
 #pragma unroll 1
@@ -243,11 +385,11 @@ __global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
 #pragma unroll
                 for (int m = 0; m < RF4; ++m) r[m] = rec[i * RF4 + m];
 #pragma unroll
-                for (int q = 0; q < kMTpt; ++q) mpair_near<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
+                for (int q = 0; q < TPT; ++q) mpair_near<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
             }
         }
 #pragma unroll
-        for (int q = 0; q < kMTpt; ++q)
+        for (int q = 0; q < TPT; ++q)
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 float s, e;
@@ -275,8 +417,8 @@ __global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
     }
     double2* out = a.out + (a.splits > 1 ? size_t(split) * size_t(NF) * size_t(a.n_tgt) : 0);
 #pragma unroll
-    for (int q = 0; q < kMTpt; ++q) {
-        const int64_t j = int64_t(blockIdx.x) * kMTpt * kThreads + int64_t(q) * kThreads + tid;
+    for (int q = 0; q < TPT; ++q) {
+        const int64_t j = int64_t(blockIdx.x) * TPT * kThreads + int64_t(q) * kThreads + tid;
         if (j < a.n_tgt)
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
@@ -312,8 +454,11 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
         cl[d] = __double2float_rn(c[d] - double(ch[d]));
     }
     const int rf = 4 * mrec_f4_rt(kind, normals, nf);
+    // field fi of this source: rec[fi * fs] (packed: pair-interleaved, see MRef2)
+    const bool pk = a.packed != 0;
+    const int fs = pk ? 2 : 1;
     float* rec = reinterpret_cast<float*>(tiles + size_t(tile) * tile_bytes + RSI_TILE_HDR_BYTES) +
-                 size_t(threadIdx.x) * rf;
+                 (pk ? size_t(threadIdx.x >> 1) * 2 * rf + (threadIdx.x & 1) : size_t(threadIdx.x) * rf);
     float px = 4.0f, py = 4.0f, pz = 4.0f;
     if (valid) {
         float h, l;
@@ -324,36 +469,37 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
         df_diff(src.zh[i], src.zl[i], ch[2], cl[2], h, l);
         pz = h;
     }
-    rec[0] = px;
-    rec[1] = py;
-    rec[2] = pz;
-    rec[3] = fmaf(px, px, fmaf(py, py, pz * pz));
+    const float sg = pk ? -1.0f : 1.0f;  // packed: -pz, -B, -n.p and |p|^2 / 2
+    rec[0 * fs] = px;
+    rec[1 * fs] = py;
+    rec[2 * fs] = sg * pz;
+    rec[3 * fs] = (pk ? 0.5f : 1.0f) * fmaf(px, px, fmaf(py, py, pz * pz));
     if (kind == RSI_STAGE_PISTON) {
-        rec[4] = valid ? float(amp_scale * src.w[i]) : 0.0f;
-        rec[5] = rec[6] = rec[7] = 0.0f;
+        rec[4 * fs] = valid ? float(amp_scale * src.w[i]) : 0.0f;
+        rec[5 * fs] = rec[6 * fs] = rec[7 * fs] = 0.0f;
     } else {
         for (int f = 0; f < nf; ++f) {
-            float* b = rec + 4 + 4 * f;
+            float* b = rec + (4 + 4 * f) * fs;
             if (valid) {
                 const double k = double(a.kh[f]) + double(a.kl[f]);
-                const double2 sg = sigma[size_t(f) * size_t(n_src) + size_t(i)];
-                const double br = amp_scale * src.w[i] * sg.x, bi = amp_scale * src.w[i] * sg.y;
-                b[0] = float(br);
-                b[1] = float(bi);
-                b[2] = float(-k * bi);
-                b[3] = float(k * br);
+                const double2 sgm = sigma[size_t(f) * size_t(n_src) + size_t(i)];
+                const double br = amp_scale * src.w[i] * sgm.x, bi = amp_scale * src.w[i] * sgm.y;
+                b[0 * fs] = sg * float(br);
+                b[1 * fs] = sg * float(bi);
+                b[2 * fs] = float(-k * bi);
+                b[3 * fs] = float(k * br);
             } else {
-                b[0] = b[1] = b[2] = b[3] = 0.0f;
+                b[0 * fs] = b[1 * fs] = b[2 * fs] = b[3 * fs] = 0.0f;
             }
         }
         if (normals == RSI_NORMALS_POINTS) {
-            float* n = rec + 4 + 4 * nf;
+            float* n = rec + (4 + 4 * nf) * fs;
             const float nx = valid ? float(src.nx[i]) : 0.0f, ny = valid ? float(src.ny[i]) : 0.0f,
                         nz = valid ? float(src.nz[i]) : 1.0f;
-            n[0] = nx;
-            n[1] = ny;
-            n[2] = nz;
-            n[3] = fmaf(nx, px, fmaf(ny, py, nz * pz));
+            n[0 * fs] = nx;
+            n[1 * fs] = ny;
+            n[2 * fs] = nz;
+            n[3 * fs] = sg * fmaf(nx, px, fmaf(ny, py, nz * pz));
         }
     }
     const double rad = block_reduce(valid ? double(px * px + py * py + pz * pz) : 0.0, true, red);
@@ -372,9 +518,9 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
 
 size_t msmem(size_t tile_bytes) { return RSI_PIPE_STAGES * tile_bytes + RSI_PIPE_STAGES * sizeof(uint64_t); }
 
-template <int KIND, int NORM, int NF>
+template <int KIND, int NORM, int NF, int PK>
 int mlaunch(const MultiArgs& a, cudaStream_t s, bool occ, int* occ_out) {
-    auto kern = stage_multi_kernel<KIND, NORM, NF>;
+    auto kern = stage_multi_kernel<KIND, NORM, NF, PK>;
     static bool attr = false;
     if (!attr) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
@@ -388,26 +534,30 @@ int mlaunch(const MultiArgs& a, cudaStream_t s, bool occ, int* occ_out) {
         *occ_out = b > 0 ? b : 1;
         return RSI_OK;
     }
-    const int64_t per_block = int64_t(kThreads) * kMTpt;
+    const int64_t per_block = int64_t(kThreads) * (PK ? 1 : kMTpt);
     dim3 grid(unsigned((a.n_tgt + per_block - 1) / per_block), unsigned(a.splits));
     kern<<<grid, kThreads, msmem(a.tile_bytes), s>>>(a);
     RSI_CHECK_LAUNCH("stage_multi_kernel");
     return RSI_OK;
 }
 
-template <int KIND, int NORM>
+template <int KIND, int NORM, int PK>
 int mdispatch_nf(const MultiArgs& a, cudaStream_t s, bool occ, int* o) {
     switch (a.nf) {
-        case 2: return mlaunch<KIND, NORM, 2>(a, s, occ, o);
-        case 3: return mlaunch<KIND, NORM, 3>(a, s, occ, o);
-        default: return mlaunch<KIND, NORM, 4>(a, s, occ, o);
+        case 2: return mlaunch<KIND, NORM, 2, PK>(a, s, occ, o);
+        case 3: return mlaunch<KIND, NORM, 3, PK>(a, s, occ, o);
+        default: return mlaunch<KIND, NORM, 4, PK>(a, s, occ, o);
     }
+}
+template <int KIND, int NORM>
+int mdispatch_pk(const MultiArgs& a, cudaStream_t s, bool occ, int* o) {
+    return a.packed ? mdispatch_nf<KIND, NORM, 1>(a, s, occ, o) : mdispatch_nf<KIND, NORM, 0>(a, s, occ, o);
 }
 
 int mdispatch(const MultiArgs& a, cudaStream_t s, bool occ, int* o) {
-    if (a.kind == RSI_STAGE_PISTON) return mdispatch_nf<RSI_STAGE_PISTON, RSI_NORMALS_Z>(a, s, occ, o);
-    if (a.normals == RSI_NORMALS_POINTS) return mdispatch_nf<RSI_STAGE_RSI, RSI_NORMALS_POINTS>(a, s, occ, o);
-    return mdispatch_nf<RSI_STAGE_RSI, RSI_NORMALS_Z>(a, s, occ, o);
+    if (a.kind == RSI_STAGE_PISTON) return mdispatch_pk<RSI_STAGE_PISTON, RSI_NORMALS_Z>(a, s, occ, o);
+    if (a.normals == RSI_NORMALS_POINTS) return mdispatch_pk<RSI_STAGE_RSI, RSI_NORMALS_POINTS>(a, s, occ, o);
+    return mdispatch_pk<RSI_STAGE_RSI, RSI_NORMALS_Z>(a, s, occ, o);
 }
 
 struct MPlan {
@@ -445,6 +595,9 @@ int mplan(const rsi_stage& st, int nf, const double* ks, int64_t n_src, int64_t 
     a.kind = st.kind;
     a.normals = normals;
     a.nf = nf;
+    if (st.variant != 0 && st.variant != 2 && st.variant != 3)
+        return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi: variant must be 0, 2 or 3");
+    a.packed = st.variant != 2;  // 3 (and 0): two sources per f32x2 instruction; 2: scalar
     a.S = p.S;
     a.n_tiles = p.n_tiles;
     a.n_tgt = n_tgt;
@@ -455,7 +608,8 @@ int mplan(const rsi_stage& st, int nf, const double* ks, int64_t n_src, int64_t 
         a.kl[f] = float(k - double(a.kh[f]));
     }
     a.tp = two_pi_split();
-    const int64_t blocks = (n_tgt + int64_t(kThreads) * kMTpt - 1) / (int64_t(kThreads) * kMTpt);
+    const int tpt = a.packed ? 1 : kMTpt;
+    const int64_t blocks = (n_tgt + int64_t(kThreads) * tpt - 1) / (int64_t(kThreads) * tpt);
     int splits = st.splits;
     if (splits < 0) return rsi_fail(RSI_E_INVAL, "splits must be >= 0");
     if (splits == 0) {

@@ -38,7 +38,7 @@ def host(p):
 
 @pytest.mark.parametrize("nf", [2, 3, 4])
 @pytest.mark.parametrize("case", ["piston", "rsi_flat", "rsi_curved"])
-@pytest.mark.parametrize("shape", [{}, {"tile": 32, "splits": 3}, {"tile": 128, "splits": 1}])
+@pytest.mark.parametrize("shape", [{}, {"tile": 32, "splits": 3}, {"tile": 128, "splits": 1, "variant": 2}])
 def test_multi_matches_single_stages_and_oracle(nf, case, shape):
     freqs = [1.7e6, 3.1e6, 5.5e6, 9.2e6][:nf]
     if case == "piston":
@@ -62,10 +62,12 @@ def test_multi_matches_single_stages_and_oracle(nf, case, shape):
     rsi.sync_status()
     hs = host(src)
     tq = {k: v for k, v in host(tgt).items() if k in ("x", "y", "z")}
+    packed = shape.get("variant", 0) != 2
     for f, k in enumerate(ks):
-        one = rsi.stage_struct(kind, "fp32c", k, 1.0, normals, variant=2, **shape)
+        one = rsi.stage_struct(kind, "fp32c", k, 1.0, normals, **dict(shape, variant=3 if packed else 2))
         single = rsi.propagate_stage(one, src, None if sig is None else sig[f].contiguous(), tgt).cpu().numpy()
-        assert rel(got[f], single) < 1e-6, f  # the same arithmetic per frequency
+        # the same arithmetic per frequency (the packed form sums in a different order)
+        assert rel(got[f], single) < (2e-5 if packed else 1e-6), f
         want = oracle.piston_field(hs, tq, k) if sig is None else oracle.rsi_field(hs, sig[f].cpu().numpy(), tq, k)
         assert rel(got[f], want) < 1e-4, f
 
@@ -101,8 +103,8 @@ def test_chain_multi_matches_oracle():
         want, _ = oracle.chain(cfg)
         k_last = oracle.wavenumber(cfg["freq"], cfg["media"][-1]["c"])
         assert rel(img.cpu().numpy(), k_last * want) < 1e-4
-        single = rsi.run_chain(cfg, stage_opts={"variant": 2}).image
-        assert rel(img.cpu().numpy(), single.cpu().numpy()) < 1e-6
+        single = rsi.run_chain(cfg).image
+        assert rel(img.cpu().numpy(), single.cpu().numpy()) < 2e-5
 
 
 def test_c2_frequencies_together_match_stored_oracle():
