@@ -218,12 +218,14 @@ ISSUE_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
 
 def multi_ops(kind: str, nf: int) -> dict:
     """Per pair-term counts of the multi-frequency stage kernel (nf frequencies
-    on shared points, scalar arithmetic): the shared geometry once per pair,
-    phase, sincos and epilogue per frequency; the source record (1 + nf float4
-    for RSI, 2 for the piston) is read once per two targets."""
-    if kind == "rsi":  # shared: r - R (10), obliquity and cos/r (3); per f: 10 + the sincos scaling
-        return {"fp32": 13.0 / nf + 11.0, "mufu": 2.0 + 1.0 / nf, "lds": (1.0 + nf) / (2.0 * nf)}
-    return {"fp32": 11.0 / nf + 4.0, "mufu": 2.0 + 1.0 / nf, "lds": 1.0 / nf}
+    on shared points, two sources per packed f32x2 instruction, one target per
+    thread): the shared geometry once per source pair, phase, sincos and
+    epilogue per frequency, plus one scalar scaling of each sincos argument;
+    the packed record of a source pair (2 + 2 nf float4 for RSI, 4 for the
+    piston) is read once per target."""
+    if kind == "rsi":  # per source pair: shared 14 packed, per f 9 packed
+        return {"fp32": 14.0 / (2 * nf) + 4.5 + 1.0, "mufu": 2.0 + 1.0 / nf, "lds": (2.0 + 2 * nf) / (2.0 * nf)}
+    return {"fp32": 11.0 / (2 * nf) + 1.5 + 1.0, "mufu": 2.0 + 1.0 / nf, "lds": 4.0 / (2.0 * nf)}
 
 
 def alu_roofline(kind: str, n_sm: int, clock_hz: float, ops: dict | None = None):
