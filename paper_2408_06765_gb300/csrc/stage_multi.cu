@@ -18,6 +18,13 @@ using namespace rsi_fp32;
 
 constexpr int kMaxNF = 4;
 constexpr int kMTpt = 2;
+// resident CTAs per SM asked of the compiler for the packed form (one target
+// per thread): 4 measured best on the 3-frequency RSI stage (1910 Gpair-terms/s
+// at 64 registers; 3 CTAs 1890, 2 CTAs 1782); four frequencies keep 3 CTAs
+// (at the 64-register cap of 4 CTAs their accumulators spill)
+#ifndef RSI_MULTI_PACKED_MIN_BLOCKS
+#define RSI_MULTI_PACKED_MIN_BLOCKS 4
+#endif
 
 struct MultiArgs {
     int kind, normals, nf, packed, S, n_tiles, tiles_per_split, splits;
@@ -282,7 +289,8 @@ __device__ __forceinline__ void munpack(const float* tile_rec, int i, float4* r)
 }
 
 template <int KIND, int NORM, int NF, int PK>
-__global__ void __launch_bounds__(kThreads, 2) stage_multi_kernel(MultiArgs a) {
+__global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED_MIN_BLOCKS) : 2)
+    stage_multi_kernel(MultiArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RSI_PIPE_STAGES * a.tile_bytes);
     init_barriers(bars);
