@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--epochs", type=int, default=1500, help="c5: training epochs")
     ap.add_argument("--sigma-b", type=float, default=0.25, help="c5: Fourier feature scale")
     ap.add_argument("--lr", type=float, default=1e-3, help="c5: peak learning rate")
+    ap.add_argument("--gemm-shape", default="1024,32768,512",
+                    help="--case gemm: M,N,K (default: the surrogate's output layer at batch 1024)")
     ap.add_argument("--engine", choices=["tcgen05", "mma_sync"], default="tcgen05", help="c5: GEMM engine")
     ap.add_argument("--sweep", action="store_true",
                     help="with --case stage: time every tile / targets-per-thread / variant")
@@ -762,26 +764,29 @@ def run_raytrace_f2(args):
 
 def run_gemm_case(args):
     """The surrogate's dominant kernel alone: the output-layer GEMM of batch-1024
-    inference, [1024 x 512] x [512 x 32768] + bias with an f32 output, `steps`
-    times on random BF16 operands (the GEMM engine of --engine)."""
+    inference, [1024 x 512] x [512 x 32768] + bias with an f32 output (or the
+    --gemm-shape M,N,K), on random BF16 operands (the GEMM engine of --engine);
+    each of the `steps` samples averages 20 back-to-back launches."""
     import torch
     from paper_2408_06765_gb300 import build, rsi
     build.build()
     rsi.load()
     g = torch.Generator(device="cuda").manual_seed(0)
-    M, N, K = 1024, 32768, 512
+    M, N, K = (int(x) for x in args.gemm_shape.split(","))
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
     bias = torch.randn(N, device="cuda", generator=g)
     out = torch.empty(M, N, device="cuda")
+    reps = 20  # back-to-back launches per sample: the host's per-call work overlaps the kernels
     times = []
     for _ in range(args.warmup + args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        rsi.nn_gemm("f32", A, B, out_f32=out, bias=bias, engine=args.engine)
+        for _ in range(reps):
+            rsi.nn_gemm("f32", A, B, out_f32=out, bias=bias, engine=args.engine)
         e1.record()
         e1.synchronize()
-        times.append(e0.elapsed_time(e1))
+        times.append(e0.elapsed_time(e1) / reps)
     rsi.sync_status()
     ms = min(times[args.warmup:])
     nbytes = 2.0 * (A.numel() + B.numel()) + 4.0 * (out.numel() + bias.numel())

@@ -241,7 +241,11 @@ __device__ __forceinline__ void epilogue4(float4 v, size_t o, int col, const flo
 // Every wait is bounded; on a timeout all roles stop, the CTA drains its
 // copies and MMAs, frees tensor memory and records RSI_DEV_TIMEOUT.
 // ---------------------------------------------------------------------------
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_EPI_WARPS = 8, TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+#ifndef RSI_TC_STAGES
+#define RSI_TC_STAGES 4  // operand ring depth (4 x 48 KB with 256-wide tiles fills shared memory)
+#endif
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = RSI_TC_STAGES, TC_EPI_WARPS = 8,
+              TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
 // epilogue staging: per warp 32 rows x 32 floats, 16-byte chunk j of row r
 // stored at chunk j ^ (r & 7) (conflict-free row writes and column reads)
