@@ -408,6 +408,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (__any_sync(0xffffffffu, abort_flag)) break;  // warp-uniform: tcgen05.ld below is .sync.aligned
             const TcTile T = tc_tile(t, m_tiles, n_tiles, TBN, kt_total, kts);
             const int acc = tc & 1;
+            // this warp's TBN/2 bias values, one float4 per lane, loaded before
+            // the accumulator wait so that their latency (L2, under the full
+            // load of the operand and output streams) hides behind it; each
+            // block takes its 32 values from the lanes by shuffles
+            const bool add_bias = EPI != 2 && splits == 1 && bias != nullptr;
+            float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (add_bias && 4 * lane < TBN / 2)
+                bq = __ldg(reinterpret_cast<const float4*>(bias + T.n0 + h * (TBN / 2)) + lane);
             const bool ok = mbar_wait_bounded(smem_u32(&acc_full[acc]), uint32_t(tc / 2) & 1u);
             if (!__all_sync(0xffffffffu, ok)) {
                 abort_flag = 1;
@@ -437,14 +445,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
                 }
-                if (EPI != 2 && splits == 1 && bias != nullptr) {
+                if (add_bias) {
+                    const int src = (cb - h * (TBN / 2)) / 4;  // the lane holding columns col0 .. col0 + 3
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const float4 b = *reinterpret_cast<const float4*>(bias + col0 + 4 * i);
-                        v[4 * i] += b.x;
-                        v[4 * i + 1] += b.y;
-                        v[4 * i + 2] += b.z;
-                        v[4 * i + 3] += b.w;
+                        v[4 * i] += __shfl_sync(0xffffffffu, bq.x, src + i);
+                        v[4 * i + 1] += __shfl_sync(0xffffffffu, bq.y, src + i);
+                        v[4 * i + 2] += __shfl_sync(0xffffffffu, bq.z, src + i);
+                        v[4 * i + 3] += __shfl_sync(0xffffffffu, bq.w, src + i);
                     }
                 }
                 if (EPI != 2 || splits > 1) {  // f32 block: output, z, or partial sums of split T.z
