@@ -961,7 +961,7 @@ def run_surrogate_c5(args):
     hp = params[ho]
     for c0 in range(0, (n_hold // 256) * 256, 256):
         pb = torch.tensor(hp[c0:c0 + 256], dtype=torch.float32, device="cuda")
-        pred = surrogate.modulate(net.predict(pb) * scale, hp[c0:c0 + 256])
+        pred = surrogate.modulate(net.predict(pb), hp[c0:c0 + 256], scale=scale)
         errs.append(surrogate.rel_errors(pred, imgs[ho][c0:c0 + 256]).cpu().numpy())
     errs = np.concatenate(errs)
     # split of the error: the best complex scale per field (amplitude and
@@ -969,7 +969,7 @@ def run_surrogate_c5(args):
     shape_errs = []
     for c0 in range(0, (n_hold // 256) * 256, 256):
         pb = torch.tensor(hp[c0:c0 + 256], dtype=torch.float32, device="cuda")
-        pred = surrogate.modulate(net.predict(pb) * scale, hp[c0:c0 + 256]).reshape(256, -1)
+        pred = surrogate.modulate(net.predict(pb), hp[c0:c0 + 256], scale=scale).reshape(256, -1)
         ref = imgs[ho][c0:c0 + 256].reshape(256, -1)
         alpha = (pred.conj() * ref).sum(1) / (pred.conj() * pred).sum(1)
         shape_errs.append(surrogate.rel_errors(alpha[:, None] * pred, ref).cpu().numpy())
@@ -987,7 +987,7 @@ def run_surrogate_c5(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(10):
-        surrogate.modulate(inf.predict(pq) * scale, params[:1024])
+        surrogate.modulate(inf.predict(pq), params[:1024], scale=scale)
     e1.record()
     e1.synchronize()
     nn_fields_s = 10 * 1024 / (e0.elapsed_time(e1) * 1e-3)

@@ -418,11 +418,13 @@ int rsi_nn_adam(float *w, float *m, float *v, const float *g, int64_t n, float l
                 float beta2, float eps, int32_t step, void *w_bf16, void *stream);
 /* bf16 copy of an f32 array.                                               */
 int rsi_nn_cast_bf16(const float *in, int64_t n, void *out_bf16, void *stream);
-/* out = in * exp(sign i psi) per pixel of batch images (complex f32 pairs,
- * row-major [nz][nx] over `window`, relative coordinates), with
- * psi = kx x + kz z + phi0 and carrier[b] = (kx, kz, phi0, unused) (f64).  */
+/* out = scale * in * exp(sign i psi) per pixel of batch images (complex f32
+ * pairs, row-major [nz][nx] over `window`, relative coordinates), with
+ * psi = kx x + kz z + phi0 and carrier[b] = (kx, kz, phi0, unused) (f64).
+ * The phase is reduced in FP32 to about 2e-6 rad; windows of more than 2^24
+ * pixels and a non-finite scale return RSI_E_INVAL.                        */
 int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window, int32_t sign,
-                   const float *in, float *out, void *stream);
+                   float scale, const float *in, float *out, void *stream);
 
 /* ---- measurement hooks (no counterpart in the paper) --------------------- */
 /* Number of kernels this library has enqueued in this process.             */

@@ -510,15 +510,17 @@ __global__ void features_kernel(const float* __restrict__ p, const float* __rest
     int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (q >= int64_t(batch) * F) return;
     const int b = int(q / F), f = int(q - int64_t(b) * F);
-    double a = 0.0;
+    // FP32 throughout: the features leave rounded to BF16 (2^-9), far above
+    // the FP32 error of the scaled inputs and of sincospi
+    float a = 0.0f;
     for (int j = 0; j < n_in; ++j) {
-        double u = 2.0 * (double(p[b * n_in + j]) - lo[j]) / (double(hi[j]) - lo[j]) - 1.0;
-        a += double(Bm[f * n_in + j]) * u;
+        const float u = fmaf(2.0f / (hi[j] - lo[j]), p[b * n_in + j] - lo[j], -1.0f);
+        a = fmaf(Bm[f * n_in + j], u, a);
     }
-    double s, c;
-    sincospi(a, &s, &c);
-    out[size_t(b) * 2 * F + f] = __float2bfloat16_rn(float(s));
-    out[size_t(b) * 2 * F + F + f] = __float2bfloat16_rn(float(c));
+    float s, c;
+    sincospif(a, &s, &c);
+    out[size_t(b) * 2 * F + f] = __float2bfloat16_rn(s);
+    out[size_t(b) * 2 * F + F + f] = __float2bfloat16_rn(c);
 }
 
 __global__ void transpose_kernel(const bf16* __restrict__ in, int rows, int cols, bf16* __restrict__ out) {
@@ -615,24 +617,58 @@ __global__ void cast_kernel(const float* __restrict__ in, int64_t n, bf16* __res
 }
 
 // img[b][j] (complex, float pairs) *= exp(sign * i psi_b(j)),
-// psi = kx x_i + kz z_j + phi0; carrier[b] = (kx, kz, phi0, unused)
-__global__ void carrier_kernel(const double* __restrict__ carrier, int batch, int nx, int nz, double x0,
-                               double dx, double z0, double dz, int sign, const float2* __restrict__ in,
-                               float2* __restrict__ out) {
-    int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t per = int64_t(nx) * nz;
-    if (q >= int64_t(batch) * per) return;
-    const int b = int(q / per);
-    const int64_t j = q - int64_t(b) * per;
-    const int iz = int(j / nx), ix = int(j - int64_t(iz) * nx);
-    const double* cb = carrier + 4 * b;
-    double x = x0 + (ix + 0.5) * dx, z = z0 + (iz + 0.5) * dz;
-    double psi = cb[0] * x + cb[1] * z + cb[2];
-    double s, c;
-    sincospi(psi / M_PI, &s, &c);
-    s *= sign;
-    float2 v = in[q];
-    out[q] = make_float2(float(v.x * c - v.y * s), float(v.x * s + v.y * c));
+// psi = kx x_i + kz z_j + phi0; carrier[b] = (kx, kz, phi0, unused).
+// In turns, psi / 2 pi = a + ix u + iz w with, per image,
+//   a = (phi0 + kx (x0 + dx/2) + kz (z0 + dz/2)) / 2 pi  (reduced mod 1),
+//   u = kx dx / 2 pi,  w = kz dz / 2 pi,
+// formed once per block in FP64 (GB300's FP64 rate is low, so none of it is
+// per pixel).  Per pixel ix u mod 1 is exact in FP32: with u = uh + ul (two
+// floats), p = ix uh and its rounding error e = fma(ix, uh, -p) are exact,
+// p - rint(p) is exact, and ix ul is a tiny correction; likewise iz w.  The
+// sum lies within a few turns and is reduced once more, so the phase carries
+// about 3e-7 turns (2e-6 rad) of error, then one FP32 sincospi.
+__device__ __forceinline__ float frac_mul(float i, float h, float l) {
+    const float p = i * h;
+    const float e = fmaf(i, h, -p);
+    return ((p - rintf(p)) + e) + i * l;
+}
+
+__global__ void __launch_bounds__(256) carrier_kernel(const double* __restrict__ carrier, int batch, int nx,
+                                                      int per, double x0, double dx, double z0, double dz, int sign,
+                                                      float scale, const float2* __restrict__ in,
+                                                      float2* __restrict__ out) {
+    __shared__ float k[6];  // ah, al, uh, ul, wh, wl
+    for (int b = blockIdx.y; b < batch; b += gridDim.y) {
+        __syncthreads();  // the previous image's constants are no longer read
+        if (threadIdx.x == 0) {
+            const double* cb = carrier + 4 * b;
+            const double inv2pi = 0.15915494309189535;  // 1 / (2 pi)
+            double ad = (cb[2] + cb[0] * (x0 + 0.5 * dx) + cb[1] * (z0 + 0.5 * dz)) * inv2pi;
+            ad -= rint(ad);
+            const double ud = cb[0] * dx * inv2pi, wd = cb[1] * dz * inv2pi;
+            k[0] = float(ad);
+            k[1] = float(ad - double(k[0]));
+            k[2] = float(ud);
+            k[3] = float(ud - double(k[2]));
+            k[4] = float(wd);
+            k[5] = float(wd - double(k[4]));
+        }
+        __syncthreads();
+        const float ah = k[0], al = k[1], uh = k[2], ul = k[3], wh = k[4], wl = k[5];
+        const float2* src = in + int64_t(b) * per;
+        float2* dst = out + int64_t(b) * per;
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < per; j += gridDim.x * blockDim.x) {
+            const int iz = j / nx, ix = j - iz * nx;
+            float t = (ah + frac_mul(float(ix), uh, ul)) + frac_mul(float(iz), wh, wl);
+            t = (t - rintf(t)) + al;
+            float s, c;
+            sincospif(2.0f * t, &s, &c);
+            s = sign > 0 ? s * scale : -s * scale;
+            c *= scale;
+            const float2 v = src[j];
+            dst[j] = make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
+        }
+    }
 }
 
 int sm_count() {
@@ -871,14 +907,19 @@ extern "C" int rsi_nn_cast_bf16(const float* in, int64_t n, void* out_bf16, void
 }
 
 extern "C" int rsi_nn_carrier(const double* carrier, int32_t batch, const rsi_grid* window, int32_t sign,
-                              const float* in, float* out, void* stream) {
-    if (!carrier || !window || !in || !out || batch < 1 || (sign != 1 && sign != -1))
+                              float scale, const float* in, float* out, void* stream) {
+    if (!carrier || !window || !in || !out || batch < 1 || (sign != 1 && sign != -1) || !isfinite(scale))
         return rsi_fail(RSI_E_INVAL, "rsi_nn_carrier: bad arguments");
     if (window->nx < 1 || window->nz < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_carrier: empty window");
-    int64_t n = int64_t(batch) * window->nx * window->nz;
+    const int64_t per = int64_t(window->nx) * window->nz;
+    if (per > (int64_t(1) << 24))  // pixel indices stay exact in FP32
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_carrier: window of %lld pixels exceeds 2^24", (long long)per);
     double dx = (window->x1 - window->x0) / window->nx, dz = (window->z1 - window->z0) / window->nz;
-    carrier_kernel<<<unsigned((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        carrier, batch, window->nx, window->nz, window->x0, dx, window->z0, dz, sign,
+    // about 4 pixels per thread, one row of blocks per image
+    const unsigned bx = unsigned(std::max<int64_t>(1, std::min<int64_t>(256, (per + 1023) / 1024)));
+    const dim3 grid(bx, unsigned(std::min(batch, 65535)));
+    carrier_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        carrier, batch, window->nx, int(per), window->x0, dx, window->z0, dz, sign, scale,
         reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out));
     RSI_CHECK_LAUNCH("carrier_kernel");
     return RSI_OK;

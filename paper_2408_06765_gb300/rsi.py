@@ -157,7 +157,7 @@ def load(path: str | None = None):
         L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
         L.rsi_nn_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
         L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
-        L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, vp, vp, vp]
+        L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, ctypes.c_float, vp, vp, vp]
         L.rsi_selftest_wait_timeout.argtypes = [i64, vp]
         _lib = L
         return L
@@ -715,8 +715,8 @@ def nn_cast_bf16(x, out, stream=None):
     return out
 
 
-def nn_carrier(carrier, window: dict, sign: int, x, out, stream=None):
+def nn_carrier(carrier, window: dict, sign: int, x, out, stream=None, scale: float = 1.0):
     G = grid_struct(window)
-    _check(load().rsi_nn_carrier(_ptr(carrier), carrier.shape[0], ctypes.byref(G), int(sign), _ptr(x),
-                                 _ptr(out), _stream(stream)), "rsi_nn_carrier")
+    _check(load().rsi_nn_carrier(_ptr(carrier), carrier.shape[0], ctypes.byref(G), int(sign), float(scale),
+                                 _ptr(x), _ptr(out), _stream(stream)), "rsi_nn_carrier")
     return out

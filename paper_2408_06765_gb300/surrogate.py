@@ -203,11 +203,12 @@ def demodulate(images, params, device="cuda"):
     return out
 
 
-def modulate(env, params, device="cuda"):
-    """Image (complex64 [n, 128, 128]) from an interleaved envelope."""
+def modulate(env, params, device="cuda", scale: float = 1.0):
+    """Image (complex64 [n, 128, 128]) from an interleaved envelope, times
+    `scale` (the network's amplitude scale, applied in the same pass)."""
     car = torch.tensor(carrier_coeffs(params), dtype=torch.float64, device=device)
     out = torch.empty_like(env)
-    rsi.nn_carrier(car, WINDOW, +1, env.contiguous(), out)
+    rsi.nn_carrier(car, WINDOW, +1, env.contiguous(), out, scale=scale)
     return torch.view_as_complex(out.view(env.shape[0], 128, 128, 2))
 
 
@@ -243,8 +244,7 @@ class Surrogate:
         the error estimate is within the threshold, RSI elsewhere."""
         params = np.asarray(params, np.float64)
         p = torch.tensor(params, dtype=torch.float32, device=device)
-        env = self.net.predict(p) * self.net.scale
-        img = modulate(env, params, device)
+        img = modulate(self.net.predict(p), params, device, scale=self.net.scale)
         est = self.error_estimate(params)
         fall = np.nonzero(est > self.threshold)[0]
         if len(fall):

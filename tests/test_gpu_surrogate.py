@@ -164,6 +164,9 @@ def test_carrier_round_trip_and_definition():
     env = surrogate.demodulate(img, params)
     back = surrogate.modulate(env, params)
     assert rel(torch.view_as_real(back), torch.view_as_real(img)) < 1e-6
+    # the amplitude scale rides along in the same pass
+    back3 = surrogate.modulate(env, params, scale=3.0)
+    assert rel(torch.view_as_real(back3), 3.0 * torch.view_as_real(back)) < 1e-6
     # psi at one pixel, restated
     x_off, tilt, path, f, depth = params[0]
     k1, k2 = 2 * np.pi * f / 1480.0, 2 * np.pi * f / 5900.0
@@ -175,6 +178,20 @@ def test_carrier_round_trip_and_definition():
     want = complex(img[0, 7, 5]) * np.exp(-1j * psi)
     got = env[0].view(128, 128, 2)[7, 5]
     assert abs(complex(got[0], got[1]) - want) < 1e-5 * abs(want) + 1e-6
+    # every pixel of every image against the same definition in FP64
+    xs = -20e-3 + (np.arange(128) + 0.5) * 40e-3 / 128
+    zs = (np.arange(128) + 0.5) * 40e-3 / 128
+    full = img.cpu().numpy().astype(np.complex128)
+    for b in range(3):
+        x_off, tilt, path, f, depth = params[b]
+        k1, k2 = 2 * np.pi * f / 1480.0, 2 * np.pi * f / 5900.0
+        s = 5900.0 / 1480.0 * np.sin(tilt)
+        c = np.sqrt(max(0.0, 1 - s * s))
+        psi = k1 * path + k2 * (s * xs[None, :] + c * (zs[:, None] + depth))
+        want = full[b] * np.exp(-1j * psi)
+        e = env[b].view(128, 128, 2).cpu().numpy().astype(np.float64)
+        got = e[..., 0] + 1j * e[..., 1]
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5, b
 
 
 def small_net(engine="tcgen05"):
@@ -243,13 +260,13 @@ def test_surrogate_pipeline_gain_and_gate():
     losses = surrogate.train(net, params[tr], env[tr] / scale, epochs=20, lr=1e-3)
     assert losses[-1] < losses[0]
     pb = torch.tensor(params[ho], dtype=torch.float32, device="cuda")
-    pred = surrogate.modulate(net.predict(pb) * scale, params[ho])
+    pred = surrogate.modulate(net.predict(pb), params[ho], scale=scale)
     errs = surrogate.rel_errors(pred, imgs[ho]).cpu().numpy()
     assert np.all(np.isfinite(errs))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(5):
-        surrogate.modulate(net.predict(pb) * scale, params[ho])
+        surrogate.modulate(net.predict(pb), params[ho], scale=scale)
     torch.cuda.synchronize()
     nn_rate = 5 * 256 / (time.perf_counter() - t0)
     assert nn_rate > rsi_rate  # what the network gains over the method
