@@ -990,7 +990,19 @@ def run_surrogate_c5(args):
         surrogate.modulate(inf.predict(pq), params[:1024], scale=scale)
     e1.record()
     e1.synchronize()
-    nn_fields_s = 10 * 1024 / (e0.elapsed_time(e1) * 1e-3)
+    nn_fields_s_eager = 10 * 1024 / (e0.elapsed_time(e1) * 1e-3)
+    # the same batch through the CUDA-graph path; every call stages its
+    # parameters and carrier coefficients from the host
+    ginf = surrogate.GraphedInference(inf, scale)
+    batches = [params[(1024 * i) % (len(params) - 1024):][:1024] for i in range(20)]
+    ginf(batches[0])
+    torch.cuda.synchronize()
+    e0.record()
+    for bp in batches:
+        ginf(bp)
+    e1.record()
+    e1.synchronize()
+    nn_fields_s = len(batches) * 1024 / (e0.elapsed_time(e1) * 1e-3)
     # the dominant kernel: the output-layer GEMM of inference, [1024 x 512] x
     # [512 x 32768] with FP32 output (128 MiB, larger than L2), timed alone
     H, Wo = inf.H[inf.depth], inf.W16[-1]
@@ -1038,6 +1050,7 @@ def run_surrogate_c5(args):
             "held_out_fraction_below": {"1e-2": float(np.mean(errs <= 1e-2)), "3e-2": float(np.mean(errs <= 3e-2)),
                                         "1e-1": float(np.mean(errs <= 1e-1))},
             "surrogate_fields_per_s_batch1024": nn_fields_s,
+            "surrogate_fields_per_s_batch1024_eager": nn_fields_s_eager,
             "engine": args.engine, "train_step_ms_batch256": step_ms,
             # the f32 output (134 MB) dominates the bytes: HBM-write-bound;
             # the tensor-core rate is reported beside it

@@ -421,7 +421,8 @@ int rsi_nn_cast_bf16(const float *in, int64_t n, void *out_bf16, void *stream);
 /* out = scale * in * exp(sign i psi) per pixel of batch images (complex f32
  * pairs, row-major [nz][nx] over `window`, relative coordinates), with
  * psi = kx x + kz z + phi0 and carrier[b] = (kx, kz, phi0, unused) (f64).
- * The phase is reduced in FP32 to about 2e-6 rad; windows of more than 2^24
+ * The phase carries about 2e-6 rad of error, its sine and cosine about 4e-7;
+ * windows of more than 2^24
  * pixels and a non-finite scale return RSI_E_INVAL.                        */
 int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window, int32_t sign,
                    float scale, const float *in, float *out, void *stream);

@@ -626,7 +626,9 @@ __global__ void cast_kernel(const float* __restrict__ in, int64_t n, bf16* __res
 // floats), p = ix uh and its rounding error e = fma(ix, uh, -p) are exact,
 // p - rint(p) is exact, and ix ul is a tiny correction; likewise iz w.  The
 // sum lies within a few turns and is reduced once more, so the phase carries
-// about 3e-7 turns (2e-6 rad) of error, then one FP32 sincospi.
+// about 3e-7 turns (2e-6 rad) of error; the sine and cosine of the reduced
+// angle (|angle| <= pi) come from the hardware approximation (absolute error
+// about 4e-7).
 __device__ __forceinline__ float frac_mul(float i, float h, float l) {
     const float p = i * h;
     const float e = fmaf(i, h, -p);
@@ -657,12 +659,20 @@ __global__ void __launch_bounds__(256) carrier_kernel(const double* __restrict__
         const float ah = k[0], al = k[1], uh = k[2], ul = k[3], wh = k[4], wl = k[5];
         const float2* src = in + int64_t(b) * per;
         float2* dst = out + int64_t(b) * per;
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < per; j += gridDim.x * blockDim.x) {
-            const int iz = j / nx, ix = j - iz * nx;
+        const int j0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+        const int sz = stride / nx, sx = stride - sz * nx;  // the stride in rows and columns
+        int iz = j0 / nx, ix = j0 - iz * nx;
+        for (int j = j0; j < per; j += stride) {
             float t = (ah + frac_mul(float(ix), uh, ul)) + frac_mul(float(iz), wh, wl);
             t = (t - rintf(t)) + al;
             float s, c;
-            sincospif(2.0f * t, &s, &c);
+            __sincosf(6.283185307179586f * t, &s, &c);
+            ix += sx;
+            iz += sz;
+            if (ix >= nx) {
+                ix -= nx;
+                ++iz;
+            }
             s = sign > 0 ? s * scale : -s * scale;
             c *= scale;
             const float2 v = src[j];

@@ -194,9 +194,18 @@ def rsi_images(params, n_piston=1 << 14, n_iface=1 << 16, chunk=512, index0=0, d
     return torch.cat(out, 0)
 
 
+def _coeffs(params, device):
+    """carrier_coeffs on the device: staged in pinned memory and copied
+    without blocking, so the host does not wait for the kernels in flight."""
+    host = torch.from_numpy(carrier_coeffs(params))
+    if torch.device(device).type != "cuda":
+        return host.to(device)
+    return host.pin_memory().to(device, non_blocking=True)
+
+
 def demodulate(images, params, device="cuda"):
     """Envelope = image * exp(-i psi), as interleaved f32 [n, 2*128*128]."""
-    car = torch.tensor(carrier_coeffs(params), dtype=torch.float64, device=device)
+    car = _coeffs(params, device)
     x = torch.view_as_real(images.contiguous()).reshape(images.shape[0], -1)
     out = torch.empty_like(x)
     rsi.nn_carrier(car, WINDOW, -1, x, out)
@@ -206,7 +215,7 @@ def demodulate(images, params, device="cuda"):
 def modulate(env, params, device="cuda", scale: float = 1.0):
     """Image (complex64 [n, 128, 128]) from an interleaved envelope, times
     `scale` (the network's amplitude scale, applied in the same pass)."""
-    car = torch.tensor(carrier_coeffs(params), dtype=torch.float64, device=device)
+    car = _coeffs(params, device)
     out = torch.empty_like(env)
     rsi.nn_carrier(car, WINDOW, +1, env.contiguous(), out, scale=scale)
     return torch.view_as_complex(out.view(env.shape[0], 128, 128, 2))
@@ -219,6 +228,58 @@ def rel_errors(pred, ref):
     return (torch.linalg.vector_norm(d, dim=1) / torch.linalg.vector_norm(r, dim=1)).float()
 
 
+class GraphedInference:
+    """The surrogate's inference at a fixed batch (the network's B_alloc):
+    Fourier features, hidden layers, output layer and the carrier pass with
+    the amplitude scale, captured once into a CUDA graph and replayed per
+    batch.  Each call stages the parameters and carrier coefficients in
+    pinned host buffers, copies them to fixed device buffers without
+    blocking, and replays the graph: one launch instead of seven calls
+    through Python, so the batch runs at the kernels' speed.  The returned
+    images (complex64 [B, 128, 128]) are a view of a buffer that the next
+    call overwrites."""
+
+    def __init__(self, net: MLP, scale: float):
+        self.net, self.scale, self.B = net, float(scale), net.B_alloc
+        dev = net.device
+        self.p = torch.zeros(self.B, 5, dtype=torch.float32, device=dev)
+        self.car = torch.zeros(self.B, 4, dtype=torch.float64, device=dev)
+        self.out = torch.empty(self.B, 2 * 128 * 128, dtype=torch.float32, device=dev)
+        self.p_host = torch.zeros(self.B, 5, dtype=torch.float32).pin_memory()
+        self.car_host = torch.zeros(self.B, 4, dtype=torch.float64).pin_memory()
+        self.copied = None  # event: the last call's host buffers have been read
+        # one plain run first: the library's one-time set-up (kernel
+        # attributes, the status word) happens outside the capture
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            self._body()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._body()
+
+    def _body(self):
+        y = self.net.forward(self.p)
+        rsi.nn_carrier(self.car, WINDOW, +1, y, self.out, scale=self.scale)
+
+    def __call__(self, params) -> torch.Tensor:
+        params = np.asarray(params, np.float64)
+        if params.shape != (self.B, 5):
+            raise ValueError(f"GraphedInference takes exactly {self.B} parameter rows")
+        if self.copied is not None:
+            self.copied.synchronize()  # the previous call's copies have read the host buffers
+        self.p_host.copy_(torch.from_numpy(params.astype(np.float32)))
+        self.car_host.copy_(torch.from_numpy(carrier_coeffs(params)))
+        self.p.copy_(self.p_host, non_blocking=True)
+        self.car.copy_(self.car_host, non_blocking=True)
+        self.copied = torch.cuda.Event()
+        self.copied.record()
+        self.graph.replay()
+        return torch.view_as_complex(self.out.view(self.B, 128, 128, 2))
+
+
 class Surrogate:
     """Trained network + held-out error table for the fallback gate."""
 
@@ -226,6 +287,7 @@ class Surrogate:
         self.net, self.threshold, self.k = net, threshold, k
         self.held_u = self._norm(held_params)
         self.held_err = np.asarray(held_err, np.float64)
+        self._graph = None
 
     @staticmethod
     def _norm(params):
@@ -241,10 +303,12 @@ class Surrogate:
 
     def infer(self, params, device="cuda"):
         """Images for params (batch = the network's batch): surrogate where
-        the error estimate is within the threshold, RSI elsewhere."""
+        the error estimate is within the threshold, RSI elsewhere.  The
+        network runs through its CUDA graph (built on the first call)."""
         params = np.asarray(params, np.float64)
-        p = torch.tensor(params, dtype=torch.float32, device=device)
-        img = modulate(self.net.predict(p), params, device, scale=self.net.scale)
+        if self._graph is None:
+            self._graph = GraphedInference(self.net, self.net.scale)
+        img = self._graph(params).clone()
         est = self.error_estimate(params)
         fall = np.nonzero(est > self.threshold)[0]
         if len(fall):

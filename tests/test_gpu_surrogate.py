@@ -194,6 +194,21 @@ def test_carrier_round_trip_and_definition():
         assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5, b
 
 
+def test_graphed_inference_matches_eager():
+    """The CUDA-graph inference path gives the eager path's images, on two
+    batches in a row (its pinned staging buffers are reused)."""
+    net = surrogate.MLP(batch=256, seed=5)
+    g = surrogate.GraphedInference(net, scale=0.7)
+    rng = np.random.default_rng(9)
+    for _ in range(2):
+        params = surrogate.LO + (surrogate.HI - surrogate.LO) * rng.uniform(size=(256, 5))
+        got = g(params).clone()
+        pq = torch.tensor(params, dtype=torch.float32, device="cuda")
+        want = surrogate.modulate(net.predict(pq), params, scale=0.7)
+        assert rel(torch.view_as_real(got), torch.view_as_real(want)) < 1e-6
+    rsi.sync_status()
+
+
 def small_net(engine="tcgen05"):
     return surrogate.MLP(n_freq=64, width=128, depth=2, n_out=256, batch=128, seed=3, sigma_b=1.0, engine=engine)
 
