@@ -1029,6 +1029,18 @@ def run_surrogate_c5(args):
         net.train_step(p0, t0_, 0.0)
     e1.record()
     e1.synchronize()
+    step_ms_eager = e0.elapsed_time(e1) / 20
+    # the same step replayed from the CUDA graph that train() uses
+    trainer = surrogate.GraphedTrainer(net, [0.0] * 23)
+    idx0 = torch.arange(256, device="cuda")
+    p_rows, t_rows = p0, t0_
+    for _ in range(3):
+        trainer.step(p_rows, t_rows, idx0)
+    e0.record()
+    for _ in range(20):
+        trainer.step(p_rows, t_rows, idx0)
+    e1.record()
+    e1.synchronize()
     step_ms = e0.elapsed_time(e1) / 20
     rsi_fields_s = n / gen_s
     sur = surrogate.Surrogate(net, params[ho][:len(errs)], errs)
@@ -1052,6 +1064,7 @@ def run_surrogate_c5(args):
             "surrogate_fields_per_s_batch1024": nn_fields_s,
             "surrogate_fields_per_s_batch1024_eager": nn_fields_s_eager,
             "engine": args.engine, "train_step_ms_batch256": step_ms,
+            "train_step_ms_batch256_eager": step_ms_eager,
             # the f32 output (134 MB) dominates the bytes: HBM-write-bound;
             # the tensor-core rate is reported beside it
             "roofline": {"kernel": "output-layer GEMM 1024 x 32768 x 512, f32 out", "bound": "hbm",

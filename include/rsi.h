@@ -416,6 +416,12 @@ int rsi_nn_colsum(const void *m_bf16, int32_t rows, int32_t cols, float *out, vo
  * m, v and gradient g at step >= 1; writes a bf16 copy to w_bf16 if given. */
 int rsi_nn_adam(float *w, float *m, float *v, const float *g, int64_t n, float lr, float beta1,
                 float beta2, float eps, int32_t step, void *w_bf16, void *stream);
+/* The same Adam step with its schedule in device memory: hyper points to
+ * three floats (lr, 1 - beta1^t, 1 - beta2^t) that the kernel reads when it
+ * runs, so that a training step captured in a CUDA graph can be replayed
+ * while the caller updates the learning rate and step between replays.    */
+int rsi_nn_adam_dev(float *w, float *m, float *v, const float *g, int64_t n, const float *hyper,
+                    float beta1, float beta2, float eps, void *w_bf16, void *stream);
 /* bf16 copy of an f32 array.                                               */
 int rsi_nn_cast_bf16(const float *in, int64_t n, void *out_bf16, void *stream);
 /* out = scale * in * exp(sign i psi) per pixel of batch images (complex f32

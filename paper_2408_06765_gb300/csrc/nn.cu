@@ -596,11 +596,18 @@ __global__ void colsum_kernel(const bf16* __restrict__ m, int rows, int cols, fl
         out[c] = t;
     }
 }
+// hyper, when given, holds (lr, c1, c2) in device memory and overrides the
+// scalar arguments (a schedule that a replayed CUDA graph can follow)
 __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
-                            float c1, float c2, bf16* __restrict__ wh) {
+                            float c1, float c2, const float* __restrict__ hyper, bf16* __restrict__ wh) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (hyper) {
+        lr = hyper[0];
+        c1 = hyper[1];
+        c2 = hyper[2];
+    }
     float gi = g[i];
     float mi = b1 * m[i] + (1.0f - b1) * gi;
     float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -903,7 +910,16 @@ extern "C" int rsi_nn_adam(float* w, float* m, float* v, const float* g, int64_t
     if (!w || !m || !v || !g || n < 1 || step < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_adam: bad arguments");
     float c1 = float(1.0 - pow(double(beta1), step)), c2 = float(1.0 - pow(double(beta2), step));
     adam_kernel<<<unsigned((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        w, m, v, g, n, lr, beta1, beta2, eps, c1, c2, static_cast<bf16*>(w_bf16));
+        w, m, v, g, n, lr, beta1, beta2, eps, c1, c2, nullptr, static_cast<bf16*>(w_bf16));
+    RSI_CHECK_LAUNCH("adam_kernel");
+    return RSI_OK;
+}
+
+extern "C" int rsi_nn_adam_dev(float* w, float* m, float* v, const float* g, int64_t n, const float* hyper,
+                               float beta1, float beta2, float eps, void* w_bf16, void* stream) {
+    if (!w || !m || !v || !g || !hyper || n < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_adam_dev: bad arguments");
+    adam_kernel<<<unsigned((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        w, m, v, g, n, 0.0f, beta1, beta2, eps, 1.0f, 1.0f, hyper, static_cast<bf16*>(w_bf16));
     RSI_CHECK_LAUNCH("adam_kernel");
     return RSI_OK;
 }

@@ -47,7 +47,7 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_propagate_stage_multi", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
-           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_cast_bf16", "rsi_nn_carrier",
+           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_adam_dev", "rsi_nn_cast_bf16", "rsi_nn_carrier",
            "rsi_selftest_wait_timeout"]
 NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
 NN_ENGINE = {"mma_sync": 0, "tcgen05": 1}
@@ -156,6 +156,7 @@ def load(path: str | None = None):
         L.rsi_nn_loss.argtypes = [vp, vp, i64, f32, vp, vp, i32, vp, vp]
         L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
         L.rsi_nn_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
+        L.rsi_nn_adam_dev.argtypes = [vp, vp, vp, vp, i64, vp, f32, f32, f32, vp, vp]
         L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
         L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, ctypes.c_float, vp, vp, vp]
         L.rsi_selftest_wait_timeout.argtypes = [i64, vp]
@@ -708,6 +709,13 @@ def nn_adam(w, m, v, g, lr, step, w_bf16=None, beta1=0.9, beta2=0.999, eps=1e-8,
     _check(load().rsi_nn_adam(_ptr(w), _ptr(m), _ptr(v), _ptr(g), w.numel(), float(lr), float(beta1),
                               float(beta2), float(eps), int(step), _ptr(w_bf16), _stream(stream)),
            "rsi_nn_adam")
+
+
+def nn_adam_dev(w, m, v, g, hyper, w_bf16=None, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """Adam with (lr, 1 - beta1^t, 1 - beta2^t) read from the device tensor
+    `hyper` (f32 [3]) when the kernel runs."""
+    _check(load().rsi_nn_adam_dev(_ptr(w), _ptr(m), _ptr(v), _ptr(g), w.numel(), _ptr(hyper), float(beta1),
+                                  float(beta2), float(eps), _ptr(w_bf16), _stream(stream)), "rsi_nn_adam_dev")
 
 
 def nn_cast_bf16(x, out, stream=None):

@@ -228,6 +228,58 @@ def rel_errors(pred, ref):
     return (torch.linalg.vector_norm(d, dim=1) / torch.linalg.vector_norm(r, dim=1)).float()
 
 
+class GraphedTrainer:
+    """Training steps (forward, loss and its gradient, backward, Adam on every
+    layer) of `net` replayed from one CUDA graph.  The graph reads the batch
+    from fixed device buffers and Adam's (lr, 1 - beta1^t, 1 - beta2^t) from a
+    device tensor (rsi_nn_adam_dev), which each step refreshes from a
+    schedule held on the device, so nothing in a step waits for the host.
+    The net must have taken one eager step (train_step) first: that step runs
+    every kernel's one-time set-up, which a capture cannot hold."""
+
+    BETA1, BETA2 = 0.9, 0.999
+
+    def __init__(self, net: MLP, lrs):
+        if net.step_count < 1:
+            raise ValueError("GraphedTrainer needs one eager training step first")
+        self.net = net
+        dev, B = net.device, net.B_alloc
+        self.p = torch.zeros(B, 5, dtype=torch.float32, device=dev)
+        self.t = torch.zeros(B, net.y.shape[1], dtype=torch.float32, device=dev)
+        self.hyper = torch.zeros(3, dtype=torch.float32, device=dev)
+        # schedule row for step t (counted from the net's next step): lr and
+        # the bias corrections, formed as rsi_nn_adam forms them (FP64 pow of
+        # the FP32 betas, rounded to FP32)
+        b1, b2 = float(np.float32(self.BETA1)), float(np.float32(self.BETA2))
+        t0 = net.step_count + 1
+        rows = [(lr, 1.0 - b1 ** (t0 + i), 1.0 - b2 ** (t0 + i)) for i, lr in enumerate(lrs)]
+        self.sched = torch.tensor(np.asarray(rows, np.float32), device=dev)
+        self.i = 0
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            net.forward(self.p)
+            net.loss(self.t)
+            net.backward()
+            for i in range(len(net.W)):
+                rsi.nn_adam_dev(net.W[i], net.mW[i], net.vW[i], net.gW[i], self.hyper, net.W16[i],
+                                self.BETA1, self.BETA2)
+                rsi.nn_adam_dev(net.b[i], net.mb[i], net.vb[i], net.gb[i], self.hyper, None,
+                                self.BETA1, self.BETA2)
+
+    def step(self, p_all, t_all, idx) -> torch.Tensor:
+        """One step on rows idx (a device index tensor) of the training set;
+        returns the device loss buffer."""
+        if self.i >= len(self.sched):
+            raise RuntimeError("GraphedTrainer: the learning-rate schedule is exhausted")
+        torch.index_select(p_all, 0, idx, out=self.p)
+        torch.index_select(t_all, 0, idx, out=self.t)
+        self.hyper.copy_(self.sched[self.i])
+        self.graph.replay()
+        self.i += 1
+        self.net.step_count += 1
+        return self.net.loss_buf
+
+
 class GraphedInference:
     """The surrogate's inference at a fixed batch (the network's B_alloc):
     Fourier features, hidden layers, output layer and the carrier pass with
@@ -316,21 +368,28 @@ class Surrogate:
         return img, est, fall
 
 
-def train(net: MLP, params, env, epochs: int, lr: float = 1e-3, seed: int = 0, log=None):
-    """Adam on shuffled mini-batches of (params, scaled envelopes)."""
+def train(net: MLP, params, env, epochs: int, lr: float = 1e-3, seed: int = 0, log=None, graph: bool = True):
+    """Adam on shuffled mini-batches of (params, scaled envelopes), cosine
+    learning-rate decay.  With graph=True every step after the first is a
+    replay of one CUDA graph (GraphedTrainer); the steps compute the same."""
     n = params.shape[0]
     B = net.B_alloc
     rng = np.random.default_rng(seed)
     p_all = torch.tensor(params, dtype=torch.float32, device=net.device)
     steps = (n // B) * epochs
+    lrs = [lr * 0.5 * (1.0 + math.cos(math.pi * s / max(1, steps))) for s in range(steps)]
     total = 0
+    trainer = None
     losses = []
     for ep in range(epochs):
         order = torch.tensor(rng.permutation(n)[: (n // B) * B], device=net.device).view(-1, B)
         for idx in order:
-            frac = total / max(1, steps)
-            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * frac))
-            loss = net.train_step(p_all[idx], env[idx], lr_t)
+            if graph and total > 0:
+                if trainer is None:
+                    trainer = GraphedTrainer(net, lrs[total:])
+                loss = trainer.step(p_all, env, idx)
+            else:
+                loss = net.train_step(p_all[idx], env[idx], lrs[total])
             total += 1
         losses.append(float(loss.item()))
         if log:
