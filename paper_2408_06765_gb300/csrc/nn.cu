@@ -783,9 +783,17 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, int lay
 template <int EPI>
 int gemm_tc_launch(const bf16* A, const bf16* B, int M, int N, int K, int layout, const float* bias,
                    const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
-    if (N % 256 == 0)
+    // The widest output tile that still gives every SM a tile; else the
+    // narrowest.  Small GEMMs (the hidden layers at batch 256) are latency-
+    // bound: narrower tiles spread them over more SMs and shorten each CTA's
+    // main loop and epilogue.
+    const int64_t rows = M / TC_BM, sms = sm_count();
+    const int kt = K / TC_BK, units = (kt + (kt + splits - 1) / splits - 1) / ((kt + splits - 1) / splits);
+    if (N % 256 == 0 && rows * (N / 256) * units >= sms)
         return gemm_tc_launch_bn<EPI, 256>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
-    return gemm_tc_launch_bn<EPI, 128>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
+    if (N % 128 == 0 && rows * (N / 128) * units >= sms)
+        return gemm_tc_launch_bn<EPI, 128>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
+    return gemm_tc_launch_bn<EPI, 64>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
 }
 
 template <int EPI>

@@ -60,10 +60,14 @@ def test_gemm_epilogues_match_fp32_reference(M, N, K):
     assert rel(h.float(), ref * s * (1 + aux * (1 - s))) < 6e-3
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 512, 256), (384, 256, 128), (256, 384, 1024)])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 512, 256), (384, 256, 128), (256, 384, 1024),
+                                   (1024, 8192, 128), (1024, 3072, 64)])
 def test_gemm_tcgen05_matches_fp32_reference(M, N, K):
     """The tcgen05 engine (accumulators in tensor memory) against the same
-    FP32 reference, every epilogue, with and without split K."""
+    FP32 reference, every epilogue, with and without split K.  The engine
+    takes the widest output tile that still gives every SM a tile: the small
+    shapes run 64-wide tiles, 1024 x 3072 128-wide and 1024 x 8192 256-wide
+    (152 SMs)."""
     g = torch.Generator(device="cuda").manual_seed(7 * M + N + K)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
