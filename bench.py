@@ -41,10 +41,12 @@ OPS = {
     # pair; piston 14 packed per two pairs plus the same scaling
     "rsi": {"fp32": 12, "mufu": 3, "lds": 1.0},
     "piston": {"fp32": 8, "mufu": 3, "lds": 1.0},
-    # ray-tracing pair (Sec. 2.2): linear prediction of the crossing from the
-    # tile's reference ray, then 2 safeguarded Newton steps (~29 FP32 and 3
-    # MUFU each); ~88 FP32 and 11 MUFU around them
-    "raytrace": {"fp32": 146, "mufu": 17, "lds": 2.0},
+    # ray-tracing pair (Sec. 2.2), two transducer points per f32x2
+    # instruction: linear prediction of the crossing from the tile's reference
+    # ray, 2 Newton steps (16 packed FP32 and 3 MUFU per point each), ~100
+    # packed FP32 per two pairs in all plus 9 scalar (the products of the fast
+    # divisions, the sincos scaling), ~14 compares, selects and clamps, 17 MUFU
+    "raytrace": {"fp32": 59, "alu": 14, "mufu": 17, "lds": 2.0},
 }
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "rsi_pair_terms_per_s"
@@ -234,7 +236,7 @@ def alu_roofline(kind: str, n_sm: int, clock_hz: float, ops: dict | None = None)
     """Peak pairs/s of a stage kernel at `clock_hz`: the tighter of the issue
     limit (one warp instruction per scheduler per clock) and the MUFU limit."""
     o = ops or OPS[kind]
-    issue = (o["fp32"] + o["mufu"] + o["lds"]) / (ISSUE_LANES_PER_SM * n_sm * clock_hz)
+    issue = (o["fp32"] + o.get("alu", 0) + o["mufu"] + o["lds"]) / (ISSUE_LANES_PER_SM * n_sm * clock_hz)
     mufu = o["mufu"] / (MUFU_LANES_PER_SM * n_sm * clock_hz)
     return 1.0 / max(issue, mufu), ("mufu" if mufu >= issue else "issue")
 

@@ -177,6 +177,28 @@ __device__ __forceinline__ RayRef ray_reference(float qxh, float qxl, float qyh,
     return R;
 }
 
+// safeguarded steps for the crossing offset dt of one pair whose plain Newton
+// steps still move it by `step`: Newton inside a bracket of the monotone
+// residual, bisection otherwise, until the step falls below kCrossTol
+__device__ __forceinline__ float cross_safeguarded(const RayRef& R, const RtArgs& a, float h1q, float h2q, float s1h,
+                                                float bfix, float lo0, float hi0, float dt, float step) {
+    float lo = lo0, hi = hi0;
+#pragma unroll 1
+    for (int it = 0; it < kCrossExtra && fabsf(step) > kCrossTol; ++it) {
+        float G, dG;
+        snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG);
+        if (G > 0.0f)
+            hi = dt;
+        else
+            lo = dt;
+        const float dn = dt - __fdividef(G, dG);
+        const float nt = (dn >= lo && dn <= hi) ? dn : 0.5f * (lo + hi);
+        step = nt - dt;
+        dt = nt;
+    }
+    return dt;
+}
+
 // one transducer point (offset p, amplitude A) onto one reference ray; NW
 // Newton steps for the crossing (0: a.newton at run time)
 template <int NW>
@@ -221,24 +243,8 @@ __device__ __forceinline__ void ray_pair(const RayRef& R, const float4& rec, flo
         dt = nt;
     }
     // then, for the rays still moving by more than kCrossTol (those that graze
-    // the interface near the target converge more slowly), safeguarded steps:
-    // Newton inside a bracket of the monotone residual, bisection otherwise
-    if (fabsf(step) > kCrossTol) {
-        float lo = lo0, hi = hi0;
-#pragma unroll 1
-        for (int it = 0; it < kCrossExtra && fabsf(step) > kCrossTol; ++it) {
-            float G, dG;
-            snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG);
-            if (G > 0.0f)
-                hi = dt;
-            else
-                lo = dt;
-            const float dn = dt - __fdividef(G, dG);
-            const float nt = (dn >= lo && dn <= hi) ? dn : 0.5f * (lo + hi);
-            step = nt - dt;
-            dt = nt;
-        }
-    }
+    // the interface near the target converge more slowly), safeguarded steps
+    if (fabsf(step) > kCrossTol) dt = cross_safeguarded(R, a, h1q, h2q, s1h, bfix, lo0, hi0, dt, step);
     // e1 = (X - P) - (X_c - c) = (dt u + t_c (u - u_c), -p_z); e2 = -(p_h + e1_h, 0)
     const float e1x = fmaf(dt, ux, R.tc * wx), e1y = fmaf(dt, uy, R.tc * wy), e1z = -pz;
     const float e2x = -(px + e1x), e2y = -(py + e1y);
@@ -262,8 +268,106 @@ __device__ __forceinline__ void ray_pair(const RayRef& R, const float4& rec, flo
     acc_i = fmaf(amp, s, acc_i);
 }
 
+#ifndef RSI_RT_PACKED
+#define RSI_RT_PACKED 1  // two transducer points per f32x2 instruction
+#endif
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __fadd2_rn(x, neg2(y)); }
+
+// ray_pair for two transducer points at once: the same operations in the
+// same order, the additions, products and FMAs two at a time (f32x2), the
+// reciprocal square roots, divisions, clamps and sincos per point, and the
+// safeguarded steps only for a point whose ray has not converged
+template <int NW>
+__device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, float A0, const float4& r1, float A1,
+                                          const RtArgs& a, float k1, float k2, float2& acc_r, float2& acc_i) {
+    const float2 px = make_float2(r0.x, r1.x), py = make_float2(r0.y, r1.y), pz = make_float2(r0.z, r1.z);
+    const float2 vx = sub2(f2(R.dx), px), vy = sub2(f2(R.dy), py);
+    const float2 v2 = __ffma2_rn(vx, vx, __fmul2_rn(vy, vy));
+    const bool okx = v2.x > 1e-24f, oky = v2.y > 1e-24f;
+    const float2 iv = make_float2(okx ? rsqrt_ap(v2.x) : 0.0f, oky ? rsqrt_ap(v2.y) : 0.0f);
+    const float2 rho = __fmul2_rn(v2, iv);
+    float2 ux = __fmul2_rn(vx, iv), uy = __fmul2_rn(vy, iv);
+    if (!okx) ux.x = R.ux, uy.x = R.uy;
+    if (!oky) ux.y = R.ux, uy.y = R.uy;
+    const float2 dpp = __ffma2_rn(f2(2.0f * R.dx), px,
+                                  __ffma2_rn(f2(2.0f * R.dy), py, neg2(__ffma2_rn(px, px, __fmul2_rn(py, py)))));
+    const float2 dd = __fadd2_rn(__fadd2_rn(f2(R.rho), rho), f2(1e-30f));
+    const float2 drho = make_float2(__fdividef(dpp.x, dd.x), __fdividef(dpp.y, dd.y));
+    const float2 sw = __fmul2_rn(f2(R.irho), iv);
+    float2 wx = __fmul2_rn(__ffma2_rn(f2(R.dx), drho, __fmul2_rn(neg2(px), f2(R.rho))), sw);
+    float2 wy = __fmul2_rn(__ffma2_rn(f2(R.dy), drho, __fmul2_rn(neg2(py), f2(R.rho))), sw);
+    if (!(R.irho > 0.0f && iv.x > 0.0f)) wx.x = ux.x - R.ux, wy.x = uy.x - R.uy;
+    if (!(R.irho > 0.0f && iv.y > 0.0f)) wx.y = ux.y - R.ux, wy.y = uy.y - R.uy;
+    const float2 h1 = sub2(f2(R.H1), pz);
+    const float h2 = R.H2;
+    const float2 h1q = __fmul2_rn(h1, h1);
+    const float h2q = h2 * h2;
+    const float2 s1h = __fmul2_rn(f2(a.s1), h1q);
+    const float2 bfix = sub2(f2(R.bc), drho);
+    const float lo0 = -R.tc;
+    float2 dt = neg2(__ffma2_rn(f2(R.a_r), drho, __fmul2_rn(f2(R.a_h), pz)));
+    dt.x = fminf(fmaxf(dt.x, lo0), bfix.x);
+    dt.y = fminf(fmaxf(dt.y, lo0), bfix.y);
+    float2 step = f2(INFINITY);
+    const int nw = NW ? NW : a.newton;
+#pragma unroll
+    for (int it = 0; it < (NW ? NW : 16); ++it) {
+        if (!NW && it >= nw) break;
+        const float2 t = __fadd2_rn(f2(R.tc), dt), b = sub2(bfix, dt);
+        const float2 q1 = __ffma2_rn(t, t, h1q), q2 = __ffma2_rn(b, b, f2(h2q));
+        const float2 e1 = make_float2(rsqrt_ap(q1.x), rsqrt_ap(q1.y));
+        const float2 e2 = make_float2(rsqrt_ap(q2.x), rsqrt_ap(q2.y));
+        const float2 G = __ffma2_rn(__fmul2_rn(f2(a.s1), t), e1, neg2(__fmul2_rn(__fmul2_rn(f2(a.s2), b), e2)));
+        const float2 dG = __ffma2_rn(s1h, __fmul2_rn(__fmul2_rn(e1, e1), e1),
+                                     __fmul2_rn(f2(R.s2h22), __fmul2_rn(__fmul2_rn(e2, e2), e2)));
+        const float2 dn = sub2(dt, make_float2(__fdividef(G.x, dG.x), __fdividef(G.y, dG.y)));
+        const float2 nt = make_float2(fminf(fmaxf(dn.x, lo0), bfix.x), fminf(fmaxf(dn.y, lo0), bfix.y));
+        step = sub2(nt, dt);
+        dt = nt;
+    }
+    if (fabsf(step.x) > kCrossTol) dt.x = cross_safeguarded(R, a, h1q.x, h2q, s1h.x, bfix.x, lo0, bfix.x, dt.x, step.x);
+    if (fabsf(step.y) > kCrossTol) dt.y = cross_safeguarded(R, a, h1q.y, h2q, s1h.y, bfix.y, lo0, bfix.y, dt.y, step.y);
+    const float2 e1x = __ffma2_rn(dt, ux, __fmul2_rn(f2(R.tc), wx));
+    const float2 e1y = __ffma2_rn(dt, uy, __fmul2_rn(f2(R.tc), wy));
+    const float2 e1z = neg2(pz);
+    const float2 e2x = neg2(__fadd2_rn(px, e1x)), e2y = neg2(__fadd2_rn(py, e1y));
+    const float2 t1 = __ffma2_rn(f2(2.0f * R.tc), __ffma2_rn(f2(R.ux), e1x, __fmul2_rn(f2(R.uy), e1y)),
+                                 __ffma2_rn(f2(2.0f * R.H1), e1z,
+                                            __ffma2_rn(e1x, e1x, __ffma2_rn(e1y, e1y, __fmul2_rn(e1z, e1z)))));
+    const float2 t2 = __ffma2_rn(f2(2.0f * R.bc), __ffma2_rn(f2(R.ux), e2x, __fmul2_rn(f2(R.uy), e2y)),
+                                 __ffma2_rn(e2x, e2x, __fmul2_rn(e2y, e2y)));
+    const float2 q1 = __ffma2_rn(f2(R.D1), f2(R.D1), t1), q2 = __ffma2_rn(f2(R.D2), f2(R.D2), t2);
+    const float2 ir1 = make_float2(rsqrt_ap(q1.x), rsqrt_ap(q1.y)), ir2 = make_float2(rsqrt_ap(q2.x), rsqrt_ap(q2.y));
+    const float2 D1 = __fmul2_rn(q1, ir1), D2 = __fmul2_rn(q2, ir2);
+    const float2 s1d = __fadd2_rn(f2(R.D1), D1), s2d = __fadd2_rn(f2(R.D2), D2);
+    const float2 dD1 = make_float2(__fdividef(t1.x, s1d.x), __fdividef(t1.y, s1d.y));
+    const float2 dD2 = make_float2(__fdividef(t2.x, s2d.x), __fdividef(t2.y, s2d.y));
+    const float2 u = __ffma2_rn(f2(k1), dD1, __ffma2_rn(f2(k2), dD2, f2(R.tau)));
+    const float2 cos1 = __fmul2_rn(h1, ir1), cos2 = __fmul2_rn(f2(h2), ir2);
+    const float2 tn = __fmul2_rn(f2(a.Tn), cos1), td = __ffma2_rn(f2(a.Td1), cos1, __fmul2_rn(f2(a.Td2), cos2));
+    const float2 T = make_float2(__fdividef(tn.x, td.x), __fdividef(tn.y, td.y));
+    const float2 cc = __fmul2_rn(__fmul2_rn(__fmul2_rn(f2(a.c21), cos1), cos1), f2(R.ih22));
+    const float2 den = __fmul2_rn(__ffma2_rn(cc, __fmul2_rn(D2, q2), D1), __ffma2_rn(f2(a.c21), D2, D1));
+    const float2 amp = __fmul2_rn(__fmul2_rn(make_float2(A0, A1), T), make_float2(rsqrt_ap(den.x), rsqrt_ap(den.y)));
+    float2 sn, cs;
+    __sincosf(u.x, &sn.x, &cs.x);
+    __sincosf(u.y, &sn.y, &cs.y);
+    acc_r = __ffma2_rn(amp, cs, acc_r);
+    acc_i = __ffma2_rn(amp, sn, acc_i);
+}
+
+// resident CTAs per SM asked of the compiler: 4 (64 registers) measured best
+// for the packed form on the f2 workload (171.6 Gpair/s; 3 CTAs 160.6, no
+// bound 143.7), although ptxas then keeps 20 bytes per thread in local memory
+#ifndef RSI_RT_MIN_BLOCKS
+#define RSI_RT_MIN_BLOCKS 4
+#endif
+
 template <int TPT, int NW>
-__global__ void __launch_bounds__(kRtThreads) raytrace_kernel(RtArgs a) {
+__global__ void __launch_bounds__(kRtThreads, RSI_RT_MIN_BLOCKS) raytrace_kernel(RtArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RSI_PIPE_STAGES * a.tile_bytes);
     const int tid = threadIdx.x;
@@ -312,6 +416,25 @@ __global__ void __launch_bounds__(kRtThreads) raytrace_kernel(RtArgs a) {
                                    __ldg(a.tgt.zh + j), __ldg(a.tgt.zl + j), hdr, a);
             ar[q] = ai[q] = 0.0f;
         }
+#if RSI_RT_PACKED
+        {  // tiles hold an even number of points (32 .. 256)
+            float2 pr[TPT], pi[TPT];
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) pr[q] = pi[q] = f2(0.0f);
+#pragma unroll 1
+            for (int i = 0; i < a.S; i += 2) {
+                const float4 r0 = rec[2 * i], r1 = rec[2 * i + 2];
+                const float A0 = rec[2 * i + 1].x, A1 = rec[2 * i + 3].x;
+#pragma unroll
+                for (int q = 0; q < TPT; ++q) ray_pair2<NW>(ref[q], r0, A0, r1, A1, a, k1, k2, pr[q], pi[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < TPT; ++q) {
+                ar[q] = pr[q].x + pr[q].y;
+                ai[q] = pi[q].x + pi[q].y;
+            }
+        }
+#else
 #pragma unroll 1
         for (int i = 0; i < a.S; ++i) {
             const float4 ra = rec[2 * i];
@@ -319,6 +442,7 @@ __global__ void __launch_bounds__(kRtThreads) raytrace_kernel(RtArgs a) {
 #pragma unroll
             for (int q = 0; q < TPT; ++q) ray_pair<NW>(ref[q], ra, A, a, k1, k2, ar[q], ai[q]);
         }
+#endif
 #pragma unroll
         for (int q = 0; q < TPT; ++q) {
             float s, e;
