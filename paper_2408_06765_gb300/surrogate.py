@@ -1,7 +1,7 @@
 """Learned surrogate of the RSI chain (not in the paper): a Fourier-feature MLP
 that maps (x-offset, tilt, water path, frequency, image depth) to the
 128 x 128 field image of one water -> steel chain, trained on images the GPU
-RSI path computes, with the RSI path as its fallback and its judge.
+RSI path computes, with the RSI path as its fallback and the measure of its error.
 
 Every numerical step runs in librsi.so (rsi_nn_* kernels: BF16 tensor-core
 GEMMs with FP32 accumulation and fused bias/SiLU epilogues, FP32 master
