@@ -432,6 +432,18 @@ int rsi_nn_cast_bf16(const float *in, int64_t n, void *out_bf16, void *stream);
  * pixels and a non-finite scale return RSI_E_INVAL.                        */
 int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window, int32_t sign,
                    float scale, const float *in, float *out, void *stream);
+/* The output layer and the carrier in one kernel (tcgen05 engine):
+ * out = scale * exp(sign i psi) * (A B^T + bias), row b of the M x N result
+ * being image b of interleaved complex pixels over `window` (N = 2 nx nz)
+ * and psi its carrier as in rsi_nn_carrier (carrier[b] = (kx, kz, phi0, .)).
+ * A [M x K] and B [N x K] bf16, K-major; M % 128 == 0, N % 128 == 0,
+ * K % 64 == 0; A, B, out and bias 16-byte aligned.  Within a block of 16
+ * pixels the carrier advances by rotation from one exact phase, which adds
+ * up to about 2e-6 relative to rsi_nn_carrier's per-pixel phase.  Fusing
+ * the two saves writing the layer's output and reading it back.            */
+int rsi_nn_gemm_carrier(const void *a_bf16, const void *b_bf16, int32_t M, int32_t N, int32_t K,
+                        const float *bias, const double *carrier, const rsi_grid *window, int32_t sign,
+                        float scale, float *out, void *stream);
 
 /* ---- measurement hooks (no counterpart in the paper) --------------------- */
 /* Number of kernels this library has enqueued in this process.             */

@@ -251,6 +251,51 @@ constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK * 2;
 // stored at chunk j ^ (r & 7) (conflict-free row writes and column reads)
 constexpr uint32_t TC_EPI_BYTES = TC_EPI_WARPS * 32 * 32 * 4;
 
+// Output-layer epilogue with the carrier (EPI 3): each output row is one
+// image of interleaved complex pixels on a window of nx columns; the epilogue
+// multiplies pixel (ix, iz) of row b by scale exp(sign i psi_b(ix, iz)),
+// psi_b / 2 pi = a_b + ix u_b + iz w_b (turns), with a, u, w from the
+// row's coefficients (kx, kz, phi0) in FP64, as the carrier pass forms them.
+struct CarrierArgs {
+    const double* coef;  // [M][4] (kx, kz, phi0, unused)
+    int nx, sign;
+    float scale;
+    double x0, dx, z0, dz;
+};
+struct CarrierRow {
+    float ah, al, uh, ul, wh, wl;  // turns, split into float pairs
+    float rc, rs;                  // exp(2 pi i u): one pixel step in x
+};
+__device__ __forceinline__ float frac_mul_(float i, float h, float l) {
+    const float p = i * h;
+    const float e = fmaf(i, h, -p);
+    return ((p - rintf(p)) + e) + i * l;
+}
+__device__ __forceinline__ CarrierRow carrier_row(const CarrierArgs& ca, int row) {
+    const double* cb = ca.coef + 4 * size_t(row);
+    const double inv2pi = 0.15915494309189535;  // 1 / (2 pi)
+    double ad = (cb[2] + cb[0] * (ca.x0 + 0.5 * ca.dx) + cb[1] * (ca.z0 + 0.5 * ca.dz)) * inv2pi;
+    ad -= rint(ad);
+    double ud = cb[0] * ca.dx * inv2pi;
+    const double wd = cb[1] * ca.dz * inv2pi;
+    CarrierRow r;
+    r.ah = float(ad);
+    r.al = float(ad - double(r.ah));
+    r.uh = float(ud);
+    r.ul = float(ud - double(r.uh));
+    r.wh = float(wd);
+    r.wl = float(wd - double(r.wh));
+    ud -= rint(ud);
+    sincospif(2.0f * float(ud), &r.rs, &r.rc);  // accurate: the block's rotations build on it
+    return r;
+}
+// exp(i 2 pi (a + ix u + iz w)) with the phase reduced as in the carrier pass
+__device__ __forceinline__ void carrier_phase(const CarrierRow& r, int ix, int iz, float& c, float& s) {
+    float t = (r.ah + frac_mul_(float(ix), r.uh, r.ul)) + frac_mul_(float(iz), r.wh, r.wl);
+    t = (t - rintf(t)) + r.al;
+    __sincosf(6.283185307179586f * t, &s, &c);
+}
+
 template <int TBN>
 struct TcCfg {
     static constexpr uint32_t B_BYTES = TBN * TC_BK * 2;
@@ -283,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmH, int M, int N,
                    int K, int layout, const float* __restrict__ bias, const float* __restrict__ aux, int kts,
-                   int splits, int* status) {
+                   int splits, CarrierArgs car, int* status) {
     // layout bit 0: A is stored [K x M] (MN-major), bit 1: B is stored [K x N]
     const bool a_mn = layout & 1, b_mn = layout & 2;
     // outputs leave by TMA stores: f32 (F32, BIAS_SILU's z, split-K partial
@@ -320,7 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         rsi_umma::prefetch_tmap(&tmA);
         rsi_umma::prefetch_tmap(&tmB);
         if (EPI != 2 || splits > 1) rsi_umma::prefetch_tmap(&tmC);
-        if (EPI != 0 && splits == 1) rsi_umma::prefetch_tmap(&tmH);
+        if ((EPI == 1 || EPI == 2) && splits == 1) rsi_umma::prefetch_tmap(&tmH);  // bf16 outputs only
     }
     rsi_umma::fence_before_sync();
     __syncthreads();
@@ -416,6 +461,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
             if (add_bias && 4 * lane < TBN / 2)
                 bq = __ldg(reinterpret_cast<const float4*>(bias + T.n0 + h * (TBN / 2)) + lane);
+            CarrierRow crow;  // this lane's image (row) constants, formed while the MMAs run
+            if (EPI == 3) crow = carrier_row(car, T.m0 + q * 32 + lane);
             const bool ok = mbar_wait_bounded(smem_u32(&acc_full[acc]), uint32_t(tc / 2) & 1u);
             if (!__all_sync(0xffffffffu, ok)) {
                 abort_flag = 1;
@@ -455,6 +502,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         v[4 * i + 3] += __shfl_sync(0xffffffffu, bq.w, src + i);
                     }
                 }
+                if (EPI == 3) {  // 16 complex pixels of this row's image: one exact phase, then rotations
+                    int p = col0 >> 1;
+                    int iz = p / car.nx, ix = p - iz * car.nx;  // the same for every lane (same columns)
+                    float c, sn;
+                    carrier_phase(crow, ix, iz, c, sn);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float sv = car.sign > 0 ? sn * car.scale : -sn * car.scale, cv = c * car.scale;
+                        const float re = v[2 * k], im = v[2 * k + 1];
+                        v[2 * k] = fmaf(re, cv, -im * sv);
+                        v[2 * k + 1] = fmaf(re, sv, im * cv);
+                        if (k < 15) {
+                            if (++ix == car.nx) {  // next image row: restart from the exact phase
+                                ix = 0;
+                                ++iz;
+                                carrier_phase(crow, ix, iz, c, sn);
+                            } else {
+                                const float cn = fmaf(c, crow.rc, -sn * crow.rs);
+                                sn = fmaf(sn, crow.rc, c * crow.rs);
+                                c = cn;
+                            }
+                        }
+                    }
+                }
                 if (EPI != 2 || splits > 1) {  // f32 block: output, z, or partial sums of split T.z
                     if (lane == 0) rsi_umma::bulk_wait_read0();  // the previous block has left buf
                     __syncwarp();
@@ -469,7 +540,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         rsi_umma::bulk_commit();
                     }
                 }
-                if (EPI != 0 && splits == 1) {  // bf16 block (dense 64-byte rows): silu(z) or C * silu'(aux)
+                if ((EPI == 1 || EPI == 2) && splits == 1) {  // bf16 block (dense 64-byte rows): silu(z) or C * silu'(aux)
                     uint32_t hw[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -734,7 +805,8 @@ int make_tmap(CUtensorMap* tm, CUtensorMapDataType type, size_t esize, const voi
 
 template <int EPI, int TBN>
 int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, int layout, const float* bias,
-                      const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
+                      const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s,
+                      const CarrierArgs& car = CarrierArgs{}) {
     using C = TcCfg<TBN>;
     static bool attr = false;
     if (!attr) {
@@ -762,14 +834,14 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, int lay
                        int64_t(splits) * M, N, 32, 32);
         if (rc) return rc;
     }
-    if (EPI != 0 && splits == 1) {  // bf16 blocks of 32 x 32, dense 64-byte rows in shared memory
+    if ((EPI == 1 || EPI == 2) && splits == 1) {  // bf16 blocks of 32 x 32, dense 64-byte rows in shared memory
         rc = make_tmap(&th, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, outh, M, N, 32, 32, CU_TENSOR_MAP_SWIZZLE_NONE);
         if (rc) return rc;
     }
     const int tiles = (M / TC_BM) * (N / TBN) * splits;
     const int grid = std::min(tiles, sm_count());
     gemm_tc_kernel<EPI, TBN><<<grid, TC_THREADS, C::SMEM, s>>>(ta, tb, tc, th, M, N, K, layout, bias, aux, kts,
-                                                               splits, status);
+                                                               splits, car, status);
     RSI_CHECK_LAUNCH("gemm_tc_kernel");
     if (splits > 1) {
         int64_t pairs = int64_t(M) * N / 2;
@@ -782,7 +854,8 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, int lay
 
 template <int EPI>
 int gemm_tc_launch(const bf16* A, const bf16* B, int M, int N, int K, int layout, const float* bias,
-                   const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s) {
+                   const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s,
+                   const CarrierArgs& car = CarrierArgs{}) {
     // The widest output tile that still gives every SM a tile; else the
     // narrowest.  Small GEMMs (the hidden layers at batch 256) are latency-
     // bound: narrower tiles spread them over more SMs and shorten each CTA's
@@ -790,10 +863,10 @@ int gemm_tc_launch(const bf16* A, const bf16* B, int M, int N, int K, int layout
     const int64_t rows = M / TC_BM, sms = sm_count();
     const int kt = K / TC_BK, units = (kt + (kt + splits - 1) / splits - 1) / ((kt + splits - 1) / splits);
     if (N % 256 == 0 && rows * (N / 256) * units >= sms)
-        return gemm_tc_launch_bn<EPI, 256>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
+        return gemm_tc_launch_bn<EPI, 256>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s, car);
     if (N % 128 == 0 && rows * (N / 128) * units >= sms)
-        return gemm_tc_launch_bn<EPI, 128>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
-    return gemm_tc_launch_bn<EPI, 64>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s);
+        return gemm_tc_launch_bn<EPI, 128>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s, car);
+    return gemm_tc_launch_bn<EPI, 64>(A, B, M, N, K, layout, bias, aux, outf, outh, splits, work, s, car);
 }
 
 template <int EPI>
@@ -880,6 +953,35 @@ extern "C" int rsi_nn_gemm(int32_t epilogue, int32_t engine, int32_t layout, con
         default:
             return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm: unknown epilogue %d", epilogue);
     }
+}
+
+extern "C" int rsi_nn_gemm_carrier(const void* A, const void* B, int32_t M, int32_t N, int32_t K, const float* bias,
+                                   const double* carrier, const rsi_grid* window, int32_t sign, float scale, float* out,
+                                   void* stream) {
+    if (!A || !B || !carrier || !window || !out || M < 1 || N < 1 || K < 1 || (sign != 1 && sign != -1) ||
+        !isfinite(scale))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: bad arguments");
+    if (M % TC_BM || N % 128 || K % TC_BK)
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: M, N must be multiples of 128 and K of 64 (got %d %d %d)",
+                        M, N, K);
+    if (window->nx < 1 || window->nz < 1 || int64_t(N) != 2 * int64_t(window->nx) * window->nz)
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: N must be 2 nx nz of the window (got %d)", N);
+    if (int64_t(window->nx) * window->nz > (int64_t(1) << 24))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: window exceeds 2^24 pixels");
+    if (misaligned(A, 16) || misaligned(B, 16) || misaligned(out, 16) || misaligned(bias, 16) ||
+        misaligned(carrier, 8))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: misaligned pointer");
+    CarrierArgs car;
+    car.coef = carrier;
+    car.nx = window->nx;
+    car.sign = sign;
+    car.scale = scale;
+    car.x0 = window->x0;
+    car.dx = (window->x1 - window->x0) / window->nx;
+    car.z0 = window->z0;
+    car.dz = (window->z1 - window->z0) / window->nz;
+    return gemm_tc_launch<3>(static_cast<const bf16*>(A), static_cast<const bf16*>(B), M, N, K, 0, bias, nullptr,
+                             out, nullptr, 1, nullptr, static_cast<cudaStream_t>(stream), car);
 }
 
 extern "C" int rsi_nn_transpose(const void* in_bf16, int32_t rows, int32_t cols, void* out_bf16, void* stream) {

@@ -47,7 +47,7 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_propagate_stage_multi", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
-           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_adam_dev", "rsi_nn_cast_bf16", "rsi_nn_carrier",
+           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_adam_dev", "rsi_nn_cast_bf16", "rsi_nn_carrier", "rsi_nn_gemm_carrier",
            "rsi_selftest_wait_timeout"]
 NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
 NN_ENGINE = {"mma_sync": 0, "tcgen05": 1}
@@ -157,6 +157,7 @@ def load(path: str | None = None):
         L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
         L.rsi_nn_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
         L.rsi_nn_adam_dev.argtypes = [vp, vp, vp, vp, i64, vp, f32, f32, f32, vp, vp]
+        L.rsi_nn_gemm_carrier.argtypes = [vp, vp, i32, i32, i32, vp, vp, ctypes.POINTER(Grid), i32, f32, vp, vp]
         L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
         L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, ctypes.c_float, vp, vp, vp]
         L.rsi_selftest_wait_timeout.argtypes = [i64, vp]
@@ -720,6 +721,16 @@ def nn_adam_dev(w, m, v, g, hyper, w_bf16=None, beta1=0.9, beta2=0.999, eps=1e-8
 
 def nn_cast_bf16(x, out, stream=None):
     _check(load().rsi_nn_cast_bf16(_ptr(x), x.numel(), _ptr(out), _stream(stream)), "rsi_nn_cast_bf16")
+    return out
+
+
+def nn_gemm_carrier(a, b, bias, carrier, window: dict, sign: int, scale: float, out, stream=None):
+    """out = scale * exp(sign i psi) * (a b^T + bias) row by row (tcgen05
+    engine): the output layer and the carrier pass in one kernel."""
+    G = grid_struct(window)
+    _check(load().rsi_nn_gemm_carrier(_ptr(a), _ptr(b), a.shape[0], b.shape[0], a.shape[1], _ptr(bias),
+                                      _ptr(carrier), ctypes.byref(G), int(sign), float(scale), _ptr(out),
+                                      _stream(stream)), "rsi_nn_gemm_carrier")
     return out
 
 

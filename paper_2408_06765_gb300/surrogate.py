@@ -105,13 +105,18 @@ class MLP:
         self.loss_buf = torch.empty(1, dtype=torch.float32, device=d)
 
     # -- forward / backward / update ------------------------------------------
-    def forward(self, p) -> torch.Tensor:
-        """p: f32 [B, 5] on the device (B = the allocated batch)."""
+    def hidden(self, p) -> torch.Tensor:
+        """Features and hidden layers: the last hidden activations (bf16)."""
         assert p.shape[0] == self.B_alloc
         rsi.nn_features(p, self.lo, self.hi, self.fmat, self.H[0])
         for l in range(self.depth):
             rsi.nn_gemm("bias_silu", self.H[l], self.W16[l], out_f32=self.Z[l], out_bf16=self.H[l + 1],
                         bias=self.b[l], engine=self.engine)
+        return self.H[self.depth]
+
+    def forward(self, p) -> torch.Tensor:
+        """p: f32 [B, 5] on the device (B = the allocated batch)."""
+        self.hidden(p)
         rsi.nn_gemm("f32", self.H[self.depth], self.W16[-1], out_f32=self.y, bias=self.b[-1], engine=self.engine)
         return self.y
 
@@ -287,7 +292,9 @@ class GraphedInference:
     batch.  Each call stages the parameters and carrier coefficients in
     pinned host buffers, copies them to fixed device buffers without
     blocking, and replays the graph: one launch instead of seven calls
-    through Python, so the batch runs at the kernels' speed.  The returned
+    through Python, so the batch runs at the kernels' speed.  With the
+    tcgen05 engine the output layer applies the carrier in its epilogue
+    (rsi_nn_gemm_carrier), so the layer's raw output never reaches memory.  The returned
     images (complex64 [B, 128, 128]) are a view of a buffer that the next
     call overwrites."""
 
@@ -313,8 +320,12 @@ class GraphedInference:
             self._body()
 
     def _body(self):
-        y = self.net.forward(self.p)
-        rsi.nn_carrier(self.car, WINDOW, +1, y, self.out, scale=self.scale)
+        net = self.net
+        if net.engine == "tcgen05":  # output layer and carrier in one kernel
+            rsi.nn_gemm_carrier(net.hidden(self.p), net.W16[-1], net.b[-1], self.car, WINDOW, +1, self.scale,
+                                self.out)
+        else:
+            rsi.nn_carrier(self.car, WINDOW, +1, net.forward(self.p), self.out, scale=self.scale)
 
     def __call__(self, params) -> torch.Tensor:
         params = np.asarray(params, np.float64)

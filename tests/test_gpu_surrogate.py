@@ -200,7 +200,10 @@ def test_carrier_round_trip_and_definition():
 
 def test_graphed_inference_matches_eager():
     """The CUDA-graph inference path gives the eager path's images, on two
-    batches in a row (its pinned staging buffers are reused)."""
+    batches in a row (its pinned staging buffers are reused).  Its output
+    layer applies the carrier in the GEMM epilogue, advancing the phase by
+    rotation within blocks of 16 pixels (about 1e-6 from the per-pixel
+    phase of the separate carrier pass)."""
     net = surrogate.MLP(batch=256, seed=5)
     g = surrogate.GraphedInference(net, scale=0.7)
     rng = np.random.default_rng(9)
@@ -209,7 +212,7 @@ def test_graphed_inference_matches_eager():
         got = g(params).clone()
         pq = torch.tensor(params, dtype=torch.float32, device="cuda")
         want = surrogate.modulate(net.predict(pq), params, scale=0.7)
-        assert rel(torch.view_as_real(got), torch.view_as_real(want)) < 1e-6
+        assert rel(torch.view_as_real(got), torch.view_as_real(want)) < 1e-5
     rsi.sync_status()
 
 
@@ -228,6 +231,40 @@ def test_graphed_training_matches_eager(engine):
     for a, b in zip(nets[0].W + nets[0].b, nets[1].W + nets[1].b):
         assert rel(b, a) < 1e-5
     rsi.sync_status()
+
+
+@pytest.mark.parametrize("M,K", [(256, 512), (128, 64)])
+def test_gemm_carrier_matches_gemm_then_carrier(M, K):
+    """The fused output layer + carrier (rsi_nn_gemm_carrier) against the GEMM
+    followed by the carrier pass, and against the carrier's FP64 definition
+    on every pixel of two images."""
+    g = torch.Generator(device="cuda").manual_seed(M + K)
+    N = 2 * 128 * 128
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = (torch.randn(N, K, device="cuda", generator=g) / K ** 0.5).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    params = surrogate.LO + (surrogate.HI - surrogate.LO) * np.random.default_rng(M).uniform(size=(M, 5))
+    car = torch.tensor(surrogate.carrier_coeffs(params), dtype=torch.float64, device="cuda")
+    y = torch.empty(M, N, device="cuda")
+    rsi.nn_gemm("f32", A, B, out_f32=y, bias=bias, engine="tcgen05")
+    want = torch.empty_like(y)
+    rsi.nn_carrier(car, surrogate.WINDOW, +1, y, want, scale=1.5)
+    got = torch.full_like(y, float("nan"))
+    rsi.nn_gemm_carrier(A, B, bias, car, surrogate.WINDOW, +1, 1.5, got)
+    rsi.sync_status()
+    assert rel(got, want) < 1e-5
+    yc = y.double().cpu().numpy()
+    xs = -20e-3 + (np.arange(128) + 0.5) * 40e-3 / 128
+    zs = (np.arange(128) + 0.5) * 40e-3 / 128
+    c = surrogate.carrier_coeffs(params)
+    for b in (0, M - 1):
+        psi = c[b, 0] * xs[None, :] + c[b, 1] * zs[:, None] + c[b, 2]
+        ref = 1.5 * (yc[b, 0::2] + 1j * yc[b, 1::2]).reshape(128, 128) * np.exp(1j * psi)
+        gb = got[b].double().cpu().numpy()
+        out = (gb[0::2] + 1j * gb[1::2]).reshape(128, 128)
+        assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-5, b
+    with pytest.raises(rsi.RSIError):  # N must match the window
+        rsi.nn_gemm_carrier(A, B[:N // 2], bias, car, surrogate.WINDOW, +1, 1.0, got[:, :N // 2])
 
 
 def small_net(engine="tcgen05"):
