@@ -1028,7 +1028,9 @@ def run_surrogate_c5(args):
     fused = args.engine == "tcgen05"
     car1024 = torch.tensor(surrogate.carrier_coeffs(params[:1024]), dtype=torch.float64, device="cuda")
     if fused:
-        gemm = lambda: rsi.nn_gemm_carrier(H, Wo, inf.b[-1], car1024, surrogate.WINDOW, +1, scale, inf.y)
+        rows1024 = torch.empty(8 * 1024, dtype=torch.float32, device="cuda")
+        gemm = lambda: rsi.nn_gemm_carrier(H, Wo, inf.b[-1], car1024, surrogate.WINDOW, +1, scale, inf.y,
+                                           workspace=rows1024)
     else:
         gemm = lambda: rsi.nn_gemm("f32", H, Wo, out_f32=inf.y, bias=inf.b[-1], engine=args.engine)
     for _ in range(3):

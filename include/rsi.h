@@ -437,13 +437,15 @@ int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window,
  * being image b of interleaved complex pixels over `window` (N = 2 nx nz)
  * and psi its carrier as in rsi_nn_carrier (carrier[b] = (kx, kz, phi0, .)).
  * A [M x K] and B [N x K] bf16, K-major; M % 128 == 0, N % 128 == 0,
- * K % 64 == 0; A, B, out and bias 16-byte aligned.  Within a block of 16
- * pixels the carrier advances by rotation from one exact phase, which adds
- * up to about 2e-6 relative to rsi_nn_carrier's per-pixel phase.  Fusing
- * the two saves writing the layer's output and reading it back.            */
+ * K % 64 == 0; A, B, out, bias and workspace 16-byte aligned; workspace
+ * holds M x 32 bytes (each row's phase constants, formed once per call).
+ * Within a block of 16 pixels the carrier advances by rotation from one
+ * exact phase, which adds up to about 2e-6 relative to rsi_nn_carrier's
+ * per-pixel phase.  Fusing the two saves writing the layer's output and
+ * reading it back.                                                          */
 int rsi_nn_gemm_carrier(const void *a_bf16, const void *b_bf16, int32_t M, int32_t N, int32_t K,
                         const float *bias, const double *carrier, const rsi_grid *window, int32_t sign,
-                        float scale, float *out, void *stream);
+                        float scale, float *out, float *workspace, void *stream);
 
 /* ---- measurement hooks (no counterpart in the paper) --------------------- */
 /* Number of kernels this library has enqueued in this process.             */

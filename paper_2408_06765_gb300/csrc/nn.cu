@@ -258,6 +258,7 @@ constexpr uint32_t TC_EPI_BYTES = TC_EPI_WARPS * 32 * 32 * 4;
 // row's coefficients (kx, kz, phi0) in FP64, as the carrier pass forms them.
 struct CarrierArgs {
     const double* coef;  // [M][4] (kx, kz, phi0, unused)
+    const float4* rows;  // [M][2]: each row's CarrierRow, formed once per call by carrier_rows_kernel
     int nx, sign;
     float scale;
     double x0, dx, z0, dz;
@@ -294,6 +295,15 @@ __device__ __forceinline__ void carrier_phase(const CarrierRow& r, int ix, int i
     float t = (r.ah + frac_mul_(float(ix), r.uh, r.ul)) + frac_mul_(float(iz), r.wh, r.wl);
     t = (t - rintf(t)) + r.al;
     __sincosf(6.283185307179586f * t, &s, &c);
+}
+
+// the per-row constants of the fused output layer, once per call
+__global__ void carrier_rows_kernel(CarrierArgs ca, int M, float4* __restrict__ rows) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= M) return;
+    const CarrierRow r = carrier_row(ca, b);
+    rows[2 * b] = make_float4(r.ah, r.al, r.uh, r.ul);
+    rows[2 * b + 1] = make_float4(r.wh, r.wl, r.rc, r.rs);
 }
 
 template <int TBN>
@@ -461,8 +471,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float4 bq = make_float4(0.f, 0.f, 0.f, 0.f);
             if (add_bias && 4 * lane < TBN / 2)
                 bq = __ldg(reinterpret_cast<const float4*>(bias + T.n0 + h * (TBN / 2)) + lane);
-            CarrierRow crow;  // this lane's image (row) constants, formed while the MMAs run
-            if (EPI == 3) crow = carrier_row(car, T.m0 + q * 32 + lane);
+            CarrierRow crow;  // this lane's image (row) constants, loaded while the MMAs run
+            if (EPI == 3) {
+                const float4 c0 = __ldg(car.rows + 2 * (T.m0 + q * 32 + lane));
+                const float4 c1 = __ldg(car.rows + 2 * (T.m0 + q * 32 + lane) + 1);
+                crow.ah = c0.x, crow.al = c0.y, crow.uh = c0.z, crow.ul = c0.w;
+                crow.wh = c1.x, crow.wl = c1.y, crow.rc = c1.z, crow.rs = c1.w;
+            }
             const bool ok = mbar_wait_bounded(smem_u32(&acc_full[acc]), uint32_t(tc / 2) & 1u);
             if (!__all_sync(0xffffffffu, ok)) {
                 abort_flag = 1;
@@ -505,23 +520,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (EPI == 3) {  // 16 complex pixels of this row's image: one exact phase, then rotations
                     int p = col0 >> 1;
                     int iz = p / car.nx, ix = p - iz * car.nx;  // the same for every lane (same columns)
-                    float c, sn;
-                    carrier_phase(crow, ix, iz, c, sn);
+                    // e = scale exp(sign i psi) as (c, s); a pixel's value (re, im) becomes
+                    // re (c, s) + im (-s, c); one step in x multiplies e by (rc, sign rs).
+                    // Both products run two lanes at a time (f32x2).
+                    const float2 rot = make_float2(crow.rc, car.sign > 0 ? crow.rs : -crow.rs);
+                    const float2 nrot = make_float2(-rot.y, rot.x);
+                    float2 e;
+                    carrier_phase(crow, ix, iz, e.x, e.y);
+                    e = make_float2(e.x * car.scale, (car.sign > 0 ? e.y : -e.y) * car.scale);
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
-                        const float sv = car.sign > 0 ? sn * car.scale : -sn * car.scale, cv = c * car.scale;
-                        const float re = v[2 * k], im = v[2 * k + 1];
-                        v[2 * k] = fmaf(re, cv, -im * sv);
-                        v[2 * k + 1] = fmaf(re, sv, im * cv);
+                        const float2 o = __ffma2_rn(make_float2(v[2 * k], v[2 * k]), e,
+                                                    __fmul2_rn(make_float2(v[2 * k + 1], v[2 * k + 1]),
+                                                               make_float2(-e.y, e.x)));
+                        v[2 * k] = o.x;
+                        v[2 * k + 1] = o.y;
                         if (k < 15) {
                             if (++ix == car.nx) {  // next image row: restart from the exact phase
                                 ix = 0;
                                 ++iz;
-                                carrier_phase(crow, ix, iz, c, sn);
+                                carrier_phase(crow, ix, iz, e.x, e.y);
+                                e = make_float2(e.x * car.scale, (car.sign > 0 ? e.y : -e.y) * car.scale);
                             } else {
-                                const float cn = fmaf(c, crow.rc, -sn * crow.rs);
-                                sn = fmaf(sn, crow.rc, c * crow.rs);
-                                c = cn;
+                                e = __ffma2_rn(make_float2(e.x, e.x), rot, __fmul2_rn(make_float2(e.y, e.y), nrot));
                             }
                         }
                     }
@@ -957,9 +978,9 @@ extern "C" int rsi_nn_gemm(int32_t epilogue, int32_t engine, int32_t layout, con
 
 extern "C" int rsi_nn_gemm_carrier(const void* A, const void* B, int32_t M, int32_t N, int32_t K, const float* bias,
                                    const double* carrier, const rsi_grid* window, int32_t sign, float scale, float* out,
-                                   void* stream) {
-    if (!A || !B || !carrier || !window || !out || M < 1 || N < 1 || K < 1 || (sign != 1 && sign != -1) ||
-        !isfinite(scale))
+                                   float* workspace, void* stream) {
+    if (!A || !B || !carrier || !window || !out || !workspace || M < 1 || N < 1 || K < 1 ||
+        (sign != 1 && sign != -1) || !isfinite(scale))
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: bad arguments");
     if (M % TC_BM || N % 128 || K % TC_BK)
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: M, N must be multiples of 128 and K of 64 (got %d %d %d)",
@@ -969,7 +990,7 @@ extern "C" int rsi_nn_gemm_carrier(const void* A, const void* B, int32_t M, int3
     if (int64_t(window->nx) * window->nz > (int64_t(1) << 24))
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: window exceeds 2^24 pixels");
     if (misaligned(A, 16) || misaligned(B, 16) || misaligned(out, 16) || misaligned(bias, 16) ||
-        misaligned(carrier, 8))
+        misaligned(carrier, 8) || misaligned(workspace, 16))
         return rsi_fail(RSI_E_INVAL, "rsi_nn_gemm_carrier: misaligned pointer");
     CarrierArgs car;
     car.coef = carrier;
@@ -980,6 +1001,10 @@ extern "C" int rsi_nn_gemm_carrier(const void* A, const void* B, int32_t M, int3
     car.dx = (window->x1 - window->x0) / window->nx;
     car.z0 = window->z0;
     car.dz = (window->z1 - window->z0) / window->nz;
+    car.rows = reinterpret_cast<const float4*>(workspace);
+    carrier_rows_kernel<<<unsigned((M + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        car, M, reinterpret_cast<float4*>(workspace));
+    RSI_CHECK_LAUNCH("carrier_rows_kernel");
     return gemm_tc_launch<3>(static_cast<const bf16*>(A), static_cast<const bf16*>(B), M, N, K, 0, bias, nullptr,
                              out, nullptr, 1, nullptr, static_cast<cudaStream_t>(stream), car);
 }

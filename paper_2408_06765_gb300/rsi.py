@@ -157,7 +157,8 @@ def load(path: str | None = None):
         L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
         L.rsi_nn_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
         L.rsi_nn_adam_dev.argtypes = [vp, vp, vp, vp, i64, vp, f32, f32, f32, vp, vp]
-        L.rsi_nn_gemm_carrier.argtypes = [vp, vp, i32, i32, i32, vp, vp, ctypes.POINTER(Grid), i32, f32, vp, vp]
+        L.rsi_nn_gemm_carrier.argtypes = [vp, vp, i32, i32, i32, vp, vp, ctypes.POINTER(Grid), i32, f32, vp, vp,
+                                          vp]
         L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
         L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, ctypes.c_float, vp, vp, vp]
         L.rsi_selftest_wait_timeout.argtypes = [i64, vp]
@@ -724,13 +725,17 @@ def nn_cast_bf16(x, out, stream=None):
     return out
 
 
-def nn_gemm_carrier(a, b, bias, carrier, window: dict, sign: int, scale: float, out, stream=None):
+def nn_gemm_carrier(a, b, bias, carrier, window: dict, sign: int, scale: float, out, workspace=None,
+                    stream=None):
     """out = scale * exp(sign i psi) * (a b^T + bias) row by row (tcgen05
-    engine): the output layer and the carrier pass in one kernel."""
+    engine): the output layer and the carrier pass in one kernel.  workspace:
+    f32 tensor of at least 8 a.shape[0] elements (allocated here if None)."""
+    if workspace is None:
+        workspace = torch.empty(8 * a.shape[0], dtype=torch.float32, device=a.device)
     G = grid_struct(window)
     _check(load().rsi_nn_gemm_carrier(_ptr(a), _ptr(b), a.shape[0], b.shape[0], a.shape[1], _ptr(bias),
                                       _ptr(carrier), ctypes.byref(G), int(sign), float(scale), _ptr(out),
-                                      _stream(stream)), "rsi_nn_gemm_carrier")
+                                      _ptr(workspace), _stream(stream)), "rsi_nn_gemm_carrier")
     return out
 
 

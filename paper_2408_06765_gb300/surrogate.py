@@ -304,6 +304,7 @@ class GraphedInference:
         self.p = torch.zeros(self.B, 5, dtype=torch.float32, device=dev)
         self.car = torch.zeros(self.B, 4, dtype=torch.float64, device=dev)
         self.out = torch.empty(self.B, 2 * 128 * 128, dtype=torch.float32, device=dev)
+        self.rows = torch.empty(8 * self.B, dtype=torch.float32, device=dev)  # carrier row constants
         self.p_host = torch.zeros(self.B, 5, dtype=torch.float32).pin_memory()
         self.car_host = torch.zeros(self.B, 4, dtype=torch.float64).pin_memory()
         self.copied = None  # event: the last call's host buffers have been read
@@ -323,7 +324,7 @@ class GraphedInference:
         net = self.net
         if net.engine == "tcgen05":  # output layer and carrier in one kernel
             rsi.nn_gemm_carrier(net.hidden(self.p), net.W16[-1], net.b[-1], self.car, WINDOW, +1, self.scale,
-                                self.out)
+                                self.out, workspace=self.rows)
         else:
             rsi.nn_carrier(self.car, WINDOW, +1, net.forward(self.p), self.out, scale=self.scale)
 
