@@ -267,6 +267,29 @@ def test_gemm_carrier_matches_gemm_then_carrier(M, K):
         rsi.nn_gemm_carrier(A, B[:N // 2], bias, car, surrogate.WINDOW, +1, 1.0, got[:, :N // 2])
 
 
+def test_gemm_carrier_row_wrap_and_sign():
+    """A window of 24 x 8 pixels (N = 384): image rows end inside blocks of 16
+    pixels, where the fused epilogue restarts from the exact phase; sign -1
+    (demodulation)."""
+    g = torch.Generator(device="cuda").manual_seed(5)
+    M, K, nx, nz = 128, 64, 24, 8
+    N = 2 * nx * nz
+    win = {"x0": -3e-3, "x1": 4e-3, "nx": nx, "z0": 1e-3, "z1": 9e-3, "nz": nz}
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = (torch.randn(N, K, device="cuda", generator=g) / K ** 0.5).to(torch.bfloat16)
+    bias = torch.randn(N, device="cuda", generator=g)
+    params = surrogate.LO + (surrogate.HI - surrogate.LO) * np.random.default_rng(6).uniform(size=(M, 5))
+    car = torch.tensor(surrogate.carrier_coeffs(params), dtype=torch.float64, device="cuda")
+    y = torch.empty(M, N, device="cuda")
+    rsi.nn_gemm("f32", A, B, out_f32=y, bias=bias, engine="tcgen05")
+    want = torch.empty_like(y)
+    rsi.nn_carrier(car, win, -1, y, want, scale=0.5)
+    got = torch.full_like(y, float("nan"))
+    rsi.nn_gemm_carrier(A, B, bias, car, win, -1, 0.5, got)
+    rsi.sync_status()
+    assert rel(got, want) < 1e-5
+
+
 def small_net(engine="tcgen05"):
     return surrogate.MLP(n_freq=64, width=128, depth=2, n_out=256, batch=128, seed=3, sigma_b=1.0, engine=engine)
 
