@@ -688,6 +688,14 @@ __global__ void colsum_kernel(const bf16* __restrict__ m, int rows, int cols, fl
         out[c] = t;
     }
 }
+// one Adam element: m, v updated in place, returns the new weight
+__device__ __forceinline__ float adam_elem(float w, float& m, float& v, float g, float lr, float b1, float b2,
+                                          float eps, float c1, float c2) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    return w - lr * (m / c1) / (sqrtf(v / c2) + eps);
+}
+
 // hyper, when given, holds (lr, c1, c2) in device memory and overrides the
 // scalar arguments (a schedule that a replayed CUDA graph can follow)
 __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
@@ -700,14 +708,59 @@ __global__ void adam_kernel(float* __restrict__ w, float* __restrict__ m, float*
         c1 = hyper[1];
         c2 = hyper[2];
     }
-    float gi = g[i];
-    float mi = b1 * m[i] + (1.0f - b1) * gi;
-    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    float mi = m[i], vi = v[i];
+    const float wi = adam_elem(w[i], mi, vi, g[i], lr, b1, b2, eps, c1, c2);
     m[i] = mi;
     v[i] = vi;
-    float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     w[i] = wi;
     if (wh) wh[i] = __float2bfloat16_rn(wi);
+}
+
+// the same step four elements per thread (n % 4 == 0, 16-byte aligned arrays):
+// the optimizer is bound by its 30 bytes of traffic per element
+__global__ void adam4_kernel(float4* __restrict__ w, float4* __restrict__ m, float4* __restrict__ v,
+                             const float4* __restrict__ g, int64_t n4, float lr, float b1, float b2, float eps,
+                             float c1, float c2, const float* __restrict__ hyper, uint2* __restrict__ wh) {
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    if (hyper) {
+        lr = hyper[0];
+        c1 = hyper[1];
+        c2 = hyper[2];
+    }
+    const float4 gi = g[i], wi = w[i];
+    float4 mi = m[i], vi = v[i], wo;
+    wo.x = adam_elem(wi.x, mi.x, vi.x, gi.x, lr, b1, b2, eps, c1, c2);
+    wo.y = adam_elem(wi.y, mi.y, vi.y, gi.y, lr, b1, b2, eps, c1, c2);
+    wo.z = adam_elem(wi.z, mi.z, vi.z, gi.z, lr, b1, b2, eps, c1, c2);
+    wo.w = adam_elem(wi.w, mi.w, vi.w, gi.w, lr, b1, b2, eps, c1, c2);
+    m[i] = mi;
+    v[i] = vi;
+    w[i] = wo;
+    if (wh) {
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(wo.x, wo.y), h1 = __floats2bfloat162_rn(wo.z, wo.w);
+        wh[i] = make_uint2(*reinterpret_cast<uint32_t*>(&h0), *reinterpret_cast<uint32_t*>(&h1));
+    }
+}
+
+bool misaligned(const void* p, size_t a);
+
+int launch_adam(float* w, float* m, float* v, const float* g, int64_t n, float lr, float b1, float b2, float eps,
+                float c1, float c2, const float* hyper, void* w_bf16, cudaStream_t s) {
+    const bool vec = n % 4 == 0 && !misaligned(w, 16) && !misaligned(m, 16) && !misaligned(v, 16) &&
+                     !misaligned(g, 16) && !misaligned(w_bf16, 8);
+    if (vec) {
+        const int64_t n4 = n / 4;
+        adam4_kernel<<<unsigned((n4 + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<float4*>(w), reinterpret_cast<float4*>(m), reinterpret_cast<float4*>(v),
+            reinterpret_cast<const float4*>(g), n4, lr, b1, b2, eps, c1, c2, hyper, static_cast<uint2*>(w_bf16));
+        RSI_CHECK_LAUNCH("adam4_kernel");
+    } else {
+        adam_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(w, m, v, g, n, lr, b1, b2, eps, c1, c2, hyper,
+                                                               static_cast<bf16*>(w_bf16));
+        RSI_CHECK_LAUNCH("adam_kernel");
+    }
+    return RSI_OK;
 }
 
 __global__ void cast_kernel(const float* __restrict__ in, int64_t n, bf16* __restrict__ out) {
@@ -1044,19 +1097,15 @@ extern "C" int rsi_nn_adam(float* w, float* m, float* v, const float* g, int64_t
                            float beta2, float eps, int32_t step, void* w_bf16, void* stream) {
     if (!w || !m || !v || !g || n < 1 || step < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_adam: bad arguments");
     float c1 = float(1.0 - pow(double(beta1), step)), c2 = float(1.0 - pow(double(beta2), step));
-    adam_kernel<<<unsigned((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        w, m, v, g, n, lr, beta1, beta2, eps, c1, c2, nullptr, static_cast<bf16*>(w_bf16));
-    RSI_CHECK_LAUNCH("adam_kernel");
-    return RSI_OK;
+    return launch_adam(w, m, v, g, n, lr, beta1, beta2, eps, c1, c2, nullptr, w_bf16,
+                       static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int rsi_nn_adam_dev(float* w, float* m, float* v, const float* g, int64_t n, const float* hyper,
                                float beta1, float beta2, float eps, void* w_bf16, void* stream) {
     if (!w || !m || !v || !g || !hyper || n < 1) return rsi_fail(RSI_E_INVAL, "rsi_nn_adam_dev: bad arguments");
-    adam_kernel<<<unsigned((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        w, m, v, g, n, 0.0f, beta1, beta2, eps, 1.0f, 1.0f, hyper, static_cast<bf16*>(w_bf16));
-    RSI_CHECK_LAUNCH("adam_kernel");
-    return RSI_OK;
+    return launch_adam(w, m, v, g, n, 0.0f, beta1, beta2, eps, 1.0f, 1.0f, hyper, w_bf16,
+                       static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int rsi_nn_cast_bf16(const float* in, int64_t n, void* out_bf16, void* stream) {

@@ -149,17 +149,20 @@ def test_transpose_colsum_cast():
     assert torch.equal(h, f.to(torch.bfloat16))
 
 
-def test_adam_matches_oracle():
+@pytest.mark.parametrize("n", [4096, 4099])  # four elements per thread; a ragged count takes the scalar kernel
+def test_adam_matches_oracle(n):
     rng = np.random.default_rng(0)
-    w0 = rng.normal(size=4096)
+    w0 = rng.normal(size=n)
     w = torch.tensor(w0, dtype=torch.float32, device="cuda")
     m, v = torch.zeros_like(w), torch.zeros_like(w)
-    wo, mo, vo = w0.astype(np.float32).astype(np.float64), np.zeros(4096), np.zeros(4096)
+    wh = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    wo, mo, vo = w0.astype(np.float32).astype(np.float64), np.zeros(n), np.zeros(n)
     for step in range(1, 6):
-        g = rng.normal(size=4096)
-        rsi.nn_adam(w, m, v, torch.tensor(g, dtype=torch.float32, device="cuda"), 1e-3, step)
+        g = rng.normal(size=n)
+        rsi.nn_adam(w, m, v, torch.tensor(g, dtype=torch.float32, device="cuda"), 1e-3, step, w_bf16=wh)
         wo, mo, vo = omlp.adam_step(wo, g.astype(np.float32).astype(np.float64), mo, vo, step, 1e-3)
     assert np.max(np.abs(w.cpu().numpy() - wo)) < 1e-6
+    assert torch.equal(wh, w.to(torch.bfloat16))  # the bf16 copy is the rounded master weight
 
 
 def test_carrier_round_trip_and_definition():
