@@ -446,6 +446,14 @@ int rsi_nn_carrier(const double *carrier, int32_t batch, const rsi_grid *window,
 int rsi_nn_gemm_carrier(const void *a_bf16, const void *b_bf16, int32_t M, int32_t N, int32_t K,
                         const float *bias, const double *carrier, const rsi_grid *window, int32_t sign,
                         float scale, float *out, float *workspace, void *stream);
+/* The surrogate's carrier coefficients on the device: for each of `batch`
+ * parameter rows (x-offset, tilt, water path L, frequency f, image depth d;
+ * f64, row-major [batch][5]) carrier[b] = (k2 s, k2 c, k1 L + k2 c d, 0),
+ * k = 2 pi f / c_medium, s = (c2/c1) sin(tilt), c = sqrt(max(0, 1 - s^2))
+ * (the refracted plane wave below the interface, Snell's law), in FP64; and
+ * params_f32 = the rows rounded to f32 (the network's input).               */
+int rsi_nn_carrier_coeffs(const double *params, int32_t batch, double c1, double c2, double *carrier,
+                          float *params_f32, void *stream);
 
 /* ---- measurement hooks (no counterpart in the paper) --------------------- */
 /* Number of kernels this library has enqueued in this process.             */

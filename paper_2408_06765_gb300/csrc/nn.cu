@@ -297,6 +297,27 @@ __device__ __forceinline__ void carrier_phase(const CarrierRow& r, int ix, int i
     __sincosf(6.283185307179586f * t, &s, &c);
 }
 
+// the surrogate's carrier coefficients from its parameters (x-offset, tilt,
+// water path, frequency, image depth), one row per sample, in FP64: the
+// refracted plane wave's wavenumber components kx = k2 s, kz = k2 c and the
+// phase phi0 = k1 L + k2 c depth at the window's origin, s = (c2/c1) sin(tilt),
+// c = sqrt(max(0, 1 - s^2)); also the FP32 copy of the parameters
+__global__ void carrier_coeffs_kernel(const double* __restrict__ p, int batch, double c1, double c2,
+                                      double* __restrict__ coef, float* __restrict__ pf) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const double* q = p + 5 * size_t(b);
+    const double twopi = 6.283185307179586;
+    const double k1 = twopi * q[3] / c1, k2 = twopi * q[3] / c2;
+    const double s = c2 / c1 * sin(q[1]);
+    const double c = sqrt(fmax(1.0 - s * s, 0.0));
+    coef[4 * size_t(b)] = k2 * s;
+    coef[4 * size_t(b) + 1] = k2 * c;
+    coef[4 * size_t(b) + 2] = k1 * q[2] + k2 * c * q[4];
+    coef[4 * size_t(b) + 3] = 0.0;
+    for (int j = 0; j < 5; ++j) pf[5 * size_t(b) + j] = float(q[j]);
+}
+
 // the per-row constants of the fused output layer, once per call
 __global__ void carrier_rows_kernel(CarrierArgs ca, int M, float4* __restrict__ rows) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1060,6 +1081,16 @@ extern "C" int rsi_nn_gemm_carrier(const void* A, const void* B, int32_t M, int3
     RSI_CHECK_LAUNCH("carrier_rows_kernel");
     return gemm_tc_launch<3>(static_cast<const bf16*>(A), static_cast<const bf16*>(B), M, N, K, 0, bias, nullptr,
                              out, nullptr, 1, nullptr, static_cast<cudaStream_t>(stream), car);
+}
+
+extern "C" int rsi_nn_carrier_coeffs(const double* params, int32_t batch, double c1, double c2, double* carrier,
+                                     float* params_f32, void* stream) {
+    if (!params || !carrier || !params_f32 || batch < 1 || !(c1 > 0) || !(c2 > 0))
+        return rsi_fail(RSI_E_INVAL, "rsi_nn_carrier_coeffs: bad arguments");
+    carrier_coeffs_kernel<<<unsigned((batch + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        params, batch, c1, c2, carrier, params_f32);
+    RSI_CHECK_LAUNCH("carrier_coeffs_kernel");
+    return RSI_OK;
 }
 
 extern "C" int rsi_nn_transpose(const void* in_bf16, int32_t rows, int32_t cols, void* out_bf16, void* stream) {

@@ -47,7 +47,7 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_propagate_stage_multi", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
-           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_adam_dev", "rsi_nn_cast_bf16", "rsi_nn_carrier", "rsi_nn_gemm_carrier",
+           "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_adam_dev", "rsi_nn_cast_bf16", "rsi_nn_carrier", "rsi_nn_gemm_carrier", "rsi_nn_carrier_coeffs",
            "rsi_selftest_wait_timeout"]
 NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
 NN_ENGINE = {"mma_sync": 0, "tcgen05": 1}
@@ -157,6 +157,7 @@ def load(path: str | None = None):
         L.rsi_nn_colsum.argtypes = [vp, i32, i32, vp, vp]
         L.rsi_nn_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
         L.rsi_nn_adam_dev.argtypes = [vp, vp, vp, vp, i64, vp, f32, f32, f32, vp, vp]
+        L.rsi_nn_carrier_coeffs.argtypes = [vp, i32, ctypes.c_double, ctypes.c_double, vp, vp, vp]
         L.rsi_nn_gemm_carrier.argtypes = [vp, vp, i32, i32, i32, vp, vp, ctypes.POINTER(Grid), i32, f32, vp, vp,
                                           vp]
         L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
@@ -723,6 +724,14 @@ def nn_adam_dev(w, m, v, g, hyper, w_bf16=None, beta1=0.9, beta2=0.999, eps=1e-8
 def nn_cast_bf16(x, out, stream=None):
     _check(load().rsi_nn_cast_bf16(_ptr(x), x.numel(), _ptr(out), _stream(stream)), "rsi_nn_cast_bf16")
     return out
+
+
+def nn_carrier_coeffs(params64, c1: float, c2: float, carrier, params32, stream=None):
+    """The surrogate's carrier coefficients (f64 [B, 4]) and its f32 inputs
+    from f64 parameter rows [B, 5], on the device."""
+    _check(load().rsi_nn_carrier_coeffs(_ptr(params64), params64.shape[0], float(c1), float(c2), _ptr(carrier),
+                                        _ptr(params32), _stream(stream)), "rsi_nn_carrier_coeffs")
+    return carrier
 
 
 def nn_gemm_carrier(a, b, bias, carrier, window: dict, sign: int, scale: float, out, workspace=None,

@@ -165,6 +165,18 @@ def test_adam_matches_oracle(n):
     assert torch.equal(wh, w.to(torch.bfloat16))  # the bf16 copy is the rounded master weight
 
 
+def test_carrier_coeffs_on_device():
+    """rsi_nn_carrier_coeffs against the same definition in numpy (FP64), on
+    300 rows that include post-critical tilts, and the f32 inputs."""
+    params = surrogate.LO + (surrogate.HI - surrogate.LO) * np.random.default_rng(2).uniform(size=(300, 5))
+    p64 = torch.tensor(params, dtype=torch.float64, device="cuda")
+    car = torch.empty(300, 4, dtype=torch.float64, device="cuda")
+    p32 = torch.empty(300, 5, dtype=torch.float32, device="cuda")
+    rsi.nn_carrier_coeffs(p64, surrogate.C1, surrogate.C2, car, p32)
+    assert np.allclose(car.cpu().numpy(), surrogate.carrier_coeffs(params), rtol=1e-13, atol=1e-9)
+    assert torch.equal(p32.cpu(), torch.tensor(params, dtype=torch.float32))
+
+
 def test_carrier_round_trip_and_definition():
     params = surrogate.LO + (surrogate.HI - surrogate.LO) * np.random.default_rng(1).uniform(size=(3, 5))
     img = torch.randn(3, 128, 128, dtype=torch.complex64, device="cuda")
