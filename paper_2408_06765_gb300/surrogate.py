@@ -57,23 +57,35 @@ class MLP:
         dims = [2 * n_freq] + [width] * depth + [n_out]
         self.dims = dims
         f32 = dict(dtype=torch.float32, device=device)
-        self.W, self.b = [], []
-        for i in range(len(dims) - 1):
+        # Every weight and bias (and its moments, gradient and bf16 copy) is a
+        # view into one flat buffer per role, segments padded to 64 elements
+        # (128-byte aligned for the GEMMs' tensor maps), so that one Adam
+        # launch updates all parameters; padding has zero gradient and stays 0.
+        pad = lambda n: (n + 63) // 64 * 64
+        shapes = [(dims[i + 1], dims[i]) for i in range(len(dims) - 1)]
+        total = sum(pad(r * c) + pad(r) for r, c in shapes)
+        self.flat = {k: torch.zeros(total, **f32) for k in ("w", "m", "v", "g")}
+        self.flat16 = torch.zeros(total, dtype=torch.bfloat16, device=device)
+        views = {k: ([], []) for k in ("w", "m", "v", "g", "h")}
+        off = 0
+        for r, c in shapes:
+            for k in ("w", "m", "v", "g", "h"):
+                buf = self.flat16 if k == "h" else self.flat[k]
+                views[k][0].append(buf[off:off + r * c].view(r, c))
+                views[k][1].append(buf[off + pad(r * c):off + pad(r * c) + r])
+            off += pad(r * c) + pad(r)
+        self.W, self.b = views["w"]
+        self.mW, self.mb = views["m"]
+        self.vW, self.vb = views["v"]
+        self.gW, self.gb = views["g"]
+        self.W16 = views["h"][0]
+        for i, (r, c) in enumerate(shapes):
             std = math.sqrt(2.0 / dims[i]) if i < len(dims) - 2 else math.sqrt(1.0 / dims[i])
-            self.W.append(torch.tensor(rng.normal(0.0, std, size=(dims[i + 1], dims[i])), **f32))
-            self.b.append(torch.zeros(dims[i + 1], **f32))
+            self.W[i].copy_(torch.tensor(rng.normal(0.0, std, size=(r, c)), **f32))
         self.fmat = torch.tensor(rng.normal(0.0, sigma_b, size=(n_freq, 5)), **f32)
         self.lo = torch.tensor(LO, **f32)
         self.hi = torch.tensor(HI, **f32)
-        self.W16 = [torch.empty(w.shape, dtype=torch.bfloat16, device=device) for w in self.W]
-        for w, h in zip(self.W, self.W16):
-            rsi.nn_cast_bf16(w, h)
-        self.mW = [torch.zeros_like(w) for w in self.W]
-        self.vW = [torch.zeros_like(w) for w in self.W]
-        self.mb = [torch.zeros_like(b) for b in self.b]
-        self.vb = [torch.zeros_like(b) for b in self.b]
-        self.gW = [torch.empty_like(w) for w in self.W]
-        self.gb = [torch.empty_like(b) for b in self.b]
+        rsi.nn_cast_bf16(self.flat["w"], self.flat16)
         self.step_count = 0
         self.scale = 1.0
         self._alloc(batch)
@@ -164,10 +176,11 @@ class MLP:
                                 engine=self.engine)
 
     def adam(self, lr: float):
+        """One Adam step on every parameter: a single launch over the flat
+        buffers (the bf16 copy of the biases it writes is unused)."""
         self.step_count += 1
-        for i in range(len(self.W)):
-            rsi.nn_adam(self.W[i], self.mW[i], self.vW[i], self.gW[i], lr, self.step_count, self.W16[i])
-            rsi.nn_adam(self.b[i], self.mb[i], self.vb[i], self.gb[i], lr, self.step_count)
+        f = self.flat
+        rsi.nn_adam(f["w"], f["m"], f["v"], f["g"], lr, self.step_count, self.flat16)
 
     def train_step(self, p, t, lr: float) -> torch.Tensor:
         self.forward(p)
@@ -265,11 +278,8 @@ class GraphedTrainer:
             net.forward(self.p)
             net.loss(self.t)
             net.backward()
-            for i in range(len(net.W)):
-                rsi.nn_adam_dev(net.W[i], net.mW[i], net.vW[i], net.gW[i], self.hyper, net.W16[i],
-                                self.BETA1, self.BETA2)
-                rsi.nn_adam_dev(net.b[i], net.mb[i], net.vb[i], net.gb[i], self.hyper, None,
-                                self.BETA1, self.BETA2)
+            f = net.flat
+            rsi.nn_adam_dev(f["w"], f["m"], f["v"], f["g"], self.hyper, net.flat16, self.BETA1, self.BETA2)
 
     def step(self, p_all, t_all, idx) -> torch.Tensor:
         """One step on rows idx (a device index tensor) of the training set;
