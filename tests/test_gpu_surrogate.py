@@ -213,13 +213,15 @@ def test_carrier_round_trip_and_definition():
         assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-5, b
 
 
-def test_graphed_inference_matches_eager():
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
+def test_graphed_inference_matches_eager(engine):
     """The CUDA-graph inference path gives the eager path's images, on two
-    batches in a row (its pinned staging buffers are reused).  Its output
-    layer applies the carrier in the GEMM epilogue, advancing the phase by
-    rotation within blocks of 16 pixels (about 1e-6 from the per-pixel
-    phase of the separate carrier pass)."""
-    net = surrogate.MLP(batch=256, seed=5)
+    batches in a row (its pinned staging buffers are reused).  With the
+    tcgen05 engine the output layer applies the carrier in the GEMM
+    epilogue, advancing the phase by rotation within blocks of 16 pixels
+    (about 1e-6 from the per-pixel phase of the separate carrier pass); with
+    mma.sync the graph holds the separate pass."""
+    net = surrogate.MLP(batch=256, seed=5, engine=engine)
     g = surrogate.GraphedInference(net, scale=0.7)
     rng = np.random.default_rng(9)
     for _ in range(2):
