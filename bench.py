@@ -69,7 +69,7 @@ def parse():
                     help="run frequencies that share their points one by one instead of together")
     ap.add_argument("--small", action="store_true",
                     help="f2: 2^14 transducer points onto 256^2 pixels (a profiling case)")
-    ap.add_argument("--case", choices=["chain", "stage", "gemm"], default="chain",
+    ap.add_argument("--case", choices=["chain", "stage", "gemm", "infer"], default="chain",
                     help="stage: only the RSI interface -> image kernel of the 10 MHz c2 chain "
                          "on a 256 x 256 image (small case for profiler captures)")
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
@@ -811,6 +811,38 @@ def run_gemm_case(args):
                       "tflops": 2.0 * M * N * K / ms / 1e9, "gbytes_per_s": nbytes / ms / 1e6}), flush=True)
 
 
+def run_infer_case(args):
+    """The surrogate's inference alone: GraphedInference (carrier
+    coefficients, features, hidden layers, output layer with the carrier) at
+    batch 1024 on a randomly initialised network of the c5 architecture
+    (inference cost does not depend on the weights), `steps` x 8 batches of
+    seeded parameter rows, each staged from the host as a caller would."""
+    import numpy as np
+    import torch
+    from paper_2408_06765_gb300 import build, rsi, surrogate
+    build.build()
+    rsi.load()
+    net = surrogate.MLP(batch=1024, engine=args.engine)
+    ginf = surrogate.GraphedInference(net, 1.0)
+    rng = np.random.default_rng(0)
+    batches = [surrogate.LO + (surrogate.HI - surrogate.LO) * rng.random((1024, 5)) for _ in range(8)]
+    for i in range(max(1, args.warmup)):
+        ginf(batches[i % 8])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        for bp in batches:
+            ginf(bp)
+    e1.record()
+    e1.synchronize()
+    rsi.sync_status()
+    n = args.steps * len(batches)
+    ms = e0.elapsed_time(e1) / n
+    print(json.dumps({"case": "infer", "engine": args.engine, "batch": 1024, "batches": n,
+                      "ms_per_batch": ms, "fields_per_s": 1024 / (ms * 1e-3)}), flush=True)
+
+
 def run_sequences_f3(args):
     """f3: Halton (the paper's points) against scrambled Sobol, side by side:
     on-axis error of the flat piston (closed form) and of the focused cap
@@ -1127,6 +1159,8 @@ def main():
         run_stage_case(args)
     elif args.case == "gemm":
         run_gemm_case(args)
+    elif args.case == "infer":
+        run_infer_case(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
