@@ -6,18 +6,22 @@
 //   features   u = 2 (p - lo)/(hi - lo) - 1, h0 = [sin(pi B u), cos(pi B u)]  (bf16)
 //   gemm       C[M x N] = A[M x K] B[N x K]^T on BF16 tensor cores with FP32
 //              accumulation, two engines: tcgen05 (TMA-fed, 128-byte
-//              swizzled stages, UMMA 128 x 256 x 16 into tensor memory, a
-//              producer lane and an MMA lane on mbarriers) and mma.sync
-//              (m16n8k16 fragments via ldmatrix, 3-stage cp.async pipeline);
-//              both with split K and the fused epilogues:
+//              swizzled stages, UMMA 128 x {256, 128, 64} x 16 into tensor
+//              memory, a producer lane and an MMA lane on mbarriers) and
+//              mma.sync (m16n8k16 fragments via ldmatrix, 3-stage cp.async
+//              pipeline); both with split K and the fused epilogues:
 //                F32        C (+ bias)                       -> f32
 //                BIAS_SILU  z = C + bias -> f32 z, bf16 silu(z)
 //                DSILU      C * silu'(aux)                   -> bf16   (backprop)
+//              and, tcgen05 only, the output layer with the carrier:
+//                CARRIER    scale exp(+-i psi) (C + bias)    -> f32   (inference)
 //   transpose  bf16 [R x C] -> [C x R]
 //   loss       mean (y - t)^2 and its gradient 2 (y - t)/n  -> bf16
 //   colsum     bias gradients (column sums of a bf16 matrix)
-//   adam       Kingma & Ba (2015) on FP32 master weights, bf16 copy out
-//   carrier    multiply an image by exp(+-i psi), psi = kx x + kz z + phi0
+//   adam       Kingma & Ba (2015) on FP32 master weights, bf16 copy out; the
+//              schedule by value or from device memory (a replayed graph)
+//   carrier    multiply an image by exp(+-i psi), psi = kx x + kz z + phi0;
+//              the coefficients (kx, kz, phi0) from the parameters in FP64
 #include <algorithm>
 #include <cuda.h>
 #include <cuda_bf16.h>
