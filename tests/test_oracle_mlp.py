@@ -70,3 +70,57 @@ def test_features_range_and_periodicity():
     f = mlp.features(p, lo, hi, B)
     assert f.shape == (3, 8)
     assert np.allclose(f[:, :4] ** 2 + f[:, 4:] ** 2, 1.0)
+
+
+def test_forward_matches_an_independent_torch_restatement():
+    """forward() against the network built from torch.nn.functional in FP64
+    (linear layers, F.silu, sin/cos features) with the same weights: a
+    dropped pi, a wrong input normalisation, a missing bias or SiLU on the
+    output layer would all show here."""
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    rng = np.random.default_rng(3)
+    params, B = tiny_net(rng, F=4, width=9, depth=3, n_out=6)
+    lo = np.array([-2.0, 0.0, 1.0, -1.0, 5.0])
+    hi = np.array([3.0, 0.5, 4.0, 1.0, 9.0])
+    p = lo + (hi - lo) * rng.uniform(size=(7, 5))
+    y, _ = mlp.forward(params, p, lo, hi, B)
+
+    t = lambda a: torch.tensor(a, dtype=torch.float64)
+    x = (t(p) - t(lo)) / (t(hi) - t(lo)) * 2.0 - 1.0
+    arg = torch.pi * F.linear(x, t(B))
+    h = torch.cat([torch.sin(arg), torch.cos(arg)], dim=1)
+    for W, b in zip(params["W"][:-1], params["b"][:-1]):
+        h = F.silu(F.linear(h, t(W), t(b)))
+    want = F.linear(h, t(params["W"][-1]), t(params["b"][-1])).numpy()
+    assert np.allclose(y, want, rtol=0, atol=1e-13 * np.abs(want).max())
+
+
+def test_features_at_hand_picked_inputs():
+    """Exact feature values: inputs at lo, hi and the middle of the box map
+    to u = -1, 1, 0; with integer and half-integer rows of B the arguments
+    pi B u are multiples of pi/2, whose sines and cosines are 0 and +-1."""
+    lo = np.array([0.0, -1.0])
+    hi = np.array([2.0, 3.0])
+    B = np.array([[1.0, 0.0],    # pi u1
+                  [0.0, 0.5],    # pi u2 / 2
+                  [1.0, 1.0]])   # pi (u1 + u2)
+    p = np.array([[0.0, -1.0],   # u = (-1, -1)
+                  [2.0, 3.0],    # u = ( 1,  1)
+                  [1.0, 1.0],    # u = ( 0,  0)
+                  [0.0, 3.0]])   # u = (-1,  1)
+    f = mlp.features(p, lo, hi, B)
+    want_arg = np.array([[-1.0, -0.5, -2.0],
+                         [1.0, 0.5, 2.0],
+                         [0.0, 0.0, 0.0],
+                         [-1.0, 0.5, 0.0]]) * np.pi
+    want = np.concatenate([np.sin(want_arg), np.cos(want_arg)], axis=1)
+    # sin(-pi/2) = -1, cos(pi) = -1, sin(0) = 0 ...: exact up to the rounding of pi
+    exact = np.array([[0, -1, 0, -1, 0, 1],
+                      [0, 1, 0, -1, 0, 1],
+                      [0, 0, 0, 1, 1, 1],
+                      [0, 1, 0, -1, 0, 1]], dtype=np.float64)
+    assert np.allclose(want, exact, atol=1e-15)
+    assert np.allclose(f, exact, atol=1e-15)
+    # sine block first, then cosine block, one column per row of B
+    assert f.shape == (4, 6)
