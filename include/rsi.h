@@ -215,13 +215,18 @@ int rsi_propagate_stage_multi(const rsi_stage *st, int32_t nf, const double *ks,
  * rsi_propagate_stage, but the scratch is a fixed area of
  * RSI_NOALLOC_SCRATCH_BYTES compiled into the library (held by every GPU that
  * loads it until the process exits); nothing is allocated.
- *   - A stage whose scratch need exceeds the area (staged source tiles plus
- *     partial sums; for FP32C about 2 million sources on few targets) is
- *     rejected with RSI_E_NOMEM before anything is enqueued.  With splits = 0
- *     the call first retries with fewer source splits to fit.
+ *   - The scratch a stage needs is its staged source tiles -- about 32 bytes
+ *     per source for FP32C piston and flat-interface stages (some 2.1 million
+ *     sources fit), 48 bytes with per-point normals (1.4 million) and 64
+ *     bytes for FP64 (1.0 million) -- plus, when the sources are split
+ *     across CTAs, 16 bytes per target for every split.  A stage that does
+ *     not fit is rejected with RSI_E_NOMEM before anything is enqueued.  With
+ *     splits = 0 the call first lowers the automatic split count to what
+ *     fits (chosen, below that bound, as rsi_propagate_stage chooses it).
  *   - The first call on a device looks up the area's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *     that device current) and keeps it for that device's context; a context
+ *     created anew (after cudaDeviceReset) gets a fresh lookup.  Make the
+ *     first call before any stream capture.
  *   - All calls on a device share the area: calls whose GPU work overlaps
  *     (other streams, other host threads) race; order them on one stream.
  *     No part of the area has to start at zero.                            */

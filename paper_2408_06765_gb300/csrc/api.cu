@@ -3,6 +3,8 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <cuda.h>
+
 #include <atomic>
 #include <mutex>
 
@@ -30,12 +32,44 @@ extern "C" uint64_t rsi_launch_count(void) { return g_launches.load(std::memory_
 
 extern "C" const char* rsi_last_error(void) { return g_last_error; }
 
+// ---------------------------------------------------------------------------
+// context identity: cuCtxGetCurrent and cuCtxGetId, taken through the
+// runtime's driver entry points (no link against libcuda)
+// ---------------------------------------------------------------------------
+namespace {
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+template <typename Fn>
+Fn driver_fn(const char* name) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return reinterpret_cast<Fn>(p);
+}
+}  // namespace
+
+unsigned long long rsi_context_id() {
+    static CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+    static CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    unsigned long long id = 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
 // one status word per device (a module-scope __device__ variable exists once
 // per device context)
 static __device__ int g_rsi_status;
 
 #define RSI_MAX_DEVICES 64
+// per device: the status word's device address and the context it belongs to
 static int* g_status_ptr[RSI_MAX_DEVICES];
+static unsigned long long g_status_ctx[RSI_MAX_DEVICES];
 static std::mutex g_status_mu;
 
 int* rsi_status_ptr() {
@@ -44,8 +78,11 @@ int* rsi_status_ptr() {
         rsi_fail(RSI_E_CUDA, "rsi_status_ptr: no current CUDA device");
         return nullptr;
     }
+    const unsigned long long ctx = rsi_context_id();
     std::lock_guard<std::mutex> lk(g_status_mu);
-    if (!g_status_ptr[dev]) {
+    if (!g_status_ptr[dev] || ctx == 0 || ctx != g_status_ctx[dev]) {
+        // first use on this device, or its context was created anew: the
+        // address of the previous context's word is no longer valid
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_rsi_status);
         if (e != cudaSuccess) {
@@ -53,6 +90,7 @@ int* rsi_status_ptr() {
             return nullptr;
         }
         g_status_ptr[dev] = static_cast<int*>(p);
+        g_status_ctx[dev] = rsi_context_id();
     }
     return g_status_ptr[dev];
 }

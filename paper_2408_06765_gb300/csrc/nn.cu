@@ -907,12 +907,12 @@ int gemm_tc_launch_bn(const bf16* A, const bf16* B, int M, int N, int K, int lay
                       const float* aux, float* outf, bf16* outh, int splits, float* work, cudaStream_t s,
                       const CarrierArgs& car = CarrierArgs{}) {
     using C = TcCfg<TBN>;
-    static bool attr = false;
-    if (!attr) {
+    static RsiCtxOnce attr;
+    if (attr.needed()) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(gemm_tc_kernel<EPI, TBN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           int(C::SMEM)),
                      "cudaFuncSetAttribute(gemm_tc)");
-        attr = true;
+        attr.done();
     }
     int* status = rsi_status_ptr();
     if (!status) return RSI_E_CUDA;
@@ -971,12 +971,12 @@ int gemm_tc_launch(const bf16* A, const bf16* B, int M, int N, int K, int layout
 template <int EPI>
 int gemm_launch(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, const float* aux, float* outf,
                 bf16* outh, int splits, float* work, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
+    static RsiCtxOnce attr;
+    if (attr.needed()) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(gemm_tn_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           int(GEMM_SMEM)),
                      "cudaFuncSetAttribute(gemm)");
-        attr = true;
+        attr.done();
     }
     const int kt = K / BK;
     const int kts = (kt + splits - 1) / splits;

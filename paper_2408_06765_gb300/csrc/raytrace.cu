@@ -542,12 +542,12 @@ int rt_plan(const rsi_raytrace& rt, int64_t n_src, int64_t n_tgt, RtPlan& p) {
 
 template <int NW>
 int launch_rt(dim3 grid, size_t smem, const RtArgs& a, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
+    static RsiCtxOnce attr;
+    if (attr.needed()) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(raytrace_kernel<kTpt, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           64 * 1024),
                      "cudaFuncSetAttribute(raytrace)");
-        attr = true;
+        attr.done();
     }
     raytrace_kernel<kTpt, NW><<<grid, kRtThreads, smem, s>>>(a);
     RSI_CHECK_LAUNCH("raytrace_kernel");

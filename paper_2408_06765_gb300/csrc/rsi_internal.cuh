@@ -32,6 +32,33 @@ void rsi_note_launch();
 // message on failure
 int* rsi_status_ptr();
 
+// Identity of the calling thread's current CUDA context (cuCtxGetId); 0 when
+// no context is current yet or the driver does not offer the query.  State
+// that belongs to a context -- kernel attributes, device addresses of module
+// variables -- is cached under this id, so that a context that is torn down
+// and created again (cudaDeviceReset, another primary context) is set up
+// afresh instead of reusing stale attributes or addresses.
+unsigned long long rsi_context_id();
+
+// One-time set-up per context: needed() is true until done() has been called
+// with the same context current.  Several devices used in turn simply repeat
+// the (cheap) set-up.
+struct RsiCtxOnce {
+    unsigned long long ctx = 0;
+    bool needed() const {
+        const unsigned long long id = rsi_context_id();
+        return id == 0 || id != __atomic_load_n(&ctx, __ATOMIC_ACQUIRE);
+    }
+    void done() { __atomic_store_n(&ctx, rsi_context_id(), __ATOMIC_RELEASE); }
+};
+
+// Workspace of rsi_propagate_stage with the automatic split count (st->splits
+// == 0) limited to max_splits >= 1, chosen as rsi_propagate_stage chooses it
+// below that limit; the split count of that plan goes to *splits.  0 on
+// invalid input.
+size_t rsi_stage_workspace_bytes_capped(const rsi_stage* st, int64_t n_src, int64_t n_tgt, int max_splits,
+                                        int* splits);
+
 // status codes written by kernels
 #define RSI_DEV_TIMEOUT 1
 #define RSI_DEV_NONFINITE 2

@@ -119,7 +119,9 @@ struct Plan {
 
 bool valid_tile(int S) { return S == 32 || S == 64 || S == 128 || S == 256 || S == 512; }
 
-int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p) {
+// max_auto_splits bounds the automatic split count (st.splits == 0); the
+// choice below it still minimises the busiest SM's work.
+int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p, int max_auto_splits = 128) {
     if (st.kind != RSI_STAGE_PISTON && st.kind != RSI_STAGE_RSI)
         return rsi_fail(RSI_E_INVAL, "unknown stage kind %d", st.kind);
     if (st.precision != RSI_PREC_FP64 && st.precision != RSI_PREC_FP32C)
@@ -178,7 +180,7 @@ int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p) {
         // minimise (waves x tiles per CTA), the time of the busiest SM
         int64_t best_cost = INT64_MAX;
         splits = 1;
-        for (int s = 1; s <= 128 && s <= p.n_tiles; ++s) {
+        for (int s = 1; s <= max_auto_splits && s <= p.n_tiles; ++s) {
             int64_t tps = (p.n_tiles + s - 1) / s;
             int64_t s_act = (p.n_tiles + tps - 1) / tps;
             int64_t waves = (blocks * s_act + slots - 1) / slots;
@@ -203,6 +205,15 @@ extern "C" size_t rsi_stage_workspace_bytes(const rsi_stage* st, int64_t n_src, 
     if (!st) return 0;
     Plan p;
     if (make_plan(*st, n_src, n_tgt, p) != RSI_OK) return 0;
+    return p.tiles_bytes + p.partial_bytes;
+}
+
+size_t rsi_stage_workspace_bytes_capped(const rsi_stage* st, int64_t n_src, int64_t n_tgt, int max_splits,
+                                        int* splits) {
+    if (!st || max_splits < 1) return 0;
+    Plan p;
+    if (make_plan(*st, n_src, n_tgt, p, max_splits) != RSI_OK) return 0;
+    if (splits) *splits = p.splits;
     return p.tiles_bytes + p.partial_bytes;
 }
 

@@ -43,12 +43,12 @@ __global__ void prep_fp32_kernel(int kind, int normals, int64_t n_src, PointsVie
 template <int KIND, int NORM, int TPT, int VAR>
 int launch_t(const StageArgs& a, cudaStream_t s) {
     size_t smem = RSI_PIPE_STAGES * a.tile_bytes + RSI_PIPE_STAGES * sizeof(uint64_t);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static RsiCtxOnce attr_set;
+    if (attr_set.needed()) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(stage_fp32_kernel<KIND, NORM, TPT, VAR>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
                      "cudaFuncSetAttribute(stage_fp32)");
-        attr_set = true;
+        attr_set.done();
     }
     int64_t per_block = int64_t(kThreads) * TPT;
     dim3 grid(unsigned((a.n_tgt + per_block - 1) / per_block), unsigned(a.splits));

@@ -150,12 +150,12 @@ __global__ void prep_fp64_kernel(int kind, int normals, int64_t n_src, PointsVie
 template <int KIND, int NORM>
 int launch_t(const StageArgs& a, cudaStream_t s) {
     size_t smem = RSI_PIPE_STAGES * a.tile_bytes + RSI_PIPE_STAGES * sizeof(uint64_t);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static RsiCtxOnce attr_set;
+    if (attr_set.needed()) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(stage_fp64_kernel<KIND, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           200 * 1024),
                      "cudaFuncSetAttribute(stage_fp64)");
-        attr_set = true;
+        attr_set.done();
     }
     dim3 grid(unsigned((a.n_tgt + kThreads - 1) / kThreads), unsigned(a.splits));
     stage_fp64_kernel<KIND, NORM><<<grid, kThreads, smem, s>>>(a);

@@ -529,11 +529,11 @@ size_t msmem(size_t tile_bytes) { return RSI_PIPE_STAGES * tile_bytes + RSI_PIPE
 template <int KIND, int NORM, int NF, int PK>
 int mlaunch(const MultiArgs& a, cudaStream_t s, bool occ, int* occ_out) {
     auto kern = stage_multi_kernel<KIND, NORM, NF, PK>;
-    static bool attr = false;
-    if (!attr) {
+    static RsiCtxOnce attr;
+    if (attr.needed()) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
                      "cudaFuncSetAttribute(stage_multi)");
-        attr = true;
+        attr.done();
     }
     if (occ) {
         int b = 0;

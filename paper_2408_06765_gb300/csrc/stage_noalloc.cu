@@ -31,24 +31,30 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[RSI_NOALLOC_SCR
 namespace {
 
 constexpr int kMaxDevices = 64;
+// per device: the area's device address and the context it was looked up in
 void* g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Device address of the static area for the current device.  In host code
-// the name g_noalloc_scratch is only a host-side stand-in, so the address is
-// looked up once per device (with that device current) and cached.
+// Device address of the static area in the current device's context.  In
+// host code the name g_noalloc_scratch is only a host-side stand-in, so the
+// address is looked up with the device current.  The lookup is kept per
+// device and redone whenever the device's context is not the one it was made
+// in (after cudaDeviceReset the old address would be dangling).
 int scratch_for_current_device(void** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return rsi_cuda_fail(e, "rsi_propagate_stage_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices)
         return rsi_fail(RSI_E_UNSUPPORTED, "rsi_propagate_stage_noalloc: device %d out of range", dev);
+    const unsigned long long ctx = rsi_context_id();
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return rsi_cuda_fail(e, "rsi_propagate_stage_noalloc: cudaGetSymbolAddress");
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = rsi_context_id();
     }
     *out = g_scratch_addr[dev];
     return RSI_OK;
@@ -60,16 +66,30 @@ extern "C" int rsi_propagate_stage_noalloc(const rsi_stage* st, const void* src_
                                            const double* src_sigma, const void* tgt_points, int64_t n_tgt,
                                            double* tgt_field, void* stream) {
     if (!st) return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_noalloc: null stage");
+    constexpr size_t kArea = RSI_NOALLOC_SCRATCH_BYTES;
     rsi_stage s = *st;
     size_t need = rsi_stage_workspace_bytes(&s, n_src, n_tgt);
     if (need == 0) return RSI_E_INVAL;  // the stage description was rejected; message already set
-    if (need > RSI_NOALLOC_SCRATCH_BYTES && s.splits == 0) {
-        // the automatic split count wants more room for partial sums than the
-        // static area has: use fewer splits (the same sums, grouped differently)
-        for (int sp = 64; sp >= 1; sp /= 2) {
-            s.splits = sp;
-            need = rsi_stage_workspace_bytes(&s, n_src, n_tgt);
-            if (need != 0 && need <= RSI_NOALLOC_SCRATCH_BYTES) break;
+    if (need > kArea && s.splits == 0) {
+        // The automatic split count wants more room for partial sums than the
+        // static area has.  Each split holds n_tgt complex partial sums next to
+        // the staged tiles (the split-free plan's workspace), so bound the
+        // split count by what is left and let the planner choose below that
+        // bound as it always does (fewest waves x tiles per CTA).  The sums are
+        // the same, grouped differently.
+        rsi_stage one = s;
+        one.splits = 1;
+        const size_t tiles = rsi_stage_workspace_bytes(&one, n_src, n_tgt);
+        if (tiles != 0 && tiles <= kArea) {
+            const size_t per_split = size_t(n_tgt) * 2 * sizeof(double);
+            const size_t cap = (kArea - tiles) / per_split;
+            int chosen = 1;
+            if (cap >= 2) {
+                need = rsi_stage_workspace_bytes_capped(&s, n_src, n_tgt, int(cap < 128 ? cap : 128), &chosen);
+            } else {
+                need = tiles;
+            }
+            s.splits = chosen;
         }
     }
     if (need == 0 || need > RSI_NOALLOC_SCRATCH_BYTES)

@@ -41,7 +41,8 @@ IMG = {"c128": 0, "c64": 1, "abs32": 2}
 
 SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes",
            "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points",
-           "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_interface_transmit",
+           "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_propagate_stage_noalloc",
+           "rsi_interface_transmit",
            "rsi_interface_reflect", "rsi_field_image", "rsi_field_image_sum", "rsi_launch_count",
            "rsi_raytrace_workspace_bytes", "rsi_raytrace_field", "rsi_stage_multi_workspace_bytes",
            "rsi_propagate_stage_multi", "rsi_timing_enable", "rsi_timing_read",
@@ -125,6 +126,7 @@ def load(path: str | None = None):
         L.rsi_stage_workspace_bytes.restype = sz
         L.rsi_stage_workspace_bytes.argtypes = [ctypes.POINTER(Stage), i64, i64]
         L.rsi_propagate_stage.argtypes = [ctypes.POINTER(Stage), vp, i64, vp, vp, i64, vp, vp, sz, vp]
+        L.rsi_propagate_stage_noalloc.argtypes = [ctypes.POINTER(Stage), vp, i64, vp, vp, i64, vp, vp]
         L.rsi_interface_transmit.argtypes = [ctypes.POINTER(Interface), vp, i64, vp, vp, vp]
         L.rsi_field_image.argtypes = [ctypes.POINTER(Grid), vp, ctypes.c_double, ctypes.c_double,
                                       i32, vp, vp]

@@ -23,12 +23,7 @@ RSI_E_NOMEM = -5
 def noalloc():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     build.build()
-    L = rsi.load()
-    f = L.rsi_propagate_stage_noalloc
-    f.restype = ctypes.c_int
-    f.argtypes = [ctypes.POINTER(rsi.Stage), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
-                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
-    return f
+    return rsi.load().rsi_propagate_stage_noalloc  # argument types set by the binding
 
 
 def rel_l2(a, b):
@@ -76,3 +71,34 @@ def test_noalloc_rejects_stages_beyond_the_static_area(noalloc):
     rc = noalloc(ctypes.byref(st), p, 1 << 22, p, p, 1 << 10, p, stream())
     assert rc == RSI_E_NOMEM
     assert b"static area" in rsi.load().rsi_last_error()
+
+
+def test_noalloc_lowers_the_split_count_to_fit(noalloc):
+    """With splits = 0, a stage whose automatic split count would need more
+    partial-sum space than the static area holds runs with fewer splits: the
+    same field as the workspace entry point.  1.9 million piston sources in
+    32-source tiles (32-byte header + 32 records of 32 bytes) take 59.8 MiB
+    of the 64 MiB area, so at most eight splits of 2^15 targets (0.5 MiB of
+    partial sums each) fit beside them, while the automatic count for 64
+    target blocks asks for more."""
+    L = rsi.load()
+    n_src = 1_900_000
+    pist = rsi.make_qmc_points({"kind": "disk", "centre": (0.0, 0.0, 0.0), "a": 6.35e-3}, 0, 0, n_src)
+    grid = rsi.grid_points({"x0": -0.02, "x1": 0.02, "nx": 256, "z0": 0.03, "z1": 0.07, "nz": 128})
+    k1 = 2 * math.pi * 5e6 / 1480.0
+    st = rsi.stage_struct(rsi.STAGE_PISTON, "fp32c", k1, tile=32)
+    auto = L.rsi_stage_workspace_bytes(ctypes.byref(st), pist.n, grid.n)
+    one = rsi.stage_struct(rsi.STAGE_PISTON, "fp32c", k1, tile=32, splits=1)
+    tiles_only = L.rsi_stage_workspace_bytes(ctypes.byref(one), pist.n, grid.n)
+    area = 64 << 20
+    assert auto > area >= tiles_only, (auto, tiles_only)  # the case this test is about
+    ref = rsi.propagate_stage(st, pist, None, grid)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        out = torch.full_like(ref, float("nan"))
+        rc = noalloc(ctypes.byref(st), pist.ptr(), pist.n, None, grid.ptr(), grid.n,
+                     ctypes.c_void_p(out.data_ptr()), stream())
+        assert rc == 0, L.rsi_last_error()
+        torch.cuda.synchronize()
+        rsi.sync_status()
+        assert rel_l2(out, ref) <= TOL["fp32c"]
