@@ -132,6 +132,16 @@ typedef struct rsi_grid {
  * W = 0).  points_bytes >= rsi_points_bytes(nx * nz).                       */
 int rsi_grid_points(const rsi_grid *g, void *points, size_t points_bytes, void *stream);
 
+/* Slots [first, first + count) of a point set of n points, every field, as a
+ * point set of `count` points in out_points (>= rsi_points_bytes(count)
+ * bytes, 256-byte aligned, not overlapping the input).  A stage's targets
+ * are independent of one another (each is its own sum in Eq. incident_field
+ * and Eq. rayleigh_sommerfeld), so a stage can be evaluated on a contiguous
+ * share of its target slots -- the unit of work of a target-sharded chain on
+ * several GPUs.  Requires 0 <= first, 1 <= count, first + count <= n.      */
+int rsi_points_slice(const void *points, int64_t n, int64_t first, int64_t count, void *out_points,
+                     size_t out_bytes, void *stream);
+
 /* ---- stage sums (steps a3, a5, a6) ------------------------------------- */
 enum rsi_stage_kind {
     RSI_STAGE_PISTON = 0, /* Eq. incident_field: phi(Q) = -(v0/2pi) sum w e^{ikr}/r */

@@ -40,7 +40,7 @@ TMODE = {"global": 0, "local": 1}
 IMG = {"c128": 0, "c64": 1, "abs32": 2}
 
 SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes",
-           "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points",
+           "rsi_points_offset", "rsi_make_qmc_points", "rsi_grid_points", "rsi_points_slice",
            "rsi_stage_workspace_bytes", "rsi_propagate_stage", "rsi_propagate_stage_noalloc",
            "rsi_interface_transmit",
            "rsi_interface_reflect", "rsi_field_image", "rsi_field_image_sum", "rsi_launch_count",
@@ -123,6 +123,7 @@ def load(path: str | None = None):
         L.rsi_points_offset.argtypes = [i32, i64]
         L.rsi_make_qmc_points.argtypes = [ctypes.POINTER(Surface), u64, u32, i64, vp, sz, vp]
         L.rsi_grid_points.argtypes = [ctypes.POINTER(Grid), vp, sz, vp]
+        L.rsi_points_slice.argtypes = [vp, i64, i64, i64, vp, sz, vp]
         L.rsi_stage_workspace_bytes.restype = sz
         L.rsi_stage_workspace_bytes.argtypes = [ctypes.POINTER(Stage), i64, i64]
         L.rsi_propagate_stage.argtypes = [ctypes.POINTER(Stage), vp, i64, vp, vp, i64, vp, vp, sz, vp]
@@ -249,6 +250,14 @@ def grid_points(g: dict, device="cuda", stream=None, out: Points | None = None) 
     _check(load().rsi_grid_points(ctypes.byref(G), pts.ptr(), pts.nbytes, _stream(stream)),
            "rsi_grid_points")
     return pts
+
+
+def points_slice(pts: Points, first: int, count: int, stream=None, out: Points | None = None) -> Points:
+    """Slots [first, first + count) of a point set as a point set of its own."""
+    sub = out if out is not None else Points(count, pts.buf.device)
+    _check(load().rsi_points_slice(pts.ptr(), pts.n, int(first), int(count), sub.ptr(), sub.nbytes,
+                                   _stream(stream)), "rsi_points_slice")
+    return sub
 
 
 # ---------------------------------------------------------------------------

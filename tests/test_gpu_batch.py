@@ -11,6 +11,7 @@ import torch
 import oracle
 from paper_2408_06765_gb300 import build, rsi
 from paper_2408_06765_gb300 import workloads as W
+from fieldcheck import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +62,7 @@ def test_batch_matches_plain_path_and_oracle(curved):
             assert rel_l2(got, plain) <= 1e-3
             assert rel_l2(got, plain) <= 1e-5  # same kernels, different source grouping
             if i in (2, 3):
-                assert rel_l2(got, oracle.field_image(cfg)) <= 1e-4
+                assert_close(got, oracle.field_image(cfg), 1e-4)
         # replaying the graph reproduces the images bit for bit
         b.run()
         torch.cuda.synchronize()

@@ -13,6 +13,7 @@ import torch
 
 from paper_2408_06765_gb300 import build, rsi
 from paper_2408_06765_gb300 import workloads as W
+from fieldcheck import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -46,5 +47,4 @@ def test_full_size_chain_matches_stored_oracle(name):
     rsi.sync_status()
     got = img.reshape(-1).cpu().numpy()[np.asarray(rec["pixels"])]
     want = np.asarray(rec["re"]) + 1j * np.asarray(rec["im"])
-    err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
-    assert err <= TOL, err
+    assert_close(got, want, TOL, name)

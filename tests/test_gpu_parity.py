@@ -12,6 +12,7 @@ import torch
 import oracle
 from paper_2408_06765_gb300 import build, rsi
 from paper_2408_06765_gb300 import workloads as W
+from fieldcheck import assert_close, max_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -122,15 +123,18 @@ def chain_parity(cfg, tol, stage_opts=None):
     torch.cuda.synchronize()
     rsi.sync_status()
     ref_phi, ref_kept = oracle.chain(cfg, keep=True)
-    errs = []
+    errs, worst = [], []
     for (gpts, gphi), (_, ophi) in zip(res.ifaces, ref_kept):
         idx = u32(gpts.field("IDX"))
         errs.append(rel_l2(gphi.cpu().numpy(), ophi[idx]))
+        worst.append(max_rel(gphi.cpu().numpy(), ophi[idx]))
     g = cfg["grid"]
     k_last = oracle.wavenumber(cfg["freq"], cfg["media"][len(cfg["interfaces"])]["c"])
     img_ref = (k_last / cfg["v0"]) * ref_phi.reshape(g["nz"], g["nx"])
     errs.append(rel_l2(res.image.cpu().numpy(), img_ref))
+    worst.append(max_rel(res.image.cpu().numpy(), img_ref))
     assert max(errs) <= tol, errs
+    assert max(worst) <= 10 * tol, worst  # no error confined to a few pixels
     return errs, res
 
 
@@ -210,7 +214,7 @@ def test_coincident_targets_contribute_nothing(prec):
     rsi.sync_status()
     ref = oracle.piston_field(src, src, k)
     assert np.all(np.isfinite(out.cpu().numpy()))
-    assert rel_l2(out.cpu().numpy(), ref) <= TOL[prec]
+    assert_close(out.cpu().numpy(), ref, TOL[prec])
     # curved surface: chords are not normal to the surface normals
     cyl = rsi.make_qmc_points({"kind": "cyl", "centre": (0.0, 0.0, 0.02), "wx": 0.03, "wy": 0.03,
                                "R": 0.02}, 0, 2, 700)
@@ -222,7 +226,7 @@ def test_coincident_targets_contribute_nothing(prec):
            "w": hp["W"]}
     ref = oracle.rsi_field(src, sig, src, k)
     assert np.all(np.isfinite(out.cpu().numpy()))
-    assert rel_l2(out.cpu().numpy(), ref) <= TOL[prec]
+    assert_close(out.cpu().numpy(), ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32c"])
@@ -234,7 +238,7 @@ def test_single_source_single_target(prec):
     hp = host_points(pist)
     ref = oracle.piston_field({"x": hp["X"], "y": hp["Y"], "z": hp["Z"], "w": hp["W"]},
                               {"x": np.array([1e-3]), "y": np.zeros(1), "z": np.array([0.04])}, k, 2.0)
-    assert rel_l2(out.cpu().numpy(), ref) <= TOL[prec]
+    assert_close(out.cpu().numpy(), ref, TOL[prec])
 
 
 def test_status_word_is_clean():
@@ -261,7 +265,7 @@ def test_c2_full_size_sampled():
     tg = {key: o_if[key][idx[slots]] for key in ("x", "y", "z")}
     k1 = oracle.wavenumber(cfg["freq"], 1480.0)
     ref1 = oracle.piston_field(o_pist, tg, k1)
-    assert rel_l2(gphi.cpu().numpy()[slots], ref1) <= TOL["fp32c"]
+    assert_close(gphi.cpu().numpy()[slots], ref1, TOL["fp32c"])
     # stage 2 at full size with an oracle-side source density (a tilted
     # Gaussian beam on the 2^18 interface points), sampled on 2048 pixels
     k2 = oracle.wavenumber(cfg["freq"], 5900.0)
@@ -274,4 +278,4 @@ def test_c2_full_size_sampled():
     pix = rng.choice(grid.n, 2048, replace=False)
     og = oracle.grid_points(cfg["grid"])
     ref2 = oracle.rsi_field(o_if, sig_o, {key: og[key][pix] for key in ("x", "y", "z")}, k2)
-    assert rel_l2(out.cpu().numpy()[pix], ref2) <= TOL["fp32c"]
+    assert_close(out.cpu().numpy()[pix], ref2, TOL["fp32c"])
