@@ -119,7 +119,8 @@ def config_block(cfgs, n_gpus, name="c2"):
             "precision": ("fp64" if cfgs[0]["precision"] == "fp64"
                           else "fp32 pairs, double-float phase, compensated sums"),
             "l2": "flushed (256 MiB write) before every timed step",
-            "parallelism": f"replica per GPU x{n_gpus}" if n_gpus > 1 else "1 GPU"}
+            "parallelism": (f"target-sharded chain x{n_gpus} (stage targets split over the ranks, one "
+                            "all-gather per interface and one of the image rows)" if n_gpus > 1 else "1 GPU")}
 
 
 # ---------------------------------------------------------------------------
@@ -196,12 +197,32 @@ def recorded_traffic(kernel: str = "stage_fp32_kernel"):
     return int(m.group(1)) if h.hexdigest()[:16] == m.group(2) else None
 
 
-def measure_unit_rates(rsi, torch):
+def recorded_fp64_ops():
+    """FP64-pipe thread instructions per pair of the FP64 piston stage kernel
+    from the committed ncu summary, if the kernel source is still the one the
+    counters were taken on; else None."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "stage_fp64_c1_fp64_ops.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"stage_fp64_kernel_fp64_ops_per_pair ([0-9.]+) source_sha256_16 (\w+)", open(path).read())
+    if not m:
+        return None
+    h = hashlib.sha256()
+    for f in ("stage_fp64.cu",):
+        h.update(open(os.path.join(ROOT, "paper_2408_06765_gb300", "csrc", f), "rb").read())
+    return float(m.group(1)) if h.hexdigest()[:16] == m.group(2) else None
+
+
+def measure_unit_rates(rsi, torch, kinds=("ffma", "rsqrt", "sin")):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     blocks, iters = sms * 8, 65536
     sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
     rates = {}
-    for kind in ("ffma", "rsqrt", "sin"):
+    for kind in kinds:
+        if kind == "dfma":
+            iters = 4096  # the FP64 pipe is slow: keep the probe short
         rsi.ubench(kind, blocks, 64, sink)  # warm-up
         best = float("inf")
         for _ in range(5):
@@ -283,6 +304,100 @@ def oracle_sample(cfg, seconds: float, seed: int = 0):
             "iface_slots_natural": s1, "phi1": phi1, "threads": oracle.default_threads()}
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def image_error(got, want) -> dict:
+    """Relative L2 error over the values and the worst value's error relative
+    to the largest reference value."""
+    import numpy as np
+    got, want = np.asarray(got, np.complex128).ravel(), np.asarray(want, np.complex128).ravel()
+    return {"rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+            "max_abs_over_max_ref": float(np.max(np.abs(got - want)) / np.max(np.abs(want))),
+            "values": int(want.size)}
+
+
+def golden_error(img, name: str):
+    """image_error at the stored FP64-oracle pixels tests/golden/<name>.json
+    (written by tests/golden/make_golden.py, which calls only the oracle)."""
+    import numpy as np
+    path = os.path.join(GOLDEN, name + ".json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    got = img.reshape(-1).cpu().numpy()[np.asarray(rec["pixels"])]
+    return image_error(got, np.asarray(rec["re"]) + 1j * np.asarray(rec["im"]))
+
+
+def single_core_rate(cfg, seconds: float = 4.0) -> float:
+    """FP64 oracle pair rate on ONE host thread: all piston points onto m
+    interface points of the workload, m sized for about `seconds`."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    pc, it = cfg["piston"], cfg["interfaces"][0]
+    piston = oracle.make_points(dict(pc, kind="disk"), cfg["seed"], pc["set_id"], pc["n"])
+    iface = oracle.make_points(it, cfg["seed"], it["set_id"], it["n"])
+    k1 = oracle.wavenumber(cfg["freq"], cfg["media"][0]["c"])
+
+    def run(m):
+        tg = {k: iface[k][:m] for k in ("x", "y", "z")}
+        t0 = time.perf_counter()
+        oracle.piston_field(piston, tg, k1, nthreads=1)
+        return pc["n"] * m / (time.perf_counter() - t0)
+
+    rate = run(8)
+    m = int(min(it["n"], max(8, seconds * rate / pc["n"])))
+    return run(m)
+
+
+def cpu_leg_and_error(args, cfgs, pairs_step, images):
+    """Rank 0: the FP64 oracle on the host cores (cpu_baseline) and the error
+    of the timed step's own images against it.
+      c2  the images of all three frequencies at the 1024 stored oracle pixels
+          of each; the oracle timed on a bounded sample of the chain;
+      c1, c3  the oracle runs the whole workload (timed in full), and the
+          images are compared on every pixel.
+    Each cpu_baseline also carries the oracle's rate on one thread."""
+    import oracle
+    name = args.config
+    fp64 = cfgs[0]["precision"] == "fp64"
+    err = {"tolerance": 1e-5 if fp64 else 1e-4}
+    cpu = None
+    if name == "c2":
+        err["what"] = "the timed step's images, each frequency at its 1024 stored FP64-oracle pixels"
+        for cfg, img in zip(cfgs, images):
+            err[f"{cfg['freq'] / 1e6:g}MHz"] = golden_error(img, f"c2_{cfg['freq'] / 1e6:g}MHz")
+        if not args.no_cpu_baseline:
+            cfg = cfgs[min(1, len(cfgs) - 1)]
+            smp = oracle_sample(cfg, args.cpu_seconds)
+            cpu = {"value": smp["rate"], "unit": UNIT, "cores": smp["threads"], "kind": "oracle",
+                   "sample": f"c2 at {cfg['freq'] / 1e6:g} MHz: all {cfg['piston']['n']} piston points "
+                             f"onto {smp['m']} random interface points + all "
+                             f"{cfg['interfaces'][0]['n']} interface points onto {smp['m']} random "
+                             f"pixels ({smp['pairs']:.3g} pairs, {smp['seconds']:.1f} s), FP64",
+                   "single_core_rate": single_core_rate(cfg)}
+        return cpu, err
+    labels = {"c1": ["5MHz"], "c3": ["flat", "curved"]}[name]
+    if args.no_cpu_baseline:
+        if name == "c3":
+            err["what"] = "the timed step's images at 1024 stored FP64-oracle pixels each"
+            for lab, img in zip(labels, images):
+                err[lab] = golden_error(img, f"c3_{lab}")
+            return None, err
+    t0 = time.perf_counter()
+    want = [oracle.field_image(c) for c in cfgs]
+    dt = time.perf_counter() - t0
+    err["what"] = "the timed step's images against the FP64 oracle's whole images, every pixel"
+    for lab, img, w in zip(labels, images, want):
+        err[lab] = image_error(img.cpu().numpy(), w)
+    if not args.no_cpu_baseline:
+        cpu = {"value": pairs_step / dt, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+               "sample": f"the whole {name} workload ({pairs_step:.3g} pairs, {dt:.1f} s), FP64",
+               "single_core_rate": single_core_rate(cfgs[0])}
+    return cpu, err
+
+
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
@@ -339,10 +454,32 @@ def run_ours(args):
     multi = (not args.no_multi and not args.variant and rsi.same_geometry(cfgs) and len(cfgs) <= 4
              and cfgs[0].get("precision", "fp32c") == "fp32c")
 
-    def step():
-        if multi:  # the frequencies share every point: one pass over the pair geometry
-            return rsi.run_chain_multi(cfgs, fmt="c64", workspace=ws, device=dev)
-        return [rsi.run_chain(c, fmt="c64", workspace=ws, device=dev, stage_opts=opts).image for c in cfgs]
+    sharded = world > 1
+    if sharded:
+        # one chain split over the ranks: every stage's targets divided among
+        # them, one all-gather of the transmitted amplitudes per interface and
+        # one of the image rows (shard.py); total work fixed as N grows
+        from paper_2408_06765_gb300 import shard
+        be = shard.LibrsiBackend(cfgs[0].get("precision", "fp32c"), device=dev)
+        gather = shard.torch_allgather(world)
+        counts = shard.row_counts(cfgs, world)
+        groups = [cfgs] if multi else [[c] for c in cfgs]
+
+        def step():
+            out = []
+            for grp in groups:
+                _, rows = shard.run_rank(grp, rank, world, be, gather)
+                local = (rows.reshape(len(grp), -1) if rows is not None else
+                         torch.empty((len(grp), 0), dtype=torch.complex128, device=dev))
+                full = gather(local, sum(counts), counts)
+                out += [full[f].view(c["grid"]["nz"], c["grid"]["nx"]) for f, c in enumerate(grp)]
+            return out
+    else:
+        def step():
+            if multi:  # the frequencies share every point: one pass over the pair geometry
+                return rsi.run_chain_multi(cfgs, fmt="c64", workspace=ws, device=dev)
+            fmt = "c128" if cfgs[0]["precision"] == "fp64" else "c64"  # FP64 images keep their digits
+            return [rsi.run_chain(c, fmt=fmt, workspace=ws, device=dev, stage_opts=opts).image for c in cfgs]
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -373,7 +510,12 @@ def run_ours(args):
     pis_ms, pis_n, pis_pairs = rsi.timing_read(rsi.STAGE_PISTON)
     rsi.timing_enable(False)
     rsi.sync_status()
-    total_s, value = aggregate(world, pairs_step, args.steps, sum(step_ms) * 1e-3)
+    # the job's work per step is one chain (2.58e11 pair terms for c2) whatever
+    # the number of ranks: the rate is that over the slowest rank's time
+    total_s = reduce_max(sum(step_ms) * 1e-3, world)
+    value = pairs_step * args.steps / total_s
+    last_images = step()
+    torch.cuda.synchronize()
 
     # dominant kernel: the RSI stage kernel (interface -> image dominates)
     avg_s = rsi_ms * 1e-3 / max(1, rsi_n)
@@ -402,18 +544,29 @@ def run_ours(args):
                               "peak": pis_peak / 1e9, "avg_launch_ms": pis_avg * 1e3,
                               "launches": pis_n}}
     if cfgs[0]["precision"] == "fp64":
-        roof = {"bound": "alu", "kernel": "stage_fp64_kernel", "achieved": achieved / 1e9,
-                "peak": None, "unit": "Gpair/s", "frac": None, "traffic": None,
-                "note": "FP64 path (sqrt, division and sincos in double on the FP64 pipe); "
-                        "no FP64 roofline is modelled",
-                "avg_launch_ms": avg_s * 1e3, "launches": rsi_n}
+        # FP64 pipe bound: the measured DFMA rate over the FP64-pipe thread
+        # instructions per pair that ncu counted on the piston stage kernel
+        # (sqrt, division and sincos in double are sequences of DFMA/DMUL/DADD)
+        dfma = measure_unit_rates(rsi, torch, ("dfma",))["dfma"]
+        ops64 = recorded_fp64_ops()
+        pis_achieved = (pis_pairs / max(1, pis_n)) / max(pis_avg, 1e-12)
+        peak64 = dfma / ops64 if ops64 else None
+        roof = {"bound": "fp64", "kernel": "stage_fp64_kernel<PISTON> (the RSI stage's kernel is the same "
+                                           "arithmetic plus the obliquity)",
+                "achieved": pis_achieved / 1e9, "peak": peak64 / 1e9 if peak64 else None, "unit": "Gpair/s",
+                "frac": pis_achieved / peak64 if peak64 else None, "traffic": None,
+                "fp64_ops_per_pair": ops64, "dfma_rate_tops": dfma / 1e12,
+                "dfma_lanes_per_sm_clock": dfma / (n_sm * clk_hz),
+                "peak_source": "rsi_ubench DFMA probe (measured in this run) / FP64-pipe thread instructions "
+                               "per pair counted by ncu (profiles/stage_fp64_c1_fp64_ops.md)",
+                "rsi_kernel": {"achieved": achieved / 1e9, "avg_launch_ms": avg_s * 1e3, "launches": rsi_n},
+                "avg_launch_ms": pis_avg * 1e3, "launches": pis_n}
     if cfgs[0]["precision"] != "fp64" and args.config == "c2":
         roof["traffic"] = recorded_traffic("stage_multi_kernel" if multi else "stage_fp32_kernel")
 
     e2e = None
     if not args.no_e2e:
-        host = [torch.empty((c["grid"]["nz"], c["grid"]["nx"]), dtype=torch.complex64,
-                            pin_memory=True) for c in cfgs]
+        host = [torch.empty(tuple(im.shape), dtype=im.dtype, pin_memory=True) for im in last_images]
         d2h = sum(h.numel() * h.element_size() for h in host)
         e2e_s = []
         for _ in range(args.steps):
@@ -425,42 +578,26 @@ def run_ours(args):
                 h.copy_(im, non_blocking=True)
             torch.cuda.synchronize()
             e2e_s.append(time.perf_counter() - t0)
-        _, e2e_value = aggregate(world, pairs_step, args.steps, sum(e2e_s))
+        e2e_value = pairs_step * args.steps / reduce_max(sum(e2e_s), world)
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                "note": "inputs are scalar workload parameters passed by value through the "
-                       "C ABI (no array inputs); the three c64 images are read back each step"}
+                       "C ABI (no array inputs); the step's images are read back each step"}
 
-    cpu = None
-    err = None
-    if rank == 0 and not args.no_cpu_baseline:
-        import numpy as np
-        cfg = cfgs[min(1, len(cfgs) - 1)]
-        smp = oracle_sample(cfg, args.cpu_seconds)
-        cpu = {"value": smp["rate"], "unit": UNIT, "cores": smp["threads"], "kind": "oracle",
-               "sample": f"c2 at {cfg['freq'] / 1e6:g} MHz: all {cfg['piston']['n']} piston points "
-                         f"onto {smp['m']} random interface points + all "
-                         f"{cfg['interfaces'][0]['n']} interface points onto {smp['m']} random "
-                         f"pixels ({smp['pairs']:.3g} pairs, {smp['seconds']:.1f} s), FP64"}
-        res = rsi.run_chain(cfg, keep=True, workspace=ws, device=dev)
-        gif, gphi = res.ifaces[0]
-        idx = gif.field("IDX").cpu().numpy().view(np.uint32)
-        slot_of = np.empty_like(idx)
-        slot_of[idx] = np.arange(idx.size, dtype=np.uint32)
-        g = gphi.cpu().numpy()[slot_of[smp["iface_slots_natural"]]]
-        err = float(np.linalg.norm(g - smp["phi1"]) / np.linalg.norm(smp["phi1"]))
+    cpu, err = None, None
+    if rank == 0:
+        cpu, err = cpu_leg_and_error(args, cfgs, pairs_step, last_images)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": max(3, args.warmup),
                 "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None,
+                "scaling": "strong", "vs_baseline": None,
                 "dtype": "f64" if cfgs[0]["precision"] == "fp64" else "f32",
                 "data": "synthetic (seeded scrambled-Sobol points; workload parameters only)",
                 "config": config_block(cfgs, world, args.config),
-                "field_pts_per_s": world * pixels_step * args.steps / total_s,
-                "rel_l2_err": {"piston_stage_sampled_vs_fp64_oracle": err,
-                               "tolerance": 1e-5 if cfgs[0]["precision"] == "fp64" else 1e-4},
+                "field_pts_per_s": pixels_step * args.steps / total_s,
+                "rel_l2_err": err,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches, "gpu": torch.cuda.get_device_name(dev)}
         print(json.dumps(line), flush=True)
@@ -603,6 +740,25 @@ def run_batch_c4(args):
         p = plain[j].cpu().numpy().astype(np.complex128)
         errs.append(float(np.linalg.norm(g - p) / np.linalg.norm(p)))
     sub_pairs = sum(W.pairs_of(c) for c in sub_cfgs)
+    # the FP64 oracle on 64 seeded instances (timed on the host cores) and
+    # the batched images of those instances against it
+    cpu, oracle_err = None, None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        pick = sorted(np.random.default_rng(64).choice(len(cfgs), min(64, len(cfgs)), replace=False).tolist())
+        t0 = time.perf_counter()
+        want = [oracle.field_image(cfgs[i]) for i in pick]
+        dt = time.perf_counter() - t0
+        opairs = sum(W.pairs_of(cfgs[i]) for i in pick)
+        e = [image_error(b.image(i).cpu().numpy(), w) for i, w in zip(pick, want)]
+        oracle_err = {"instances": len(pick), "max_rel_l2": max(x["rel_l2"] for x in e),
+                      "median_rel_l2": float(np.median([x["rel_l2"] for x in e])),
+                      "max_abs_over_max_ref": max(x["max_abs_over_max_ref"] for x in e), "tolerance": 1e-4}
+        cpu = {"value": opairs / dt, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+               "sample": f"{len(pick)} seeded instances of the scan, whole chains ({opairs:.3g} pairs, "
+                         f"{dt:.1f} s), FP64",
+               "single_core_rate": single_core_rate(cfgs[pick[0]])}
     # step-level bound: every piston and RSI pair at its kernel's ALU (MUFU)
     # limit, at the median SM clock of the timed region; everything else in
     # the graph (points, transmission, prep, reduce, images) counts as overhead
@@ -627,6 +783,7 @@ def run_batch_c4(args):
                                  "batch_gpair_per_s": sub_pairs / batch_sub_ms / 1e6,
                                  "plain_gpair_per_s": sub_pairs / plain_sub_ms / 1e6,
                                  "max_rel_l2": max(errs), "tolerance": 1e-3},
+            "rel_l2_err": oracle_err, "cpu_baseline": cpu,
             "roofline": {"bound": "alu", "kernel": "whole batched step: piston and RSI pairs at their "
                                                     "stage kernels' MUFU limits",
                          "achieved": pairs / t_step / 1e9, "peak": pairs / t_bound / 1e9, "unit": "Gpair/s",
