@@ -498,9 +498,10 @@ int rsi_selftest_wait_timeout(int64_t cycles, void *stream);
  *   RSI_UB_FFMA  fused multiply-add (FP32 pipe)
  *   RSI_UB_RSQRT rsqrt.approx.f32   (MUFU)
  *   RSI_UB_SIN   sin.approx.f32     (MUFU, after its range scaling)
+ *   RSI_UB_DFMA  fused multiply-add in double precision (FP64 pipe)
  * over `blocks` CTAs of 256 threads; `sink` (device, >= blocks*256 floats)
  * receives one value per thread.  Time it with events on `stream`.         */
-enum rsi_ubench_kind { RSI_UB_FFMA = 0, RSI_UB_RSQRT = 1, RSI_UB_SIN = 2 };
+enum rsi_ubench_kind { RSI_UB_FFMA = 0, RSI_UB_RSQRT = 1, RSI_UB_SIN = 2, RSI_UB_DFMA = 3 };
 int rsi_ubench(int32_t kind, int32_t blocks, int32_t iters, float *sink, void *stream);
 
 #ifdef __cplusplus

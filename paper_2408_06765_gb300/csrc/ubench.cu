@@ -1,7 +1,8 @@
 // ubench.cu -- throughput probes of the FP32 pipe and of the multi-function
-// unit (MUFU), the two units that bound the source x target kernels.  Each
-// thread runs 8 independent dependency chains so that issue, not latency,
-// limits the rate.
+// unit (MUFU), the two units that bound the FP32C source x target kernels,
+// and of the FP64 pipe, which bounds the FP64 stage kernel.  Each thread runs
+// 8 independent dependency chains so that issue, not latency, limits the
+// rate.
 #include "rsi_internal.cuh"
 
 namespace {
@@ -29,6 +30,20 @@ __global__ void __launch_bounds__(256) ubench_kernel(int iters, float* sink) {
     sink[size_t(blockIdx.x) * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void __launch_bounds__(256) ubench_dfma_kernel(int iters, float* sink) {
+    double v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = 1.0 + 1e-3 * double(threadIdx.x + 32 * c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = fma(v[c], 0.999999999, 1e-9);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += v[c];
+    sink[size_t(blockIdx.x) * blockDim.x + threadIdx.x] = float(s);
+}
+
 }  // namespace
 
 extern "C" int rsi_ubench(int32_t kind, int32_t blocks, int32_t iters, float* sink, void* stream) {
@@ -38,6 +53,7 @@ extern "C" int rsi_ubench(int32_t kind, int32_t blocks, int32_t iters, float* si
         case RSI_UB_FFMA: ubench_kernel<RSI_UB_FFMA><<<blocks, 256, 0, s>>>(iters, sink); break;
         case RSI_UB_RSQRT: ubench_kernel<RSI_UB_RSQRT><<<blocks, 256, 0, s>>>(iters, sink); break;
         case RSI_UB_SIN: ubench_kernel<RSI_UB_SIN><<<blocks, 256, 0, s>>>(iters, sink); break;
+        case RSI_UB_DFMA: ubench_dfma_kernel<<<blocks, 256, 0, s>>>(iters, sink); break;
         default: return rsi_fail(RSI_E_INVAL, "rsi_ubench: unknown kind %d", kind);
     }
     RSI_CHECK_LAUNCH("ubench_kernel");

@@ -52,7 +52,7 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_selftest_wait_timeout"]
 NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
 NN_ENGINE = {"mma_sync": 0, "tcgen05": 1}
-UB = {"ffma": 0, "rsqrt": 1, "sin": 2}
+UB = {"ffma": 0, "rsqrt": 1, "sin": 2, "dfma": 3}
 
 
 class Surface(ctypes.Structure):
