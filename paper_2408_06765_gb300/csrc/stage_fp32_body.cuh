@@ -23,7 +23,6 @@
 
 #include <math.h>
 
-#include "sincos_poly.cuh"
 #include "stage.cuh"
 
 // Build-time tuning knobs (the defaults are the measured best).
@@ -57,31 +56,7 @@ constexpr int packed_unroll() {
 
 struct TgtRef {
     float Dx, Dy, Dz, mx, my, mz, R, R2, tau;
-    float taut;  // tau in turns
 };
-
-// Source pairs out of every 4 of the packed far path whose sincos runs as a
-// polynomial on the FMA pipe (sincos_turns2) instead of on the MUFU.  The
-// MUFU pipe otherwise bounds the packed kernel: per source pair it is busy
-// 48 cycles (rsqrt x 2, sin and cos x 2, 8 cycles a warp instruction) against
-// about 25 (piston), 33 (RSI, flat) or 37 (RSI, per-point normals) issue
-// cycles; a polynomial pair costs 16 MUFU and about 10 more issue cycles.
-// The counts minimise max(MUFU, issue) in that model; RSI_FP32_POLY_PISTON,
-// RSI_FP32_POLY_RSI_Z and RSI_FP32_POLY_RSI_POINTS override them.
-#ifndef RSI_FP32_POLY_PISTON
-#define RSI_FP32_POLY_PISTON 2
-#endif
-#ifndef RSI_FP32_POLY_RSI_Z
-#define RSI_FP32_POLY_RSI_Z 2
-#endif
-#ifndef RSI_FP32_POLY_RSI_POINTS
-#define RSI_FP32_POLY_RSI_POINTS 1
-#endif
-template <int KIND, int NORM>
-constexpr int poly_of_4() {
-    return KIND == RSI_STAGE_PISTON ? RSI_FP32_POLY_PISTON
-                                    : (NORM == RSI_NORMALS_POINTS ? RSI_FP32_POLY_RSI_POINTS : RSI_FP32_POLY_RSI_Z);
-}
 
 // double-float reference of one target against one tile centre
 __device__ __forceinline__ TgtRef target_reference(float qxh, float qxl, float qyh, float qyl, float qzh,
@@ -126,7 +101,6 @@ __device__ __forceinline__ TgtRef target_reference(float qxh, float qxl, float q
     t.R = Rh;
     t.R2 = Rh * Rh;
     t.tau = x;
-    t.taut = __fmul_rn(x, tp.inv);
     return t;
 }
 
@@ -134,30 +108,6 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// sin(2 pi t) and cos(2 pi t) of two phases in turns at once, on the FMA pipe
-// instead of the MUFU: s = t - rint(t) in [-1/2, 1/2] (round to nearest by
-// adding and subtracting 1.5 * 2^23, exact for |t| < 2^22; the difference
-// t - rint(t) is exact), then the polynomials of sincos_poly.cuh in s^2.
-// 16 packed instructions for two sincos; error a few 1e-7, as the MUFU's.
-__device__ __forceinline__ float2 f2c(float v) { return make_float2(v, v); }
-__device__ __forceinline__ void sincos_turns2(float2 t, float2& sn, float2& cs) {
-    const float2 r = __fadd2_rn(__fadd2_rn(t, f2c(12582912.0f)), f2c(-12582912.0f));
-    const float2 s = __ffma2_rn(r, f2c(-1.0f), t);
-    const float2 u = __fmul2_rn(s, s);
-    float2 p = __ffma2_rn(f2c(RSI_POLY_S5), u, f2c(RSI_POLY_S4));
-    p = __ffma2_rn(p, u, f2c(RSI_POLY_S3));
-    p = __ffma2_rn(p, u, f2c(RSI_POLY_S2));
-    p = __ffma2_rn(p, u, f2c(RSI_POLY_S1));
-    p = __ffma2_rn(p, u, f2c(RSI_POLY_S0));
-    sn = __fmul2_rn(p, s);
-    float2 q = __ffma2_rn(f2c(RSI_POLY_C6), u, f2c(RSI_POLY_C5));
-    q = __ffma2_rn(q, u, f2c(RSI_POLY_C4));
-    q = __ffma2_rn(q, u, f2c(RSI_POLY_C3));
-    q = __ffma2_rn(q, u, f2c(RSI_POLY_C2));
-    q = __ffma2_rn(q, u, f2c(RSI_POLY_C1));
-    cs = __ffma2_rn(q, u, f2c(RSI_POLY_C0));
 }
 
 // the source term once the phase u and 1/r are known
@@ -243,7 +193,7 @@ __device__ __forceinline__ void pair_far(const TgtRef& t, const float4& a, const
 // negation; they are combined once per tile.
 // ---------------------------------------------------------------------------
 struct TgtRef2 {
-    float2 mx, my, mz, R2, nR, pR, tau, taut, Dx, Dy, Dz;
+    float2 mx, my, mz, R2, nR, pR, tau, Dx, Dy, Dz;
 };
 __device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
     TgtRef2 r;
@@ -254,7 +204,6 @@ __device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
     r.nR = make_float2(-t.R, -t.R);
     r.pR = make_float2(t.R, t.R);
     r.tau = make_float2(t.tau, t.tau);
-    r.taut = make_float2(t.taut, t.taut);
     r.Dx = make_float2(t.Dx, t.Dx);
     r.Dy = make_float2(t.Dy, t.Dy);
     r.Dz = make_float2(t.Dz, t.Dz);
@@ -262,11 +211,10 @@ __device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
 }
 
 // two sources (v0 = px, py; v1 = -pz, |p|^2/2; v2, v3 amplitudes; n0, n1
-// normals) onto one target reference, far path; POLY: the sincos on the FMA
-// pipe (phase in turns, kt = k / 2 pi), else on the MUFU (phase in radians)
-template <int KIND, int NORM, bool POLY>
+// normals) onto one target reference, far path
+template <int KIND, int NORM>
 __device__ __forceinline__ void pair_far2(const TgtRef2& t, const float4& v0, const float4& v1, const float4& v2,
-                                          const float4& v3, const float4& n0, const float4& n1, float2 k, float2 kt,
+                                          const float4& v3, const float4& n0, const float4& n1, float2 k,
                                           float2& ar1, float2& ar2, float2& ai1, float2& ai2) {
     const float2 px = make_float2(v0.x, v0.y), py = make_float2(v0.z, v0.w);
     const float2 pzn = make_float2(v1.x, v1.y), pwh = make_float2(v1.z, v1.w);
@@ -280,14 +228,10 @@ __device__ __forceinline__ void pair_far2(const TgtRef2& t, const float4& v0, co
     const float2 q = __fmul2_rn(am, __fadd2_rn(r0, t.pR));                    // r0^2 - R^2
     const float2 eh = __ffma2_rn(q, make_float2(-0.5f, -0.5f), th);           // (r^2 - r0^2)/2
     const float2 dr = __ffma2_rn(eh, ir, am);                                 // r - R
+    const float2 u = __ffma2_rn(k, dr, t.tau);
     float2 sn, cs;
-    if (POLY) {
-        sincos_turns2(__ffma2_rn(kt, dr, t.taut), sn, cs);
-    } else {
-        const float2 u = __ffma2_rn(k, dr, t.tau);
-        __sincosf(u.x, &sn.x, &cs.x);
-        __sincosf(u.y, &sn.y, &cs.y);
-    }
+    __sincosf(u.x, &sn.x, &cs.x);
+    __sincosf(u.y, &sn.y, &cs.y);
     if (KIND == RSI_STAGE_PISTON) {
         const float2 amp = __fmul2_rn(make_float2(v2.x, v2.y), ir);
         ar1 = __ffma2_rn(amp, cs, ar1);
@@ -363,8 +307,6 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
 #pragma unroll
     for (int q = 0; q < TPT; ++q) hr[q] = lr[q] = hi[q] = li[q] = 0.0f;
     const float k = w.kh;
-    // k / 2 pi, correctly rounded from the double-float wavenumber
-    const float kt = __double2float_rn((double(w.kh) + double(w.kl)) * (0.5 / 3.14159265358979323846));
     int failed_at = -1;
 
     for (int it = 0; it < w.ntile; ++it) {
@@ -403,27 +345,15 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
                     a1[q] = a2[q] = b1[q] = b2[q] = make_float2(0.f, 0.f);
                 }
                 const float2 k2 = make_float2(k, k);
-                const float2 kt2 = make_float2(kt, kt);
-                // groups of 4 source pairs (S / 2 is a multiple of 4): the first
-                // poly_of_4() of each group take the FMA-pipe sincos
-#pragma unroll 1
-                for (int i = 0; i < w.S / 2; i += 4) {
+#pragma unroll packed_unroll<KIND>()
+                for (int i = 0; i < w.S / 2; ++i) {
+                    const float4* pr = rec + i * 2 * rec_f4;
+                    const float4 v0 = pr[0], v1 = pr[1], v2 = pr[2], v3 = pr[3];
+                    const float4 n0 = (rec_f4 == 3) ? pr[4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 n1 = (rec_f4 == 3) ? pr[5] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const float4* pr = rec + (i + m) * 2 * rec_f4;
-                        const float4 v0 = pr[0], v1 = pr[1], v2 = pr[2], v3 = pr[3];
-                        const float4 n0 = (rec_f4 == 3) ? pr[4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float4 n1 = (rec_f4 == 3) ? pr[5] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                        for (int q = 0; q < TPT; ++q) {
-                            if (m < poly_of_4<KIND, NORM>())
-                                pair_far2<KIND, NORM, true>(r2[q], v0, v1, v2, v3, n0, n1, k2, kt2, a1[q], a2[q],
-                                                            b1[q], b2[q]);
-                            else
-                                pair_far2<KIND, NORM, false>(r2[q], v0, v1, v2, v3, n0, n1, k2, kt2, a1[q], a2[q],
-                                                             b1[q], b2[q]);
-                        }
-                    }
+                    for (int q = 0; q < TPT; ++q)
+                        pair_far2<KIND, NORM>(r2[q], v0, v1, v2, v3, n0, n1, k2, a1[q], a2[q], b1[q], b2[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < TPT; ++q) {

@@ -26,33 +26,6 @@ constexpr int kMTpt = 2;
 #define RSI_MULTI_PACKED_MIN_BLOCKS 4
 #endif
 
-// Frequencies of the packed far path whose sincos runs as a polynomial on the
-// FMA pipe (sincos_turns2) instead of on the MUFU, the lowest-numbered ones.
-// Per pair of sources the MUFU pipe otherwise bounds the kernel (a MUFU
-// warp instruction occupies its pipe 8 cycles, an FMA-pipe instruction 1
-// issue cycle); moving some frequencies' sincos to the FMA pipe balances the
-// two.  Issue cycles per source pair in the model: RSI shared 24, per MUFU
-// frequency 15 (+32 MUFU cycles), per polynomial frequency 25; piston shared
-// 16 (+16 MUFU), 9 (+32 MUFU), 19.  The counts below minimise max(MUFU,
-// issue); RSI_MULTI_POLY_RSI / _PISTON override them (0 = all on the MUFU).
-#ifdef RSI_MULTI_POLY_RSI
-constexpr int kPolyRsi[5] = {0, RSI_MULTI_POLY_RSI, RSI_MULTI_POLY_RSI, RSI_MULTI_POLY_RSI, RSI_MULTI_POLY_RSI};
-#else
-constexpr int kPolyRsi[5] = {0, 0, 1, 1, 2};
-#endif
-#ifdef RSI_MULTI_POLY_PISTON
-constexpr int kPolyPiston[5] = {0, RSI_MULTI_POLY_PISTON, RSI_MULTI_POLY_PISTON, RSI_MULTI_POLY_PISTON,
-                                RSI_MULTI_POLY_PISTON};
-#else
-constexpr int kPolyPiston[5] = {0, 0, 1, 2, 2};
-#endif
-template <int KIND, int NF>
-constexpr int poly_count() {
-    return (KIND == RSI_STAGE_PISTON ? kPolyPiston[NF] : kPolyRsi[NF]) < NF
-               ? (KIND == RSI_STAGE_PISTON ? kPolyPiston[NF] : kPolyRsi[NF])
-               : NF;
-}
-
 struct MultiArgs {
     int kind, normals, nf, packed, S, n_tiles, tiles_per_split, splits;
     int64_t n_tgt;
@@ -60,7 +33,6 @@ struct MultiArgs {
     const uint8_t* tiles;
     TgtView tgt;
     float kh[kMaxNF], kl[kMaxNF];
-    float kt[kMaxNF];  // k / 2 pi: the wavenumbers in turns per metre
     TwoPiSplit tp;
     double2* out;  // [splits][nf][n_tgt] partial sums, or the fields [nf][n_tgt]
     int* status;
@@ -80,8 +52,7 @@ __host__ __device__ inline int mrec_f4_rt(int kind, int normals, int nf) {
 
 struct MRef {
     float Dx, Dy, Dz, mx, my, mz, R, R2;
-    float tau[kMaxNF];   // k R mod 2 pi (rad)
-    float taut[kMaxNF];  // the same in turns
+    float tau[kMaxNF];
 };
 
 // double-float reference of one target against one tile centre: D, R and the
@@ -119,7 +90,6 @@ __device__ __forceinline__ MRef multi_reference(float qxh, float qxl, float qyh,
         x = __fmaf_rn(-n, a.tp.p2, x);
         x = __fmaf_rn(-n, a.tp.p3, x);
         t.tau[f] = __fadd_rn(x, pl);
-        t.taut[f] = __fmul_rn(t.tau[f], a.tp.inv);
     }
     t.Dx = dxh;
     t.Dy = dyh;
@@ -218,7 +188,7 @@ __device__ __forceinline__ void mpair_near(const MRef& t, const float4* r, const
 // ---------------------------------------------------------------------------
 struct MRef2 {
     float2 mx, my, mz, R2, nR, pR, Dx, Dy, Dz;
-    float2 tau[kMaxNF], taut[kMaxNF];
+    float2 tau[kMaxNF];
 };
 template <int NF>
 __device__ __forceinline__ MRef2 packed_mref(const MRef& t) {
@@ -233,32 +203,15 @@ __device__ __forceinline__ MRef2 packed_mref(const MRef& t) {
     r.Dy = make_float2(t.Dy, t.Dy);
     r.Dz = make_float2(t.Dz, t.Dz);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
-        r.tau[f] = make_float2(t.tau[f], t.tau[f]);
-        r.taut[f] = make_float2(t.taut[f], t.taut[f]);
-    }
+    for (int f = 0; f < NF; ++f) r.tau[f] = make_float2(t.tau[f], t.tau[f]);
     return r;
 }
 
 // two sources (records pr[0..RF4*2-1], packed) onto one target, far path;
 // acc[f] = (sum h vr c, sum h vi s, sum h vr s, sum h vi c) for RSI or
 // (sum A c / r, -, sum A s / r, -) for the piston
-// sincos of frequency f's phase: the first poly_count() frequencies on the FMA
-// pipe (phase in turns), the others on the MUFU (phase in radians)
-template <int KIND, int NF>
-__device__ __forceinline__ void msincos2(int f, const MRef2& t, const float2* kv, const float2* kt, float2 dr,
-                                         float2& sn, float2& cs) {
-    if (f < poly_count<KIND, NF>()) {
-        sincos_turns2(__ffma2_rn(kt[f], dr, t.taut[f]), sn, cs);
-    } else {
-        const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
-        __sincosf(u.x, &sn.x, &cs.x);
-        __sincosf(u.y, &sn.y, &cs.y);
-    }
-}
-
 template <int KIND, int NORM, int NF>
-__device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, const float2* kv, const float2* kt,
+__device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, const float2* kv,
                                            float2 (&acc)[NF][4]) {
     const float4 v0 = pr[0], v1 = pr[1];
     const float2 px = make_float2(v0.x, v0.y), py = make_float2(v0.z, v0.w);
@@ -278,8 +231,10 @@ __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, con
         const float2 amp = __fmul2_rn(make_float2(va.x, va.y), ir);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
+            const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
             float2 sn, cs;
-            msincos2<KIND, NF>(f, t, kv, kt, dr, sn, cs);
+            __sincosf(u.x, &sn.x, &cs.x);
+            __sincosf(u.y, &sn.y, &cs.y);
             acc[f][0] = __ffma2_rn(amp, cs, acc[f][0]);
             acc[f][2] = __ffma2_rn(amp, sn, acc[f][2]);
         }
@@ -297,8 +252,10 @@ __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, con
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
             const float4 b0 = pr[2 + 2 * f], b1 = pr[3 + 2 * f];
+            const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
             float2 sn, cs;
-            msincos2<KIND, NF>(f, t, kv, kt, dr, sn, cs);
+            __sincosf(u.x, &sn.x, &cs.x);
+            __sincosf(u.y, &sn.y, &cs.y);
             const float2 vr = __ffma2_rn(ir, make_float2(b0.x, b0.y), make_float2(b1.x, b1.y));
             const float2 vi = __ffma2_rn(ir, make_float2(b0.z, b0.w), make_float2(b1.z, b1.w));
             const float2 hv = __fmul2_rn(h, vr), hw = __fmul2_rn(h, vi);
@@ -389,12 +346,9 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
             for (int f = 0; f < NF; ++f) ar[q][f] = ai[q][f] = 0.0f;
         }
         if (PK && __all_sync(0xffffffffu, far_lane)) {
-            float2 k2[NF], kt2[NF];
+            float2 k2[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
-                k2[f] = make_float2(kv[f], kv[f]);
-                kt2[f] = make_float2(a.kt[f], a.kt[f]);
-            }
+            for (int f = 0; f < NF; ++f) k2[f] = make_float2(kv[f], kv[f]);
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
                 const MRef2 r2 = packed_mref<NF>(ref[q]);
@@ -406,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
                     float4 pr[2 * RF4];
 #pragma unroll
                     for (int m = 0; m < 2 * RF4; ++m) pr[m] = rec[i * 2 * RF4 + m];
-                    mpair_far2<KIND, NORM, NF>(r2, pr, k2, kt2, acc);
+                    mpair_far2<KIND, NORM, NF>(r2, pr, k2, acc);
                 }
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -660,7 +614,6 @@ int mplan(const rsi_stage& st, int nf, const double* ks, int64_t n_src, int64_t 
         const double k = f < nf ? ks[f] : ks[0];
         a.kh[f] = float(k);
         a.kl[f] = float(k - double(a.kh[f]));
-        a.kt[f] = float(k / (2.0 * M_PI));
     }
     a.tp = two_pi_split();
     const int tpt = a.packed ? 1 : kMTpt;
