@@ -470,6 +470,99 @@ int rsi_nn_gemm_carrier(const void *a_bf16, const void *b_bf16, int32_t M, int32
 int rsi_nn_carrier_coeffs(const double *params, int32_t batch, double c1, double c2, double *carrier,
                           float *params_f32, void *stream);
 
+/* ---- the surrogate's coordinate network (step a9; not in the paper) ------- */
+/* The surrogate evaluates one network row per (field, pixel): its inputs are
+ * built from the field's parameters (x-offset, tilt, water path L, frequency
+ * f, image depth d; f64 [field][5]) and the pixel's place in the window, its
+ * three outputs are the pixel's carrier-demodulated field divided by the
+ * field's RMS (re, im) and the log of that RMS.  Row inputs c (9 values),
+ * with x from the point where the transducer axis meets the interface and z
+ * below the interface (the window's top edge lies d below it):
+ *   sg = sign(tilt), a1 = |tilt|, x = sg (window x), z = d + (window z),
+ *   th = asin(min(1, (c2/c1) sin a1))                (Snell's law),
+ *   s = x sin th + z cos th, t = x cos th - z sin th  (refracted-axis frame),
+ *   q = a^2 f / (c1 (L + (c2/c1) max(s, 0)))          (Fresnel number),
+ *   c = [n(a1), n(L), n(f), n(d), x/S0, 2 (zw - z0)/Wz - 1, s/S0, t/S0, ln q],
+ * n(v) = 2 (v - lo)/(hi - lo) - 1 over box_lo/box_hi, S0 = (x1 - x0)/2; the
+ * network input is [sin(pi B c), cos(pi B c), c, 0 x 7] (bf16, 2F + 16
+ * wide), then `depth` SiLU layers of `width` and a linear head of 3.       */
+#define RSI_NN_IN 9
+#define RSI_NN_MAX_DEPTH 8
+typedef struct rsi_nn_net {
+    int32_t n_freq;      /* F: input rows are 2F + 16 wide, a multiple of 64     */
+    int32_t width;       /* hidden width, a multiple of 128                        */
+    int32_t depth;       /* hidden layers, 1 .. RSI_NN_MAX_DEPTH                   */
+    int32_t rows;        /* rows per forward / backward call, a multiple of 128    */
+    int32_t engine;      /* enum rsi_nn_engine (the hidden layers' GEMMs)          */
+    int32_t reserved;
+    double c1, c2;       /* sound speeds before / after the interface (m/s)        */
+    double a;            /* piston radius (m)                                      */
+    double box_lo[4], box_hi[4]; /* box of (|tilt|, L, f, d) for n()               */
+    rsi_grid window;     /* window in relative coordinates (see above)             */
+    const float *fmat;   /* device, f32 [F][9]: the Fourier matrix B               */
+} rsi_nn_net;
+
+/* Flat parameter buffers (f32 master weights, Adam moments, gradients: each
+ * rsi_nn_param_elems() floats; their bf16 copy the same count of bf16):
+ * layer l = 0 .. depth - 1 holds W_l [width][in_l] then b_l [width] (in_0 =
+ * 2F + 16, else width), layer `depth` the head W [3][width] then b [3]; every
+ * segment starts on a multiple of 64 elements.  rsi_nn_param_offset gives
+ * the element offset of W (bias = 0) or b (bias = 1) of a layer; -1 if the
+ * net or the layer is invalid.                                              */
+int64_t rsi_nn_param_elems(const rsi_nn_net *net);
+int64_t rsi_nn_param_offset(const rsi_nn_net *net, int32_t layer, int32_t bias);
+/* Bytes of the activation workspace of one forward + backward of `rows`
+ * rows (inputs, pre-activations, activations, head outputs, targets, the
+ * backward's buffers and split-K partial sums); 0 for an invalid net.       */
+size_t rsi_nn_act_bytes(const rsi_nn_net *net);
+
+enum rsi_nn_rows_mode {
+    RSI_NN_ROWS_RANDOM = 0, /* row r: a (field, pixel) pair drawn from SplitMix64
+                               (Steele, Lea & Flood 2014) at (seed, r): uniform
+                               over the n_fields x nx nz pairs               */
+    RSI_NN_ROWS_PIXELS = 1  /* row r: pair first + r, field-major: field
+                               (first + r) / (nx nz), pixel the remainder      */
+};
+/* Network input rows into the workspace `act`; with targets (f32
+ * [n_fields][nx nz][2], the demodulated field over its RMS) and log_rms (f32
+ * [n_fields]) also the rows' targets (re, im, log rms, 0) for
+ * rsi_nn_backward.  seed_dev (device, optional) overrides `seed` with a
+ * value read when the kernel runs, so that a captured training step draws new
+ * rows on every replay.  Rows past the last pair (PIXELS mode) repeat it.    */
+int rsi_nn_rows(const rsi_nn_net *net, const double *params, int64_t n_fields, int32_t mode, uint64_t seed,
+                const uint64_t *seed_dev, int64_t first, const float *targets, const float *log_rms, void *act,
+                size_t act_bytes, void *stream);
+/* Forward pass of the rows in `act`: the hidden layers on the tensor cores
+ * (bf16 weights w16, f32 biases from w32), the head in f32; head outputs
+ * y (f32 [rows][4], the fourth 0) are written to `act` and, if y is not
+ * NULL, copied to y.                                                        */
+int rsi_nn_forward(const rsi_nn_net *net, const void *w16, const float *w32, void *act, size_t act_bytes,
+                   float *y, void *stream);
+/* Backward pass after rsi_nn_forward and rsi_nn_rows with targets: gradients
+ * of loss = sum over rows and outputs of (y - t)^2 / (4 rows) into grad (f32,
+ * flat, every parameter overwritten); *loss_dev (device f32) receives the
+ * loss.                                                                     */
+int rsi_nn_backward(const rsi_nn_net *net, const void *w16, const float *w32, void *act, size_t act_bytes,
+                    float *grad, float *loss_dev, void *stream);
+/* One Adam step on every parameter (flat buffers) with the schedule in
+ * device memory (hyper: lr, 1 - beta1^t, 1 - beta2^t); refreshes w16.       */
+int rsi_nn_adam_step(const rsi_nn_net *net, float *w32, float *m, float *v, const float *grad, void *w16,
+                     const float *hyper, float beta1, float beta2, float eps, void *stream);
+/* Training targets of n_fields images (complex64 [n][nz][nx], e.g. from the
+ * RSI path): each image times exp(-i psi) (psi as in rsi_nn_infer) divided by
+ * its RMS over the window -> targets (f32 [n][nx nz][2]), and the log of that
+ * RMS -> log_rms (f32 [n]).  carrier (f64 [n][4]), params_f32 (f32 [n][5])
+ * and env (f32 [n][nx nz][2]) are scratch.                                  */
+int rsi_nn_targets(const rsi_nn_net *net, const double *params, int32_t n_fields, const float *images,
+                   double *carrier, float *params_f32, float *env, float *targets, float *log_rms, void *stream);
+/* Images of n_fields parameter rows (f64 [n][5]): for each field, its
+ * nx nz rows through the network (rows must be a multiple of nx nz), then
+ * exp(mean log rms) (re + i im) exp(i psi) with psi the refracted plane
+ * wave's phase k1 L + k2 (S x + C z) (S = (c2/c1) sin tilt, C = sqrt(max(0,
+ * 1 - S^2))).  out: complex64 [n][nz][nx]; carrier: f64 [n][4] scratch.    */
+int rsi_nn_infer(const rsi_nn_net *net, const void *w16, const float *w32, const double *params, int32_t n_fields,
+                 void *act, size_t act_bytes, double *carrier, float *out, void *stream);
+
 /* ---- measurement hooks (no counterpart in the paper) --------------------- */
 /* Number of kernels this library has enqueued in this process.             */
 uint64_t rsi_launch_count(void);

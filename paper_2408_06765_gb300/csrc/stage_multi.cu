@@ -34,7 +34,9 @@ struct MultiArgs {
     TgtView tgt;
     float kh[kMaxNF], kl[kMaxNF];
     TwoPiSplit tp;
-    double2* out;  // [splits][nf][n_tgt] partial sums, or the fields [nf][n_tgt]
+    double2* out;    // [splits][nf][n_tgt] partial sums, or the fields [nf][n_tgt]
+    double2* field;  // the fields [nf][n_tgt] (the last split of a target block sums into it)
+    unsigned* done;  // per target block: splits finished (zeroed before the launch)
     int* status;
 };
 
@@ -297,14 +299,18 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
     constexpr int RF4 = mrec_f4<KIND, NORM, NF>();
     constexpr int TPT = PK ? 1 : kMTpt;
     const int tid = threadIdx.x;
-    const int split = blockIdx.y;
+    // one-dimensional grid, the splits of a target block adjacent: they run
+    // at about the same time, so their partial sums are still in L2 when the
+    // last of them adds them up
+    const int split = int(blockIdx.x % unsigned(a.splits));
+    const int64_t tblock = int64_t(blockIdx.x / unsigned(a.splits));
     const int t_begin = split * a.tiles_per_split;
     const int ntile = max(0, min(a.n_tiles, t_begin + a.tiles_per_split) - t_begin);
     const uint32_t tb = uint32_t(a.tile_bytes);
     int64_t jt[TPT];
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
-        const int64_t j = int64_t(blockIdx.x) * TPT * kThreads + int64_t(q) * kThreads + tid;
+        const int64_t j = tblock * TPT * kThreads + int64_t(q) * kThreads + tid;
         jt[q] = j < a.n_tgt ? j : a.n_tgt - 1;
     }
     if (tid == 0)
@@ -426,15 +432,62 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
     double2* out = a.out + (a.splits > 1 ? size_t(split) * size_t(NF) * size_t(a.n_tgt) : 0);
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
-        const int64_t j = int64_t(blockIdx.x) * TPT * kThreads + int64_t(q) * kThreads + tid;
+        const int64_t j = tblock * TPT * kThreads + int64_t(q) * kThreads + tid;
         if (j < a.n_tgt)
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const double re = double(hr[q][f]) + double(lr[q][f]);
                 const double im = double(hi[q][f]) + double(li[q][f]);
-                if (!isfinite(re) || !isfinite(im)) atomicExch(a.status, RSI_DEV_NONFINITE);
+                if (a.splits == 1 && (!isfinite(re) || !isfinite(im))) atomicExch(a.status, RSI_DEV_NONFINITE);
                 out[size_t(f) * size_t(a.n_tgt) + size_t(j)] = make_double2(re, im);
             }
+    }
+    if (a.splits == 1) return;
+    // The last split of this target block to finish adds the partial sums of
+    // all splits in split order (Neumaier, FP64: the arithmetic of
+    // reduce_partials_kernel), then drops their lines from L2 unwritten.  No
+    // CTA waits for another: whichever finishes last does the sum.
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(a.done + tblock, 1u) == unsigned(a.splits - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < TPT; ++q) {
+        const int64_t j = tblock * TPT * kThreads + int64_t(q) * kThreads + tid;
+        if (j >= a.n_tgt) continue;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            double sr = 0.0, cr = 0.0, si = 0.0, ci = 0.0;
+            for (int sp = 0; sp < a.splits; ++sp) {
+                const double2 v = __ldcg(a.out + (size_t(sp) * NF + f) * size_t(a.n_tgt) + size_t(j));
+                double t = sr + v.x;
+                cr += (fabs(sr) >= fabs(v.x)) ? (sr - t) + v.x : (v.x - t) + sr;
+                sr = t;
+                t = si + v.y;
+                ci += (fabs(si) >= fabs(v.y)) ? (si - t) + v.y : (v.y - t) + si;
+                si = t;
+            }
+            const double re = sr + cr, im = si + ci;
+            if (!isfinite(re) || !isfinite(im)) atomicExch(a.status, RSI_DEV_NONFINITE);
+            a.field[size_t(f) * size_t(a.n_tgt) + size_t(j)] = make_double2(re, im);
+        }
+    }
+    __syncthreads();
+    // every split's partial sums of this block are read: discard their L2
+    // lines (128 bytes = 8 targets) so that they are never written back
+    const int64_t j0 = tblock * TPT * kThreads;
+    const int64_t nj = min(int64_t(TPT * kThreads), a.n_tgt - j0);
+    if ((j0 * int64_t(sizeof(double2))) % 128 == 0) {
+        const int lines_f = int(nj / 8);  // whole lines of one (split, frequency) row
+        for (int e = tid; e < a.splits * NF * lines_f; e += kThreads) {
+            const int row = e / lines_f, ln = e - row * lines_f;
+            const double2* ptr = a.out + size_t(row) * size_t(a.n_tgt) + size_t(j0) + size_t(ln) * 8;
+            if ((reinterpret_cast<uintptr_t>(ptr) & 127) == 0)
+                asm volatile("discard.global.L2 [%0], 128;" ::"l"(ptr) : "memory");
+        }
     }
 }
 
@@ -543,7 +596,8 @@ int mlaunch(const MultiArgs& a, cudaStream_t s, bool occ, int* occ_out) {
         return RSI_OK;
     }
     const int64_t per_block = int64_t(kThreads) * (PK ? 1 : kMTpt);
-    dim3 grid(unsigned((a.n_tgt + per_block - 1) / per_block), unsigned(a.splits));
+    const int64_t nblk = (a.n_tgt + per_block - 1) / per_block;
+    dim3 grid(unsigned(nblk * a.splits));
     kern<<<grid, kThreads, msmem(a.tile_bytes), s>>>(a);
     RSI_CHECK_LAUNCH("stage_multi_kernel");
     return RSI_OK;
@@ -570,6 +624,7 @@ int mdispatch(const MultiArgs& a, cudaStream_t s, bool occ, int* o) {
 
 struct MPlan {
     int S, n_tiles, tiles_per_split, splits;
+    int64_t blocks;  // target blocks
     size_t tile_bytes, tiles_bytes, partial_bytes;
 };
 
@@ -639,8 +694,11 @@ int mplan(const rsi_stage& st, int nf, const double* ks, int64_t n_src, int64_t 
     if (splits > 65535) return rsi_fail(RSI_E_INVAL, "too many splits");
     p.tiles_per_split = (p.n_tiles + splits - 1) / splits;
     p.splits = (p.n_tiles + p.tiles_per_split - 1) / p.tiles_per_split;
-    p.partial_bytes =
-        p.splits > 1 ? align256(size_t(p.splits) * size_t(nf) * size_t(n_tgt) * sizeof(double2)) : 0;
+    // partial sums [splits][nf][n_tgt], then one completion counter per target block
+    p.partial_bytes = p.splits > 1 ? align256(size_t(p.splits) * size_t(nf) * size_t(n_tgt) * sizeof(double2)) +
+                                         align256(size_t(blocks) * sizeof(unsigned))
+                                   : 0;
+    p.blocks = blocks;
     a.tiles_per_split = p.tiles_per_split;
     a.splits = p.splits;
     return RSI_OK;
@@ -692,12 +750,19 @@ extern "C" int rsi_propagate_stage_multi(const rsi_stage* st, int32_t nf, const 
     a.tgt = {tgt.xh, tgt.xl, tgt.yh, tgt.yl, tgt.zh, tgt.zl, tgt.x, tgt.y, tgt.z};
     double2* field = reinterpret_cast<double2*>(tgt_field);
     a.out = p.splits > 1 ? reinterpret_cast<double2*>(tiles + p.tiles_bytes) : field;
+    a.field = field;
+    a.done = nullptr;
+    if (p.splits > 1) {
+        const size_t part = align256(size_t(p.splits) * size_t(nf) * size_t(n_tgt) * sizeof(double2));
+        a.done = reinterpret_cast<unsigned*>(tiles + p.tiles_bytes + part);
+        RSI_CUDA_TRY(cudaMemsetAsync(a.done, 0, size_t(p.blocks) * sizeof(unsigned), s),
+                     "rsi_propagate_stage_multi: clear the completion counters");
+    }
     a.status = status;
     TimingScope tsc = timing_begin(s);
     int o = 0;
     rc = mdispatch(a, s, false, &o);
     if (rc != RSI_OK) return rc;
     timing_end(tsc, st->kind, double(nf) * double(n_src) * double(n_tgt), s);
-    if (p.splits > 1) return launch_reduce_partials(a.out, p.splits, int64_t(nf) * n_tgt, field, status, s);
     return RSI_OK;
 }

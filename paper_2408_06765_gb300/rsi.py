@@ -49,7 +49,9 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
            "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_adam_dev", "rsi_nn_cast_bf16", "rsi_nn_carrier", "rsi_nn_gemm_carrier", "rsi_nn_carrier_coeffs",
-           "rsi_selftest_wait_timeout"]
+           "rsi_selftest_wait_timeout", "rsi_nn_param_elems", "rsi_nn_param_offset", "rsi_nn_act_bytes",
+           "rsi_nn_rows", "rsi_nn_forward", "rsi_nn_backward", "rsi_nn_adam_step", "rsi_nn_targets",
+           "rsi_nn_infer"]
 NN_EPI = {"f32": 0, "bias_silu": 1, "dsilu": 2}
 NN_ENGINE = {"mma_sync": 0, "tcgen05": 1}
 UB = {"ffma": 0, "rsqrt": 1, "sin": 2, "dfma": 3}
@@ -87,6 +89,14 @@ class Raytrace(ctypes.Structure):
                 ("c1", ctypes.c_double), ("rho2", ctypes.c_double), ("c2", ctypes.c_double),
                 ("z_interface", ctypes.c_double), ("v0", ctypes.c_double), ("tile", ctypes.c_int32),
                 ("splits", ctypes.c_int32), ("newton", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class NNNet(ctypes.Structure):
+    _fields_ = [("n_freq", ctypes.c_int32), ("width", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("rows", ctypes.c_int32), ("engine", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("c1", ctypes.c_double), ("c2", ctypes.c_double), ("a", ctypes.c_double),
+                ("box_lo", ctypes.c_double * 4), ("box_hi", ctypes.c_double * 4), ("window", Grid),
+                ("fmat", ctypes.c_void_p)]
 
 
 class BatchInstance(ctypes.Structure):
@@ -166,6 +176,19 @@ def load(path: str | None = None):
         L.rsi_nn_cast_bf16.argtypes = [vp, i64, vp, vp]
         L.rsi_nn_carrier.argtypes = [vp, i32, ctypes.POINTER(Grid), i32, ctypes.c_float, vp, vp, vp]
         L.rsi_selftest_wait_timeout.argtypes = [i64, vp]
+        pn = ctypes.POINTER(NNNet)
+        L.rsi_nn_param_elems.restype = i64
+        L.rsi_nn_param_elems.argtypes = [pn]
+        L.rsi_nn_param_offset.restype = i64
+        L.rsi_nn_param_offset.argtypes = [pn, i32, i32]
+        L.rsi_nn_act_bytes.restype = sz
+        L.rsi_nn_act_bytes.argtypes = [pn]
+        L.rsi_nn_rows.argtypes = [pn, vp, i64, i32, u64, vp, i64, vp, vp, vp, sz, vp]
+        L.rsi_nn_forward.argtypes = [pn, vp, vp, vp, sz, vp, vp]
+        L.rsi_nn_backward.argtypes = [pn, vp, vp, vp, sz, vp, vp, vp]
+        L.rsi_nn_adam_step.argtypes = [pn, vp, vp, vp, vp, vp, vp, f32, f32, f32, vp]
+        L.rsi_nn_targets.argtypes = [pn, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.rsi_nn_infer.argtypes = [pn, vp, vp, vp, i32, vp, sz, vp, vp, vp]
         _lib = L
         return L
 
@@ -764,3 +787,75 @@ def nn_carrier(carrier, window: dict, sign: int, x, out, stream=None, scale: flo
     _check(load().rsi_nn_carrier(_ptr(carrier), carrier.shape[0], ctypes.byref(G), int(sign), float(scale),
                                  _ptr(x), _ptr(out), _stream(stream)), "rsi_nn_carrier")
     return out
+
+
+# ---------------------------------------------------------------------------
+# the surrogate's coordinate network (rsi_nn_rows / forward / backward /
+# adam_step / targets / infer)
+# ---------------------------------------------------------------------------
+NN_ROWS = {"random": 0, "pixels": 1}
+
+
+def nn_net_struct(n_freq: int, width: int, depth: int, rows: int, engine: str, c1: float, c2: float, a: float,
+                  box_lo, box_hi, window: dict, fmat) -> NNNet:
+    n = NNNet()
+    n.n_freq, n.width, n.depth, n.rows = int(n_freq), int(width), int(depth), int(rows)
+    n.engine = NN_ENGINE[engine]
+    n.c1, n.c2, n.a = float(c1), float(c2), float(a)
+    for k in range(4):
+        n.box_lo[k], n.box_hi[k] = float(box_lo[k]), float(box_hi[k])
+    n.window = grid_struct(window)
+    n.fmat = fmat.data_ptr()
+    return n
+
+
+def nn_param_elems(net: NNNet) -> int:
+    v = int(load().rsi_nn_param_elems(ctypes.byref(net)))
+    if v < 0:
+        raise RSIError("rsi_nn_param_elems", -1, load().rsi_last_error().decode(errors="replace"))
+    return v
+
+
+def nn_param_offset(net: NNNet, layer: int, bias: bool) -> int:
+    return int(load().rsi_nn_param_offset(ctypes.byref(net), int(layer), 1 if bias else 0))
+
+
+def nn_act_bytes(net: NNNet) -> int:
+    v = int(load().rsi_nn_act_bytes(ctypes.byref(net)))
+    if v == 0:
+        raise RSIError("rsi_nn_act_bytes", -1, load().rsi_last_error().decode(errors="replace"))
+    return v
+
+
+def nn_rows(net: NNNet, params64, n_fields: int, mode: str, act, seed: int = 0, seed_dev=None, first: int = 0,
+            targets=None, log_rms=None, stream=None):
+    _check(load().rsi_nn_rows(ctypes.byref(net), _ptr(params64), int(n_fields), NN_ROWS[mode],
+                              int(seed) & (2**64 - 1), _ptr(seed_dev), int(first), _ptr(targets), _ptr(log_rms),
+                              _ptr(act), act.numel(), _stream(stream)), "rsi_nn_rows")
+
+
+def nn_forward(net: NNNet, w16, w32, act, y=None, stream=None):
+    _check(load().rsi_nn_forward(ctypes.byref(net), _ptr(w16), _ptr(w32), _ptr(act), act.numel(), _ptr(y),
+                                 _stream(stream)), "rsi_nn_forward")
+
+
+def nn_backward(net: NNNet, w16, w32, act, grad, loss_dev, stream=None):
+    _check(load().rsi_nn_backward(ctypes.byref(net), _ptr(w16), _ptr(w32), _ptr(act), act.numel(), _ptr(grad),
+                                  _ptr(loss_dev), _stream(stream)), "rsi_nn_backward")
+
+
+def nn_adam_step(net: NNNet, w32, m, v, grad, w16, hyper, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().rsi_nn_adam_step(ctypes.byref(net), _ptr(w32), _ptr(m), _ptr(v), _ptr(grad), _ptr(w16),
+                                   _ptr(hyper), float(beta1), float(beta2), float(eps), _stream(stream)),
+           "rsi_nn_adam_step")
+
+
+def nn_targets(net: NNNet, params64, images, carrier, params32, env, targets, log_rms, stream=None):
+    _check(load().rsi_nn_targets(ctypes.byref(net), _ptr(params64), int(params64.shape[0]), _ptr(images),
+                                 _ptr(carrier), _ptr(params32), _ptr(env), _ptr(targets), _ptr(log_rms),
+                                 _stream(stream)), "rsi_nn_targets")
+
+
+def nn_infer(net: NNNet, w16, w32, params64, act, carrier, out, stream=None):
+    _check(load().rsi_nn_infer(ctypes.byref(net), _ptr(w16), _ptr(w32), _ptr(params64), int(params64.shape[0]),
+                               _ptr(act), act.numel(), _ptr(carrier), _ptr(out), _stream(stream)), "rsi_nn_infer")

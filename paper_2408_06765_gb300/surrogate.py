@@ -1,21 +1,24 @@
-"""Learned surrogate of the RSI chain (not in the paper): a Fourier-feature MLP
-that maps (x-offset, tilt, water path, frequency, image depth) to the
-128 x 128 field image of one water -> steel chain, trained on images the GPU
-RSI path computes, with the RSI path as its fallback and the measure of its error.
+"""Learned surrogate of the RSI chain (not in the paper): a coordinate network
+that gives the field image of one water -> steel chain for the inputs
+(x-offset, tilt, water path L, frequency f, image depth d), trained on images
+the GPU RSI path computes, with the RSI path as its fallback and the measure
+of its error.
 
-Every numerical step runs in librsi.so (rsi_nn_* kernels: BF16 tensor-core
-GEMMs with FP32 accumulation and fused bias/SiLU epilogues, FP32 master
-weights, Adam); this module sequences the calls and keeps the buffers.
+The network is evaluated per pixel (include/rsi.h, rsi_nn_net): each row
+holds the field's parameters and the pixel's place in the window, recast in
+the refracted beam's frame (Snell's law) and with the Fresnel number of the
+equivalent water path; a Fourier-feature MLP (BF16 tensor-core GEMMs with FP32
+accumulation) returns the pixel's carrier-demodulated field over the field's
+RMS and the log of that RMS.  An image's pixels are not tied to a fixed
+output basis, so a family of beams that turn through 0-90 degrees in the
+steel, narrow with frequency and move with the window stays within reach: a
+linear output layer of rank 512 over the 128 x 128 pixels leaves 12-19% of
+held-out fields unexplained however it is trained.
 
-Network (same definition as the FP64 oracle, oracle/mlp.py):
-    u = 2 (p - lo)/(hi - lo) - 1;  h0 = [sin(pi B u), cos(pi B u)]
-    h_l = silu(W_l h_{l-1} + b_l), l = 1..depth;  y = W_out h_depth + b_out
-The output y is the image times exp(-i psi), psi the phase of the refracted
-plane wave: psi = k1 L + k2 (s x + c (z + depth)) with L the water path,
-s = (c2/c1) sin(tilt) and c = sqrt(1 - s^2) (0 past the critical angle), x, z
-measured from the point where the axis meets the interface and from the
-window's top edge; real and imaginary parts interleaved and divided by a
-fixed amplitude scale.
+Every numerical step runs in librsi.so (rsi_nn_rows, rsi_nn_forward,
+rsi_nn_backward, rsi_nn_adam_step, rsi_nn_targets, rsi_nn_infer); this module
+keeps the buffers, the training schedule and the fallback gate.  The FP64
+oracle of the network is oracle/coordnet.py.
 """
 from __future__ import annotations
 
@@ -28,14 +31,204 @@ from . import rsi
 from . import workloads as W
 
 C1, C2 = W.WATER["c"], W.STEEL["c"]
+A_PISTON = 6.35e-3
+CRIT = math.asin(C1 / C2)  # critical angle of the water -> steel L wave
+# box of (|tilt|, L, f, d) for the row inputs, and of the five inputs
+BOX_LO = (0.0, 20e-3, 2e6, 1e-3)
+BOX_HI = (math.radians(15.0), 60e-3, 10e6, 20e-3)
 LO = np.array([-10e-3, math.radians(-15.0), 20e-3, 2e6, 1e-3])
 HI = np.array([10e-3, math.radians(15.0), 60e-3, 10e6, 20e-3])
 WINDOW = {"x0": -20e-3, "x1": 20e-3, "nx": 128, "z0": 0.0, "z1": 40e-3, "nz": 128}
+NPIX = WINDOW["nx"] * WINDOW["nz"]
 
 
+def fourier_matrix(n_freq: int, sigmas=(1.0, 4.0, 16.0), seed: int = 0) -> np.ndarray:
+    """B [F][9]: Gaussian rows, split as evenly as possible over the scales."""
+    rng = np.random.default_rng(seed)
+    parts = np.array_split(np.arange(n_freq), len(sigmas))
+    B = np.zeros((n_freq, rsi_in()), np.float32)
+    for idx, sg in zip(parts, sigmas):
+        B[idx] = rng.normal(0.0, sg, size=(len(idx), rsi_in()))
+    return B
+
+
+def rsi_in() -> int:
+    return 9
+
+
+class CoordNet:
+    """Parameters (flat buffers: f32 weights, Adam moments, gradient, bf16
+    copy), Fourier matrix and activation workspace of the coordinate network."""
+
+    def __init__(self, n_freq=248, width=512, depth=5, rows=65536, sigmas=(1.0, 4.0, 16.0), seed=0,
+                 engine="tcgen05", device="cuda"):
+        self.device = device
+        self.n_freq, self.width, self.depth, self.rows = n_freq, width, depth, rows
+        self.fmat = torch.tensor(fourier_matrix(n_freq, sigmas, seed), device=device)
+        self.net = rsi.nn_net_struct(n_freq, width, depth, rows, engine, C1, C2, A_PISTON, BOX_LO, BOX_HI,
+                                     WINDOW, self.fmat)
+        self.elems = rsi.nn_param_elems(self.net)
+        f32 = dict(dtype=torch.float32, device=device)
+        self.w = torch.zeros(self.elems, **f32)
+        self.m = torch.zeros(self.elems, **f32)
+        self.v = torch.zeros(self.elems, **f32)
+        self.g = torch.zeros(self.elems, **f32)
+        self.w16 = torch.zeros(self.elems, dtype=torch.bfloat16, device=device)
+        rng = np.random.default_rng(seed + 1)
+        for l in range(depth + 1):
+            out, inp = self.shape(l)
+            std = math.sqrt(2.0 / inp) if l < depth else math.sqrt(1.0 / inp)
+            self.layer(l).copy_(torch.tensor(rng.normal(0.0, std, size=(out, inp)), **f32))
+        rsi.nn_cast_bf16(self.w, self.w16)
+        self.act = torch.empty(rsi.nn_act_bytes(self.net), dtype=torch.uint8, device=device)
+        self.y = torch.zeros(rows, 4, **f32)
+        self.loss = torch.zeros(1, **f32)
+        self.hyper = torch.zeros(3, **f32)
+        self.seed = torch.zeros(1, dtype=torch.int64, device=device)
+        self.step_count = 0
+        self._carrier = None
+
+    def shape(self, l: int):
+        inp = 2 * self.n_freq + 16 if l == 0 else self.width
+        return (3 if l == self.depth else self.width), inp
+
+    def layer(self, l: int, bias: bool = False, buf=None) -> torch.Tensor:
+        """View of W_l ([out][in]) or b_l in a flat buffer (default: the weights)."""
+        buf = self.w if buf is None else buf
+        out, inp = self.shape(l)
+        o = rsi.nn_param_offset(self.net, l, bias)
+        return buf[o:o + out] if bias else buf[o:o + out * inp].view(out, inp)
+
+    # -- one training step ----------------------------------------------------
+    def rows_random(self, params64, targets, log_rms, seed: int | None = None):
+        """Rows drawn at random over the training fields (seed: the device
+        counter when None)."""
+        rsi.nn_rows(self.net, params64, params64.shape[0], "random", self.act, seed=0 if seed is None else seed,
+                    seed_dev=self.seed if seed is None else None, targets=targets, log_rms=log_rms)
+
+    def forward(self):
+        rsi.nn_forward(self.net, self.w16, self.w, self.act, self.y)
+        return self.y
+
+    def backward(self):
+        rsi.nn_backward(self.net, self.w16, self.w, self.act, self.g, self.loss)
+        return self.loss
+
+    def adam(self):
+        rsi.nn_adam_step(self.net, self.w, self.m, self.v, self.g, self.w16, self.hyper)
+
+    # -- images ---------------------------------------------------------------
+    def infer(self, params64, out=None) -> torch.Tensor:
+        """Images (complex64 [n, nz, nx]) of the parameter rows (f64 [n, 5] on
+        the device); the rows per call must hold whole fields."""
+        n = params64.shape[0]
+        if out is None:
+            out = torch.empty(n, NPIX * 2, dtype=torch.float32, device=self.device)
+        if self._carrier is None or self._carrier.shape[0] < n:
+            self._carrier = torch.empty(n, 4, dtype=torch.float64, device=self.device)
+        rsi.nn_infer(self.net, self.w16, self.w, params64, self.act, self._carrier, out)
+        return torch.view_as_complex(out.view(n, WINDOW["nz"], WINDOW["nx"], 2))
+
+
+class TrainingSet:
+    """Training targets of RSI images on the device: each image demodulated by
+    the refracted plane wave and divided by its RMS, and the log of the RMS
+    (rsi_nn_targets)."""
+
+    def __init__(self, net: CoordNet, params, images):
+        dev = net.device
+        self.params = torch.as_tensor(np.asarray(params, np.float64), device=dev)
+        n = self.params.shape[0]
+        self.targets = torch.empty(n, NPIX * 2, dtype=torch.float32, device=dev)
+        self.log_rms = torch.empty(n, dtype=torch.float32, device=dev)
+        carrier = torch.empty(n, 4, dtype=torch.float64, device=dev)
+        p32 = torch.empty(n, 5, dtype=torch.float32, device=dev)
+        env = torch.empty_like(self.targets)
+        imgs = torch.view_as_real(images.contiguous()).reshape(n, -1)
+        rsi.nn_targets(net.net, self.params, imgs, carrier, p32, env, self.targets, self.log_rms)
+
+
+class GraphedTrainer:
+    """Training steps (random rows, forward, backward, Adam) replayed from one
+    CUDA graph.  Each step first copies its learning-rate row and row seed
+    from schedules held on the device; nothing waits for the host.  The net
+    must have taken one eager step first (kernel set-up outside the capture)."""
+
+    BETA1, BETA2 = 0.9, 0.999
+
+    def __init__(self, net: CoordNet, tset: TrainingSet, lrs, seeds):
+        if net.step_count < 1:
+            raise ValueError("GraphedTrainer needs one eager training step first")
+        self.net, self.tset = net, tset
+        dev = net.device
+        b1, b2 = float(np.float32(self.BETA1)), float(np.float32(self.BETA2))
+        t0 = net.step_count + 1
+        rows = [(lr, 1.0 - b1 ** (t0 + i), 1.0 - b2 ** (t0 + i)) for i, lr in enumerate(lrs)]
+        self.sched = torch.tensor(np.asarray(rows, np.float32), device=dev)
+        self.seeds = torch.tensor(np.asarray(seeds, np.int64), device=dev)
+        self.i = 0
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            net.rows_random(tset.params, tset.targets, tset.log_rms)
+            net.forward()
+            net.backward()
+            net.adam()
+
+    def step(self) -> torch.Tensor:
+        if self.i >= len(self.sched):
+            raise RuntimeError("GraphedTrainer: the learning-rate schedule is exhausted")
+        self.net.hyper.copy_(self.sched[self.i])
+        self.net.seed.copy_(self.seeds[self.i:self.i + 1])
+        self.graph.replay()
+        self.i += 1
+        self.net.step_count += 1
+        return self.net.loss
+
+
+def train(net: CoordNet, tset: TrainingSet, steps: int, lr: float = 1e-3, warmup: int = 500, seed: int = 0,
+          log=None, graph: bool = True):
+    """Adam with a linear warm-up and cosine decay on random rows of the
+    training set; with graph=True every step after the first replays one CUDA
+    graph (GraphedTrainer).  Returns the losses every steps/20 steps."""
+    lrs = [lr * min(1.0, (s + 1) / max(1, warmup)) * 0.5 * (1.0 + math.cos(math.pi * s / max(1, steps)))
+           for s in range(steps)]
+    b1, b2 = float(np.float32(GraphedTrainer.BETA1)), float(np.float32(GraphedTrainer.BETA2))
+    seeds = np.random.default_rng(seed + 12345).integers(0, 2**62, size=steps, dtype=np.int64)
+    losses = []
+    # first step eagerly (one-time set-up of every kernel), then the graph
+    net.hyper.copy_(torch.tensor([lrs[0], 1.0 - b1 ** (net.step_count + 1), 1.0 - b2 ** (net.step_count + 1)]))
+    net.rows_random(tset.params, tset.targets, tset.log_rms, seed=int(seeds[0]))
+    net.forward()
+    net.backward()
+    net.adam()
+    net.step_count += 1
+    trainer = GraphedTrainer(net, tset, lrs[1:], seeds[1:]) if graph and steps > 1 else None
+    every = max(1, steps // 20)
+    for s in range(1, steps):
+        if trainer is not None:
+            loss = trainer.step()
+        else:
+            b1t, b2t = 1.0 - b1 ** (net.step_count + 1), 1.0 - b2 ** (net.step_count + 1)
+            net.hyper.copy_(torch.tensor([lrs[s], b1t, b2t]))
+            net.rows_random(tset.params, tset.targets, tset.log_rms, seed=int(seeds[s]))
+            net.forward()
+            loss = net.backward()
+            net.adam()
+            net.step_count += 1
+        if s % every == 0 or s == steps - 1:
+            losses.append(float(loss.item()))
+            if log:
+                log(s, losses[-1])
+    return losses
+
+
+# ---------------------------------------------------------------------------
+# the carrier: the refracted plane wave below the interface
+# ---------------------------------------------------------------------------
 def carrier_coeffs(params) -> np.ndarray:
-    """(kx, kz, phi0, 0) per sample: psi = kx x + kz z + phi0 is the phase of
-    the refracted plane wave (water path phase k1 L included)."""
+    """(kx, kz, phi0, 0) per parameter row (numpy, FP64): psi = kx x + kz z +
+    phi0 is the refracted plane wave's phase, x from the axis hit point and z
+    below the window's top edge (the water path's phase k1 L included)."""
     p = np.atleast_2d(np.asarray(params, np.float64))
     k1 = 2 * np.pi * p[:, 3] / C1
     k2 = 2 * np.pi * p[:, 3] / C2
@@ -44,160 +237,34 @@ def carrier_coeffs(params) -> np.ndarray:
     return np.stack([k2 * s, k2 * c, k1 * p[:, 2] + k2 * c * p[:, 4], np.zeros(len(p))], axis=1)
 
 
-class MLP:
-    """Weights, Adam state and activation buffers of the surrogate."""
+def _coeffs(params, device):
+    host = torch.from_numpy(carrier_coeffs(params))
+    if torch.device(device).type != "cuda":
+        return host.to(device)
+    return host.pin_memory().to(device, non_blocking=True)
 
-    def __init__(self, n_freq=128, width=512, depth=4, n_out=2 * 128 * 128, batch=256, seed=0,
-                 sigma_b=2.0, device="cuda", engine="tcgen05"):
-        self.n_in, self.F, self.width, self.depth, self.n_out = 5, n_freq, width, depth, n_out
-        self.batch = batch
-        self.engine = engine  # GEMM engine: "tcgen05" (tensor memory) or "mma_sync"
-        self.device = device
-        rng = np.random.default_rng(seed)
-        dims = [2 * n_freq] + [width] * depth + [n_out]
-        self.dims = dims
-        f32 = dict(dtype=torch.float32, device=device)
-        # Every weight and bias (and its moments, gradient and bf16 copy) is a
-        # view into one flat buffer per role, segments padded to 64 elements
-        # (128-byte aligned for the GEMMs' tensor maps), so that one Adam
-        # launch updates all parameters; padding has zero gradient and stays 0.
-        pad = lambda n: (n + 63) // 64 * 64
-        shapes = [(dims[i + 1], dims[i]) for i in range(len(dims) - 1)]
-        total = sum(pad(r * c) + pad(r) for r, c in shapes)
-        self.flat = {k: torch.zeros(total, **f32) for k in ("w", "m", "v", "g")}
-        self.flat16 = torch.zeros(total, dtype=torch.bfloat16, device=device)
-        views = {k: ([], []) for k in ("w", "m", "v", "g", "h")}
-        off = 0
-        for r, c in shapes:
-            for k in ("w", "m", "v", "g", "h"):
-                buf = self.flat16 if k == "h" else self.flat[k]
-                views[k][0].append(buf[off:off + r * c].view(r, c))
-                views[k][1].append(buf[off + pad(r * c):off + pad(r * c) + r])
-            off += pad(r * c) + pad(r)
-        self.W, self.b = views["w"]
-        self.mW, self.mb = views["m"]
-        self.vW, self.vb = views["v"]
-        self.gW, self.gb = views["g"]
-        self.W16 = views["h"][0]
-        for i, (r, c) in enumerate(shapes):
-            std = math.sqrt(2.0 / dims[i]) if i < len(dims) - 2 else math.sqrt(1.0 / dims[i])
-            self.W[i].copy_(torch.tensor(rng.normal(0.0, std, size=(r, c)), **f32))
-        self.fmat = torch.tensor(rng.normal(0.0, sigma_b, size=(n_freq, 5)), **f32)
-        self.lo = torch.tensor(LO, **f32)
-        self.hi = torch.tensor(HI, **f32)
-        rsi.nn_cast_bf16(self.flat["w"], self.flat16)
-        self.step_count = 0
-        self.scale = 1.0
-        self._alloc(batch)
 
-    def _alloc(self, B):
-        d, bf = self.device, torch.bfloat16
-        self.B_alloc = B
-        self.H = [torch.empty((B, n), dtype=bf, device=d) for n in self.dims[:-1]]
-        self.Z = [torch.empty((B, n), dtype=torch.float32, device=d) for n in self.dims[1:-1]]
-        self.y = torch.empty((B, self.n_out), dtype=torch.float32, device=d)
-        self.dy = torch.empty((B, self.n_out), dtype=bf, device=d)
-        self.dZ = [torch.empty((B, n), dtype=bf, device=d) for n in self.dims[1:-1]]
-        self.HT = [torch.empty((n, B), dtype=bf, device=d) for n in self.dims[:-1]]
-        self.dyT = torch.empty((self.n_out, B), dtype=bf, device=d)
-        self.dZT = [torch.empty((n, B), dtype=bf, device=d) for n in self.dims[1:-1]]
-        self.WT = [torch.empty((w.shape[1], w.shape[0]), dtype=bf, device=d) for w in self.W]
-        self.partial = torch.empty(1024, dtype=torch.float64, device=d)
-        # split K for the backward GEMM through the output layer (few output
-        # tiles, K = n_out): about one (tcgen05, persistent) or two (mma.sync)
-        # CTAs per SM
-        if self.engine == "tcgen05":
-            tiles = (B // 128) * (self.width // (256 if self.width % 256 == 0 else 128))
-            self.splits_out = max(1, min(self.n_out // 64, 152 // max(1, tiles)))
-        else:
-            tiles = (B // 128) * (self.width // 128)
-            self.splits_out = max(1, min(self.n_out // 32, (2 * 152) // max(1, tiles)))
-        self.work = torch.empty(self.splits_out * B * self.width if self.splits_out > 1 else 1,
-                                dtype=torch.float32, device=d)
-        self.loss_buf = torch.empty(1, dtype=torch.float32, device=d)
+def demodulate(images, params, device="cuda"):
+    """Images times exp(-i psi), as interleaved f32 [n, 2 nx nz] (rsi_nn_carrier)."""
+    car = _coeffs(params, device)
+    x = torch.view_as_real(images.contiguous()).reshape(images.shape[0], -1)
+    out = torch.empty_like(x)
+    rsi.nn_carrier(car, WINDOW, -1, x, out)
+    return out
 
-    # -- forward / backward / update ------------------------------------------
-    def hidden(self, p) -> torch.Tensor:
-        """Features and hidden layers: the last hidden activations (bf16)."""
-        assert p.shape[0] == self.B_alloc
-        rsi.nn_features(p, self.lo, self.hi, self.fmat, self.H[0])
-        for l in range(self.depth):
-            rsi.nn_gemm("bias_silu", self.H[l], self.W16[l], out_f32=self.Z[l], out_bf16=self.H[l + 1],
-                        bias=self.b[l], engine=self.engine)
-        return self.H[self.depth]
 
-    def forward(self, p) -> torch.Tensor:
-        """p: f32 [B, 5] on the device (B = the allocated batch)."""
-        self.hidden(p)
-        rsi.nn_gemm("f32", self.H[self.depth], self.W16[-1], out_f32=self.y, bias=self.b[-1], engine=self.engine)
-        return self.y
-
-    def loss(self, t, grad: bool = True) -> torch.Tensor:
-        n = self.y.numel()
-        rsi.nn_loss(self.y, t, 2.0 / n, self.dy if grad else None, self.partial, self.loss_buf)
-        return self.loss_buf
-
-    def backward(self):
-        """Gradients of the mean squared error into gW, gb (after loss())."""
-        L = self.depth
-        tc = self.engine == "tcgen05"
-        # gW[L] = dy^T H[L]; dZ[L-1] = (dy W[L]) * silu'(Z[L-1]).  The tcgen05
-        # engine reads the stored matrices in either orientation; the mma.sync
-        # engine needs K-contiguous copies.
-        if tc:
-            rsi.nn_gemm("f32", self.dy, self.H[L], out_f32=self.gW[L], engine="tcgen05", a_t=True, b_t=True)
-        else:
-            rsi.nn_transpose(self.dy, self.dyT)
-            rsi.nn_transpose(self.H[L], self.HT[L])
-            rsi.nn_gemm("f32", self.dyT, self.HT[L], out_f32=self.gW[L], engine=self.engine)
-        rsi.nn_colsum(self.dy, self.gb[L])
-        if tc:
-            rsi.nn_gemm("dsilu", self.dy, self.W16[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1],
-                        splits=self.splits_out, workspace=self.work, engine="tcgen05", b_t=True)
-        else:
-            rsi.nn_transpose(self.W16[L], self.WT[L])
-            rsi.nn_gemm("dsilu", self.dy, self.WT[L], out_bf16=self.dZ[L - 1], aux=self.Z[L - 1],
-                        splits=self.splits_out, workspace=self.work, engine=self.engine)
-        for l in range(L - 1, -1, -1):
-            if tc:
-                rsi.nn_gemm("f32", self.dZ[l], self.H[l], out_f32=self.gW[l], engine="tcgen05", a_t=True, b_t=True)
-            else:
-                rsi.nn_transpose(self.dZ[l], self.dZT[l])
-                rsi.nn_transpose(self.H[l], self.HT[l])
-                rsi.nn_gemm("f32", self.dZT[l], self.HT[l], out_f32=self.gW[l], engine=self.engine)
-            rsi.nn_colsum(self.dZ[l], self.gb[l])
-            if l > 0:
-                if tc:
-                    rsi.nn_gemm("dsilu", self.dZ[l], self.W16[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1],
-                                engine="tcgen05", b_t=True)
-                else:
-                    rsi.nn_transpose(self.W16[l], self.WT[l])
-                    rsi.nn_gemm("dsilu", self.dZ[l], self.WT[l], out_bf16=self.dZ[l - 1], aux=self.Z[l - 1],
-                                engine=self.engine)
-
-    def adam(self, lr: float):
-        """One Adam step on every parameter: a single launch over the flat
-        buffers (the bf16 copy of the biases it writes is unused)."""
-        self.step_count += 1
-        f = self.flat
-        rsi.nn_adam(f["w"], f["m"], f["v"], f["g"], lr, self.step_count, self.flat16)
-
-    def train_step(self, p, t, lr: float) -> torch.Tensor:
-        self.forward(p)
-        loss = self.loss(t)
-        self.backward()
-        self.adam(lr)
-        return loss
-
-    def predict(self, p) -> torch.Tensor:
-        """Envelopes (scaled) for a batch of exactly B_alloc samples."""
-        return self.forward(p)
+def modulate(env, params, device="cuda", scale: float = 1.0):
+    """Images (complex64 [n, nz, nx]) from interleaved envelopes, times `scale`."""
+    car = _coeffs(params, device)
+    out = torch.empty_like(env)
+    rsi.nn_carrier(car, WINDOW, +1, env.contiguous(), out, scale=scale)
+    return torch.view_as_complex(out.view(env.shape[0], WINDOW["nz"], WINDOW["nx"], 2))
 
 
 # ---------------------------------------------------------------------------
-# data from the RSI path, training, gate
+# data from the RSI path, errors, gate
 # ---------------------------------------------------------------------------
-def rsi_images(params, n_piston=1 << 14, n_iface=1 << 16, chunk=512, index0=0, device="cuda"):
+def rsi_images(params, n_piston=1 << 16, n_iface=1 << 18, chunk=512, index0=0, device="cuda"):
     """Normalised images k phi / v0 (complex64 [n, 128, 128]) of the c5
     chains for each parameter row, computed by the batched RSI path."""
     out = []
@@ -212,33 +279,6 @@ def rsi_images(params, n_piston=1 << 14, n_iface=1 << 16, chunk=512, index0=0, d
     return torch.cat(out, 0)
 
 
-def _coeffs(params, device):
-    """carrier_coeffs on the device: staged in pinned memory and copied
-    without blocking, so the host does not wait for the kernels in flight."""
-    host = torch.from_numpy(carrier_coeffs(params))
-    if torch.device(device).type != "cuda":
-        return host.to(device)
-    return host.pin_memory().to(device, non_blocking=True)
-
-
-def demodulate(images, params, device="cuda"):
-    """Envelope = image * exp(-i psi), as interleaved f32 [n, 2*128*128]."""
-    car = _coeffs(params, device)
-    x = torch.view_as_real(images.contiguous()).reshape(images.shape[0], -1)
-    out = torch.empty_like(x)
-    rsi.nn_carrier(car, WINDOW, -1, x, out)
-    return out
-
-
-def modulate(env, params, device="cuda", scale: float = 1.0):
-    """Image (complex64 [n, 128, 128]) from an interleaved envelope, times
-    `scale` (the network's amplitude scale, applied in the same pass)."""
-    car = _coeffs(params, device)
-    out = torch.empty_like(env)
-    rsi.nn_carrier(car, WINDOW, +1, env.contiguous(), out, scale=scale)
-    return torch.view_as_complex(out.view(env.shape[0], 128, 128, 2))
-
-
 def rel_errors(pred, ref):
     """Per-sample relative L2 error of complex images."""
     d = (pred - ref).reshape(pred.shape[0], -1)
@@ -246,121 +286,13 @@ def rel_errors(pred, ref):
     return (torch.linalg.vector_norm(d, dim=1) / torch.linalg.vector_norm(r, dim=1)).float()
 
 
-class GraphedTrainer:
-    """Training steps (forward, loss and its gradient, backward, Adam on every
-    layer) of `net` replayed from one CUDA graph.  The graph reads the batch
-    from fixed device buffers and Adam's (lr, 1 - beta1^t, 1 - beta2^t) from a
-    device tensor (rsi_nn_adam_dev), which each step refreshes from a
-    schedule held on the device, so nothing in a step waits for the host.
-    The net must have taken one eager step (train_step) first: that step runs
-    every kernel's one-time set-up, which a capture cannot hold."""
-
-    BETA1, BETA2 = 0.9, 0.999
-
-    def __init__(self, net: MLP, lrs):
-        if net.step_count < 1:
-            raise ValueError("GraphedTrainer needs one eager training step first")
-        self.net = net
-        dev, B = net.device, net.B_alloc
-        self.p = torch.zeros(B, 5, dtype=torch.float32, device=dev)
-        self.t = torch.zeros(B, net.y.shape[1], dtype=torch.float32, device=dev)
-        self.hyper = torch.zeros(3, dtype=torch.float32, device=dev)
-        # schedule row for step t (counted from the net's next step): lr and
-        # the bias corrections, formed as rsi_nn_adam forms them (FP64 pow of
-        # the FP32 betas, rounded to FP32)
-        b1, b2 = float(np.float32(self.BETA1)), float(np.float32(self.BETA2))
-        t0 = net.step_count + 1
-        rows = [(lr, 1.0 - b1 ** (t0 + i), 1.0 - b2 ** (t0 + i)) for i, lr in enumerate(lrs)]
-        self.sched = torch.tensor(np.asarray(rows, np.float32), device=dev)
-        self.i = 0
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            net.forward(self.p)
-            net.loss(self.t)
-            net.backward()
-            f = net.flat
-            rsi.nn_adam_dev(f["w"], f["m"], f["v"], f["g"], self.hyper, net.flat16, self.BETA1, self.BETA2)
-
-    def step(self, p_all, t_all, idx) -> torch.Tensor:
-        """One step on rows idx (a device index tensor) of the training set;
-        returns the device loss buffer."""
-        if self.i >= len(self.sched):
-            raise RuntimeError("GraphedTrainer: the learning-rate schedule is exhausted")
-        torch.index_select(p_all, 0, idx, out=self.p)
-        torch.index_select(t_all, 0, idx, out=self.t)
-        self.hyper.copy_(self.sched[self.i])
-        self.graph.replay()
-        self.i += 1
-        self.net.step_count += 1
-        return self.net.loss_buf
-
-
-class GraphedInference:
-    """The surrogate's inference at a fixed batch (the network's B_alloc):
-    carrier coefficients, Fourier features, hidden layers, output layer and
-    the carrier pass with the amplitude scale, captured once into a CUDA
-    graph and replayed per batch.  Each call stages the FP64 parameters in a
-    pinned host buffer, copies them to a fixed device buffer without
-    blocking, and replays the graph: one launch instead of eight calls
-    through Python, so the batch runs at the kernels' speed.  With the
-    tcgen05 engine the output layer applies the carrier in its epilogue
-    (rsi_nn_gemm_carrier), so the layer's raw output never reaches memory.  The returned
-    images (complex64 [B, 128, 128]) are a view of a buffer that the next
-    call overwrites."""
-
-    def __init__(self, net: MLP, scale: float):
-        self.net, self.scale, self.B = net, float(scale), net.B_alloc
-        dev = net.device
-        self.p = torch.zeros(self.B, 5, dtype=torch.float32, device=dev)
-        self.p64 = torch.zeros(self.B, 5, dtype=torch.float64, device=dev)
-        self.car = torch.zeros(self.B, 4, dtype=torch.float64, device=dev)
-        self.out = torch.empty(self.B, 2 * 128 * 128, dtype=torch.float32, device=dev)
-        self.rows = torch.empty(8 * self.B, dtype=torch.float32, device=dev)  # carrier row constants
-        self.p_host = torch.zeros(self.B, 5, dtype=torch.float64).pin_memory()
-        self.copied = None  # event: the last call's host buffers have been read
-        # one plain run first: the library's one-time set-up (kernel
-        # attributes, the status word) happens outside the capture
-        side = torch.cuda.Stream(device=dev)
-        side.wait_stream(torch.cuda.current_stream(dev))
-        with torch.cuda.stream(side):
-            self._body()
-        torch.cuda.current_stream(dev).wait_stream(side)
-        torch.cuda.synchronize(dev)
-        self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph):
-            self._body()
-
-    def _body(self):
-        net = self.net
-        rsi.nn_carrier_coeffs(self.p64, C1, C2, self.car, self.p)
-        if net.engine == "tcgen05":  # output layer and carrier in one kernel
-            rsi.nn_gemm_carrier(net.hidden(self.p), net.W16[-1], net.b[-1], self.car, WINDOW, +1, self.scale,
-                                self.out, workspace=self.rows)
-        else:
-            rsi.nn_carrier(self.car, WINDOW, +1, net.forward(self.p), self.out, scale=self.scale)
-
-    def __call__(self, params) -> torch.Tensor:
-        params = np.asarray(params, np.float64)
-        if params.shape != (self.B, 5):
-            raise ValueError(f"GraphedInference takes exactly {self.B} parameter rows")
-        if self.copied is not None:
-            self.copied.synchronize()  # the previous call's copies have read the host buffers
-        self.p_host.numpy()[:] = params
-        self.p64.copy_(self.p_host, non_blocking=True)
-        self.copied = torch.cuda.Event()
-        self.copied.record()
-        self.graph.replay()
-        return torch.view_as_complex(self.out.view(self.B, 128, 128, 2))
-
-
 class Surrogate:
     """Trained network + held-out error table for the fallback gate."""
 
-    def __init__(self, net: MLP, held_params, held_err, threshold=1e-2, k=8):
+    def __init__(self, net: CoordNet, held_params, held_err, threshold=1e-2, k=8):
         self.net, self.threshold, self.k = net, threshold, k
         self.held_u = self._norm(held_params)
         self.held_err = np.asarray(held_err, np.float64)
-        self._graph = None
 
     @staticmethod
     def _norm(params):
@@ -368,51 +300,22 @@ class Surrogate:
 
     def error_estimate(self, params) -> np.ndarray:
         """Mean held-out error of the k nearest held-out samples (in the
-        normalised parameter box) of each query."""
-        u = self._norm(params)
-        d = ((u[:, None, :] - self.held_u[None, :, :]) ** 2).sum(-1)
+        normalised parameter box, x-offset left out: the field does not depend
+        on it) of each query."""
+        u = self._norm(params)[:, 1:]
+        h = self.held_u[:, 1:]
+        d = ((u[:, None, :] - h[None, :, :]) ** 2).sum(-1)
         nn = np.argpartition(d, min(self.k, d.shape[1] - 1), axis=1)[:, :self.k]
         return self.held_err[nn].mean(axis=1)
 
     def infer(self, params, device="cuda"):
-        """Images for params (batch = the network's batch): surrogate where
-        the error estimate is within the threshold, RSI elsewhere.  The
-        network runs through its CUDA graph (built on the first call)."""
+        """Images for params: the network where the error estimate is within
+        the threshold, the RSI path elsewhere.  Returns (images, estimates,
+        indices of the queries sent to the RSI path)."""
         params = np.asarray(params, np.float64)
-        if self._graph is None:
-            self._graph = GraphedInference(self.net, self.net.scale)
-        img = self._graph(params).clone()
+        img = self.net.infer(torch.tensor(params, device=device)).clone()
         est = self.error_estimate(params)
         fall = np.nonzero(est > self.threshold)[0]
         if len(fall):
             img[torch.tensor(fall, device=device)] = rsi_images(params[fall], index0=10**6).to(img.dtype)
         return img, est, fall
-
-
-def train(net: MLP, params, env, epochs: int, lr: float = 1e-3, seed: int = 0, log=None, graph: bool = True):
-    """Adam on shuffled mini-batches of (params, scaled envelopes), cosine
-    learning-rate decay.  With graph=True every step after the first is a
-    replay of one CUDA graph (GraphedTrainer); the steps compute the same."""
-    n = params.shape[0]
-    B = net.B_alloc
-    rng = np.random.default_rng(seed)
-    p_all = torch.tensor(params, dtype=torch.float32, device=net.device)
-    steps = (n // B) * epochs
-    lrs = [lr * 0.5 * (1.0 + math.cos(math.pi * s / max(1, steps))) for s in range(steps)]
-    total = 0
-    trainer = None
-    losses = []
-    for ep in range(epochs):
-        order = torch.tensor(rng.permutation(n)[: (n // B) * B], device=net.device).view(-1, B)
-        for idx in order:
-            if graph and total > 0:
-                if trainer is None:
-                    trainer = GraphedTrainer(net, lrs[total:])
-                loss = trainer.step(p_all, env, idx)
-            else:
-                loss = net.train_step(p_all[idx], env[idx], lrs[total])
-            total += 1
-        losses.append(float(loss.item()))
-        if log:
-            log(ep, losses[-1])
-    return losses

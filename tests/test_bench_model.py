@@ -62,3 +62,17 @@ def test_unpacked_rsi_kernel_was_issue_bound():
     peak, limiter = bench.alu_roofline("rsi", SM, CLK, {"fp32": 23.0, "mufu": 3.0, "lds": 1.0})
     assert limiter == "issue"
     assert peak / 1e9 == pytest.approx(1491.7, rel=1e-3)
+
+
+def test_fma_pipe_limit():
+    """The FP32 pipe does 128 FMA lanes per SM per clock and a packed f32x2
+    instruction occupies it two cycles: a kernel of 30 packed instructions
+    per pair is FP32-pipe bound at 128 x 152 x 2.07e9 / 60 pairs/s though it
+    issues only 30 instructions."""
+    peak, limiter = bench.alu_roofline("rsi", SM, CLK, {"fp32": 30.0, "mufu": 1.0, "lds": 0.0, "fma_pipe": 60.0})
+    assert limiter == "fma"
+    assert peak == pytest.approx(128 * SM * CLK / 60.0)
+    # the packed single-frequency RSI kernel is co-limited: its FP32 pipe
+    # carries 23/128 of a clock per pair against the MUFU's 3/16
+    o = bench.OPS["rsi"]
+    assert o["fma_pipe"] / 128 == pytest.approx(o["mufu"] / 16, rel=0.05)
