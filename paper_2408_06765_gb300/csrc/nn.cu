@@ -60,7 +60,11 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ float sigmoidf_(float z) { return 1.0f / (1.0f + __expf(-z)); }
+// logistic sigmoid with the fast reciprocal division (a few ulp; the results
+// are rounded to bf16): no IEEE division and its slow-path branch in the
+// epilogue of every hidden layer.  Past z = -87 exp(-z) is infinite and the
+// quotient the limit 0.
+__device__ __forceinline__ float sigmoidf_(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_(float z) { return z * sigmoidf_(z); }
 __device__ __forceinline__ float dsilu_(float z) {
     float s = sigmoidf_(z);

@@ -18,6 +18,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kRaw = 16;   // raw inputs appended to the Fourier features (9 + 7 zeros)
 constexpr int kHead = 3;   // head outputs: re, im, log rms
 constexpr int kHeadRows = 128;  // rows per CTA of the head's backward
+constexpr int kColRows = 256;   // rows per CTA of the column sums
 
 int64_t seg(int64_t n) { return (n + 63) / 64 * 64; }
 size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -73,7 +74,7 @@ int grad_splits(const Dims& d) {
 
 struct Act {
     size_t h[RSI_NN_MAX_DEPTH + 1], z[RSI_NN_MAX_DEPTH + 1];
-    size_t y, t, dz[2], work, part, lpart, env, p32, total;
+    size_t y, t, dz[2], work, part, colpart, lpart, env, p32, total;
     int splits, head_chunks;
 };
 
@@ -98,6 +99,7 @@ Act act_layout(const Dims& d) {
     a.work = take(size_t(a.splits) * d.W * std::max(d.K0, d.W) * sizeof(float));
     a.head_chunks = d.R / kHeadRows;
     a.part = take(size_t(a.head_chunks) * (kHead * d.W + kHead + 1) * sizeof(float));
+    a.colpart = take(size_t((d.R + kColRows - 1) / kColRows) * d.W * sizeof(float));
     a.lpart = take(1024 * sizeof(double));
     a.env = take(size_t(d.R) * 2 * sizeof(float));
     a.p32 = take(size_t(d.R) * 5 * sizeof(float));
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(256) head_fwd_kernel(const bf16* __restrict__ 
 }
 
 __device__ __forceinline__ float silu_grad(float z) {
-    const float s = 1.0f / (1.0f + __expf(-z));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-z));  // fast division: the result is rounded to bf16
     return s * (1.0f + z * (1.0f - s));
 }
 
@@ -327,21 +329,47 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const bf16* __restrict__ 
     if (threadIdx.x == 0) out[kHead * W + kHead] = float(sl[0]);
 }
 
-// sum of the head partials over the CTAs in order: the head's weight and bias
-// gradients into the flat gradient buffer, and the loss
-__global__ void head_reduce_kernel(const float* __restrict__ part, int chunks, int W, float loss_scale,
-                                   float* __restrict__ gW, float* __restrict__ gb, float* __restrict__ loss) {
-    const int n = kHead * W + kHead + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
+// sum over chunks of per-chunk partial sums part[chunk][n], in a fixed order:
+// 32 values per CTA, 8 lanes per value each taking every 8th chunk (FP64),
+// the lanes added in lane order.  Values e < n_w go to out_w[e], the next
+// n_b to out_b, a last one (if n > n_w + n_b) times last_scale to *last.
+__global__ void __launch_bounds__(256) chunk_sum_kernel(const float* __restrict__ part, int chunks, int n, int n_w,
+                                                        int n_b, float last_scale, float* __restrict__ out_w,
+                                                        float* __restrict__ out_b, float* __restrict__ last) {
+    __shared__ double red[8][33];
+    const int e = blockIdx.x * 32 + threadIdx.x;
     double acc = 0.0;
-    for (int c = 0; c < chunks; ++c) acc += double(part[size_t(c) * n + e]);
-    if (e < kHead * W)
-        gW[e] = float(acc);
-    else if (e < kHead * W + kHead)
-        gb[e - kHead * W] = float(acc);
-    else if (loss)
-        *loss = float(acc * double(loss_scale));
+    if (e < n)
+        for (int c = threadIdx.y; c < chunks; c += 8) acc += double(part[size_t(c) * n + e]);
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y != 0 || e >= n) return;
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+    if (e < n_w)
+        out_w[e] = float(t);
+    else if (e < n_w + n_b)
+        out_b[e - n_w] = float(t);
+    else if (last)
+        *last = float(t * double(last_scale));
+}
+
+// column sums of a bf16 [rows][cols] matrix (cols even), first pass: CTA
+// (x, y) sums rows y kColRows .. + kColRows of columns 512 x .. + 512, two
+// adjacent columns per thread, into part[y][cols]
+__global__ void __launch_bounds__(256) colsum_part_kernel(const bf16* __restrict__ m, int rows, int cols,
+                                                          float* __restrict__ part) {
+    const int c = blockIdx.x * 512 + 2 * threadIdx.x;
+    if (c >= cols) return;
+    const int r0 = blockIdx.y * kColRows, r1 = min(rows, r0 + kColRows);
+    float s0 = 0.0f, s1 = 0.0f;
+    for (int r = r0; r < r1; ++r) {
+        const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162*>(m + size_t(r) * cols + c);
+        s0 += __low2float(v);
+        s1 += __high2float(v);
+    }
+    part[size_t(blockIdx.y) * cols + c] = s0;
+    part[size_t(blockIdx.y) * cols + c + 1] = s1;
 }
 
 // per field (one CTA): the mean of the log-RMS outputs over its pixels, then
@@ -497,10 +525,10 @@ extern "C" int rsi_nn_backward(const rsi_nn_net* net, const void* w16, const flo
         w32 + w_off(d, d.D), g, at<bf16>(act, a.dz[cur]), at<float>(act, a.part));
     RSI_CHECK_LAUNCH("head_bwd_kernel");
     const int n_part = kHead * d.W + kHead + 1;
-    head_reduce_kernel<<<unsigned((n_part + 255) / 256), 256, 0, s>>>(
-        at<float>(act, a.part), a.head_chunks, d.W, 1.0f / (4.0f * float(d.R)), grad + w_off(d, d.D),
-        grad + b_off(d, d.D), loss_dev);
-    RSI_CHECK_LAUNCH("head_reduce_kernel");
+    chunk_sum_kernel<<<unsigned((n_part + 31) / 32), dim3(32, 8), 0, s>>>(
+        at<float>(act, a.part), a.head_chunks, n_part, kHead * d.W, kHead, 1.0f / (4.0f * float(d.R)),
+        grad + w_off(d, d.D), grad + b_off(d, d.D), loss_dev);
+    RSI_CHECK_LAUNCH("chunk_sum_kernel");
     // hidden layers, last to first: gW_l = dZ^T H_{l-1}, gb_l = colsum(dZ),
     // dZ_{l-1} = (dZ W_l) * silu'(Z_{l-1})
     for (int l = d.D - 1; l >= 0; --l) {
@@ -509,8 +537,14 @@ extern "C" int rsi_nn_backward(const rsi_nn_net* net, const void* w16, const flo
                          d.W, in_of(d, l), d.R, nullptr, nullptr, grad + w_off(d, l), nullptr, a.splits,
                          at<float>(act, a.work), s);
         if (rc != RSI_OK) return rc;
-        rc = rsi_nn_colsum(dZ, d.R, d.W, grad + b_off(d, l), s);
-        if (rc != RSI_OK) return rc;
+        // bias gradient: column sums of dZ over the rows (two passes, fixed order)
+        const int chunks = (d.R + kColRows - 1) / kColRows;
+        colsum_part_kernel<<<dim3(unsigned((d.W + 511) / 512), unsigned(chunks)), 256, 0, s>>>(
+            dZ, d.R, d.W, at<float>(act, a.colpart));
+        RSI_CHECK_LAUNCH("colsum_part_kernel");
+        chunk_sum_kernel<<<unsigned((d.W + 31) / 32), dim3(32, 8), 0, s>>>(
+            at<float>(act, a.colpart), chunks, d.W, 0, d.W, 0.0f, nullptr, grad + b_off(d, l), nullptr);
+        RSI_CHECK_LAUNCH("chunk_sum_kernel");
         if (l > 0) {
             rc = rsi_nn_gemm(RSI_NN_EPI_DSILU, RSI_NN_ENGINE_TCGEN05, RSI_NN_B_T, dZ, W16 + w_off(d, l), d.R,
                              in_of(d, l), d.W, nullptr, at<float>(act, a.z[l]), nullptr, at<bf16>(act, a.dz[1 - cur]),
