@@ -82,8 +82,8 @@ def parse():
                          "c5: the learned surrogate (train on RSI fields, compare)")
     ap.add_argument("--fields", type=int, default=20000, help="c5: training fields")
     ap.add_argument("--instances", type=int, default=0, help="c4: first N instances only (0 = all)")
-    ap.add_argument("--c5-steps", type=int, default=20000, help="c5: training steps")
-    ap.add_argument("--c5-rows", type=int, default=65536, help="c5: rows (field, pixel pairs) per step")
+    ap.add_argument("--c5-steps", type=int, default=400000, help="c5: training steps")
+    ap.add_argument("--c5-rows", type=int, default=32768, help="c5: rows (field, pixel pairs) per step")
     ap.add_argument("--c5-freq", type=int, default=248, help="c5: Fourier frequencies (2F + 16 % 128 == 0)")
     ap.add_argument("--c5-width", type=int, default=512, help="c5: hidden width")
     ap.add_argument("--c5-depth", type=int, default=5, help="c5: hidden layers")

@@ -475,3 +475,45 @@ def test_coordnet_graphed_training_matches_eager():
     # the same kernels on the same rows: bit-identical weights
     assert torch.equal(nets[0].w, nets[1].w)
     assert nets[0].step_count == nets[1].step_count == 6
+
+
+@pytest.mark.slow
+def test_surrogate_gate_serves_accurate_fields_faster_than_rsi():
+    """What the trained network gains over the plain RSI path: on a sub-box
+    of the c5 inputs (tilt up to 5 degrees, 2-4 MHz, the full water-path,
+    depth and offset ranges), trained on 2048 RSI fields for 40 000 steps,
+    the gate (mean held-out error of the 8 nearest held-out fields <= 1e-2)
+    serves at least half of the queries, the fields it serves are within 1e-2
+    of the RSI path (median; each within 3e-2), and the network delivers them
+    at least 20 times faster than the RSI path computes them."""
+    import time
+    gen = np.random.Generator(np.random.Philox(key=99))
+    lo = np.array([-10e-3, 0.0, 20e-3, 2e6, 1e-3])
+    hi = np.array([10e-3, math.radians(5.0), 60e-3, 4e6, 20e-3])
+    params = lo + (hi - lo) * gen.random((2560, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    imgs = surrogate.rsi_images(params)
+    torch.cuda.synchronize()
+    rsi_fields_s = len(params) / (time.perf_counter() - t0)
+    ntr = 2048
+    net = surrogate.CoordNet(rows=32768)
+    ts = surrogate.TrainingSet(net, params[:ntr], imgs[:ntr])
+    surrogate.train(net, ts, steps=40000, lr=1e-3)
+    held = torch.tensor(params[ntr:], device="cuda")
+    out = torch.empty(len(held), surrogate.NPIX * 2, dtype=torch.float32, device="cuda")
+    net.infer(held, out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pred = net.infer(held, out)
+    torch.cuda.synchronize()
+    nn_fields_s = len(held) / (time.perf_counter() - t0)
+    rsi.sync_status()
+    errs = surrogate.rel_errors(pred, imgs[ntr:]).cpu().numpy()
+    sur = surrogate.Surrogate(net, params[ntr:ntr + 256], errs[:256], threshold=1e-2)
+    est = sur.error_estimate(params[ntr + 256:])
+    served = est <= 1e-2
+    assert served.mean() >= 0.5, served.mean()
+    assert np.median(errs[256:][served]) <= 1e-2
+    assert errs[256:][served].max() <= 3e-2
+    assert nn_fields_s >= 20 * rsi_fields_s, (nn_fields_s, rsi_fields_s)
