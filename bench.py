@@ -75,6 +75,8 @@ def parse():
                     help="stage: only the RSI interface -> image kernel of the 10 MHz c2 chain "
                          "on a 256 x 256 image (small case for profiler captures)")
     ap.add_argument("--variant", type=int, default=0, help="FP32C distance update (0 auto)")
+    ap.add_argument("--curved", action="store_true",
+                    help="--case stage: c3's curved bottom surface (per-point normals) onto its image")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--tpt", type=int, default=0)
     ap.add_argument("--config", choices=["c1", "c2", "c3", "c4", "c5", "f1", "f2", "f3", "f4"], default="c2",
@@ -659,6 +661,11 @@ def run_stage_case(args):
     cfg = W.c2_full_image(10e6)
     cfg["grid"] = dict(cfg["grid"], nx=256, nz=256)
     it = cfg["interfaces"][0]
+    normals, c_img = rsi.NORMALS_Z, 5900.0
+    if args.curved:  # c3's curved bottom surface (per-point normals) onto its 256^2 image in water
+        cfg = W.c3_multilayer(curved=True)
+        it = cfg["interfaces"][-1]
+        normals, c_img = rsi.NORMALS_POINTS, cfg["media"][-1]["c"]
     pts = rsi.make_qmc_points(it, 0, it["set_id"], it["n"])
     grid = rsi.grid_points(cfg["grid"])
     sigma = torch.ones(it["n"], dtype=torch.complex128, device="cuda")
@@ -672,8 +679,8 @@ def run_stage_case(args):
         ks = [rsi.wavenumber(f, 5900.0) for f in (10e6, 5e6, 2.25e6, 1e6)[:nf]]
         sigma = torch.ones((nf, it["n"]), dtype=torch.complex128, device="cuda")
     for tile, tpt, variant in shapes:
-        st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", rsi.wavenumber(cfg["freq"], 5900.0),
-                              normals=rsi.NORMALS_Z, tile=tile, tpt=tpt, variant=variant)
+        st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", rsi.wavenumber(cfg["freq"], c_img),
+                              normals=normals, tile=tile, tpt=tpt, variant=variant)
         out = None
         times = []
         for _ in range(args.warmup + args.steps):
@@ -689,7 +696,8 @@ def run_stage_case(args):
         rsi.sync_status()
         ms = min(times[args.warmup:])
         pairs = it["n"] * grid.n * nf
-        print(json.dumps({"case": "stage", "nf": nf, "ms": ms, "gpair_per_s": pairs / ms / 1e6,
+        print(json.dumps({"case": "stage", "curved": bool(args.curved), "nf": nf, "ms": ms,
+                          "gpair_per_s": pairs / ms / 1e6,
                           "variant": variant, "tile": tile, "tpt": tpt,
                           "checksum": float(out.abs().sum().item())}), flush=True)
 
