@@ -43,10 +43,11 @@ OPS = {
     "piston": {"fp32": 8, "mufu": 3, "lds": 1.0, "fma_pipe": 15},
     # ray-tracing pair (Sec. 2.2), two transducer points per f32x2
     # instruction: linear prediction of the crossing from the tile's reference
-    # ray, 2 Newton steps (16 packed FP32 and 3 MUFU per point each), ~100
-    # packed FP32 per two pairs in all plus 9 scalar (the products of the fast
-    # divisions, the sincos scaling), ~14 compares, selects and clamps, 17 MUFU
-    "raytrace": {"fp32": 59, "alu": 14, "mufu": 17, "lds": 2.0, "fma_pipe": 109},
+    # ray, 2 Newton steps (16 packed FP32 and 3 MUFU per point each), ~110
+    # packed FP32 per two pairs in all plus 6 scalar (the products of the fast
+    # divisions, the sincos scaling), ~14 compares, selects and clamps, 14 MUFU
+    # (the path differences by a Newton step, T12 inside the amplitude's rsqrt)
+    "raytrace": {"fp32": 61, "alu": 14, "mufu": 14, "lds": 2.0, "fma_pipe": 116},
 }
 # "fma_pipe": FP32-pipe lane cycles per pair: a packed f32x2 instruction keeps
 # the pipe two cycles (two FMAs per lane), a scalar one cycle.

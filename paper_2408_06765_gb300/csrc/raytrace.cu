@@ -254,14 +254,20 @@ __device__ __forceinline__ void ray_pair(const RayRef& R, const float4& rec, flo
     const float q1 = fmaf(R.D1, R.D1, t1), q2 = fmaf(R.D2, R.D2, t2);
     const float ir1 = rsqrt_ap(q1), ir2 = rsqrt_ap(q2);
     const float D1 = q1 * ir1, D2 = q2 * ir2;
-    const float dD1 = __fdividef(t1, R.D1 + D1), dD2 = __fdividef(t2, R.D2 + D2);
+    // D - Dc without a division: (D0 - Dc) + (q - D0^2) / (2 D0), D0 = q / sqrt(q) from the
+    // approximate reciprocal square root, q - D0^2 = t - (D0 - Dc)(D0 + Dc) (one Newton step)
+    const float am1 = D1 - R.D1, am2 = D2 - R.D2;
+    const float dD1 = fmaf(fmaf(-am1, D1 + R.D1, t1), 0.5f * ir1, am1);
+    const float dD2 = fmaf(fmaf(-am2, D2 + R.D2, t2), 0.5f * ir2, am2);
     const float u = fmaf(k1, dD1, fmaf(k2, dD2, R.tau));
     // angles of the ray, T12 (Eq. transmission_coefficient) and the spreading
     const float cos1 = h1 * ir1, cos2 = h2 * ir2;
-    const float T = __fdividef(a.Tn * cos1, fmaf(a.Td1, cos1, a.Td2 * cos2));
+    // T12 = Tn cos1 / td folded into the spreading's reciprocal square root:
+    // A T / sqrt(den) = A Tn cos1 / sqrt(den td^2)
+    const float td = fmaf(a.Td1, cos1, a.Td2 * cos2);
     // cos^2 a1 / cos^2 a2 D2 = cos^2 a1 D2^3 / h2^2
     const float den = fmaf(a.c21 * cos1 * cos1 * R.ih22, D2 * q2, D1) * fmaf(a.c21, D2, D1);
-    const float amp = A * T * rsqrt_ap(den);
+    const float amp = A * (a.Tn * cos1) * rsqrt_ap(den * (td * td));
     float s, c;
     __sincosf(u, &s, &c);
     acc_r = fmaf(amp, c, acc_r);
@@ -343,15 +349,18 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     const float2 ir1 = make_float2(rsqrt_ap(q1.x), rsqrt_ap(q1.y)), ir2 = make_float2(rsqrt_ap(q2.x), rsqrt_ap(q2.y));
     const float2 D1 = __fmul2_rn(q1, ir1), D2 = __fmul2_rn(q2, ir2);
     const float2 s1d = __fadd2_rn(f2(R.D1), D1), s2d = __fadd2_rn(f2(R.D2), D2);
-    const float2 dD1 = make_float2(__fdividef(t1.x, s1d.x), __fdividef(t1.y, s1d.y));
-    const float2 dD2 = make_float2(__fdividef(t2.x, s2d.x), __fdividef(t2.y, s2d.y));
+    // D - Dc by one Newton step, as in ray_pair
+    const float2 am1 = sub2(D1, f2(R.D1)), am2 = sub2(D2, f2(R.D2));
+    const float2 dD1 = __ffma2_rn(__ffma2_rn(neg2(am1), s1d, t1), __fmul2_rn(f2(0.5f), ir1), am1);
+    const float2 dD2 = __ffma2_rn(__ffma2_rn(neg2(am2), s2d, t2), __fmul2_rn(f2(0.5f), ir2), am2);
     const float2 u = __ffma2_rn(f2(k1), dD1, __ffma2_rn(f2(k2), dD2, f2(R.tau)));
     const float2 cos1 = __fmul2_rn(h1, ir1), cos2 = __fmul2_rn(f2(h2), ir2);
     const float2 tn = __fmul2_rn(f2(a.Tn), cos1), td = __ffma2_rn(f2(a.Td1), cos1, __fmul2_rn(f2(a.Td2), cos2));
-    const float2 T = make_float2(__fdividef(tn.x, td.x), __fdividef(tn.y, td.y));
+    // T12 = tn / td folded into the spreading's reciprocal square root, as in ray_pair
     const float2 cc = __fmul2_rn(__fmul2_rn(__fmul2_rn(f2(a.c21), cos1), cos1), f2(R.ih22));
     const float2 den = __fmul2_rn(__ffma2_rn(cc, __fmul2_rn(D2, q2), D1), __ffma2_rn(f2(a.c21), D2, D1));
-    const float2 amp = __fmul2_rn(__fmul2_rn(make_float2(A0, A1), T), make_float2(rsqrt_ap(den.x), rsqrt_ap(den.y)));
+    const float2 dt2 = __fmul2_rn(den, __fmul2_rn(td, td));
+    const float2 amp = __fmul2_rn(__fmul2_rn(make_float2(A0, A1), tn), make_float2(rsqrt_ap(dt2.x), rsqrt_ap(dt2.y)));
     float2 sn, cs;
     __sincosf(u.x, &sn.x, &cs.x);
     __sincosf(u.y, &sn.y, &cs.y);
