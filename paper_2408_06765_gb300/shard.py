@@ -189,23 +189,23 @@ class LibrsiBackend:
 
     def __init__(self, precision: str = "fp32c", device="cuda", stream=None):
         from . import rsi
-        self.rsi = rsi
+        self.lib = rsi  # the binding (the method `rsi` below is the RSI stage)
         self.prec = precision
         self.device = device
         self.stream = stream
         self.ws = rsi.Workspace(device)
 
     def points(self, surf, seed, set_id, n):
-        return self.rsi.make_qmc_points(surf, seed, set_id, n, device=self.device, stream=self.stream)
+        return self.lib.make_qmc_points(surf, seed, set_id, n, device=self.device, stream=self.stream)
 
     def grid(self, g):
-        return self.rsi.grid_points(g, device=self.device, stream=self.stream)
+        return self.lib.grid_points(g, device=self.device, stream=self.stream)
 
     def slice(self, pts, lo, hi):
-        return self.rsi.points_slice(pts, lo, hi - lo, stream=self.stream)
+        return self.lib.points_slice(pts, lo, hi - lo, stream=self.stream)
 
     def _stage(self, st, ks, src, sigma, tgt):
-        r = self.rsi
+        r = self.lib
         if len(ks) == 1 or self.prec != "fp32c":
             out = []
             for f, k in enumerate(ks):
@@ -217,11 +217,11 @@ class LibrsiBackend:
         return r.propagate_stage_multi(st, ks, src, sigma, tgt, workspace=self.ws, stream=self.stream)
 
     def piston(self, ks, v0, src, tgt):
-        st = self.rsi.stage_struct(self.rsi.STAGE_PISTON, self.prec, ks[0], v0)
+        st = self.lib.stage_struct(self.lib.STAGE_PISTON, self.prec, ks[0], v0)
         return self._stage(st, ks, src, None, tgt)
 
     def rsi(self, ks, curved, src, sigma, tgt):
-        r = self.rsi
+        r = self.lib
         st = r.stage_struct(r.STAGE_RSI, self.prec, ks[0], 1.0, r.NORMALS_POINTS if curved else r.NORMALS_Z)
         return self._stage(st, ks, src, sigma, tgt)
 
@@ -229,13 +229,13 @@ class LibrsiBackend:
         import torch
         out = torch.empty_like(phi)
         for f in range(phi.shape[0]):
-            self.rsi.interface_transmit(pts, phi[f], m_in, m_out, C, mode, out=out[f], stream=self.stream)
+            self.lib.interface_transmit(pts, phi[f], m_in, m_out, C, mode, out=out[f], stream=self.stream)
         return out
 
     def image(self, phi, ks, v0, nx, rows):
         import torch
         g = {"x0": 0.0, "x1": 1.0, "z0": 0.0, "z1": 1.0, "nx": nx, "nz": rows}  # only nx, nz are used
-        return torch.stack([self.rsi.field_image(g, phi[f], k, v0, stream=self.stream) for f, k in enumerate(ks)])
+        return torch.stack([self.lib.field_image(g, phi[f], k, v0, stream=self.stream) for f, k in enumerate(ks)])
 
     def empty(self, nf):
         import torch

@@ -166,3 +166,12 @@ def test_two_gloo_ranks_reproduce_the_one_rank_chain(which):
     for _, _, full in res:  # every rank holds the whole image after the last gather
         img = full.reshape(want.shape)
         assert np.max(np.abs(img - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_librsi_backend_offers_every_step():
+    """The product backend has every step the rank logic calls (constructing
+    it allocates nothing, so this runs without a GPU)."""
+    be = shard.LibrsiBackend("fp32c", device="cuda")
+    for name in ("points", "grid", "slice", "piston", "rsi", "transmit", "image", "empty", "concat", "cat_rows"):
+        assert callable(getattr(be, name)), name
+    assert callable(getattr(OracleBackend(), "rsi"))
