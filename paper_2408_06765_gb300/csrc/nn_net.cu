@@ -18,7 +18,7 @@ using bf16 = __nv_bfloat16;
 constexpr int kRaw = 16;   // raw inputs appended to the Fourier features (9 + 7 zeros)
 constexpr int kHead = 3;   // head outputs: re, im, log rms
 constexpr int kHeadRows = 128;  // rows per CTA of the head's backward
-constexpr int kColRows = 256;   // rows per CTA of the column sums
+constexpr int kColRows = 64;    // rows per CTA of the column sums
 
 int64_t seg(int64_t n) { return (n + 63) / 64 * 64; }
 size_t al256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -214,36 +214,51 @@ __global__ void __launch_bounds__(256) rows_kernel(RowK k, const double* __restr
     }
 }
 
-// head forward: one warp per row, y = W_h h + b_h (f32 weights in shared memory)
+// head forward, y = W_h h + b_h: each lane keeps its columns' head weights
+// (lane l holds columns 8 l .. 8 l + 7 of every 256) in registers, and a warp
+// walks rows with a stride of all the grid's warps, reading each row once
+// (coalesced 16-byte loads) and reducing the three dot products by shuffles.
+template <int NC>  // 256-column chunks per row: W = 256 NC (W = 128: half the lanes)
 __global__ void __launch_bounds__(256) head_fwd_kernel(const bf16* __restrict__ H, int W, int R,
                                                        const float* __restrict__ Wh, const float* __restrict__ bh,
                                                        float4* __restrict__ y) {
-    extern __shared__ float sW[];  // [3][W]
-    for (int e = threadIdx.x; e < kHead * W; e += blockDim.x) sW[e] = Wh[e];
-    __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= R) return;
-    const bf16* h = H + size_t(r) * W;
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-    for (int c0 = lane * 8; c0 < W; c0 += 256) {
-        const uint4 v = *reinterpret_cast<const uint4*>(h + c0);
-        const bf16* hv = reinterpret_cast<const bf16*>(&v);
+    float w[kHead][NC][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const float x = __bfloat162float(hv[e]);
-            a0 = fmaf(sW[c0 + e], x, a0);
-            a1 = fmaf(sW[W + c0 + e], x, a1);
-            a2 = fmaf(sW[2 * W + c0 + e], x, a2);
+    for (int c = 0; c < NC; ++c) {
+        const int col = c * 256 + lane * 8;
+#pragma unroll
+        for (int o = 0; o < kHead; ++o)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) w[o][c][e] = col < W ? Wh[o * W + col + e] : 0.0f;
+    }
+    const float b0 = bh[0], b1 = bh[1], b2 = bh[2];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < R; r += warps) {
+        const bf16* h = H + size_t(r) * W;
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int col = c * 256 + lane * 8;
+            if (col >= W) continue;
+            const uint4 v = *reinterpret_cast<const uint4*>(h + col);
+            const bf16* hv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float x = __bfloat162float(hv[e]);
+                a0 = fmaf(w[0][c][e], x, a0);
+                a1 = fmaf(w[1][c][e], x, a1);
+                a2 = fmaf(w[2][c][e], x, a2);
+            }
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane == 0) y[r] = make_float4(a0 + b0, a1 + b1, a2 + b2, 0.0f);
     }
-    if (lane == 0) y[r] = make_float4(a0 + bh[0], a1 + bh[1], a2 + bh[2], 0.0f);
 }
 
 __device__ __forceinline__ float silu_grad(float z) {
@@ -433,10 +448,17 @@ int hidden_forward(const rsi_nn_net& n, const Dims& d, const Act& a, const bf16*
                              at<bf16>(act, a.h[l + 1]), 1, nullptr, s);
         if (rc != RSI_OK) return rc;
     }
-    const int warps = 8;
-    const size_t smem = size_t(kHead) * d.W * sizeof(float);
-    head_fwd_kernel<<<unsigned((d.R + warps - 1) / warps), 32 * warps, smem, s>>>(
-        at<bf16>(act, a.h[d.D]), d.W, d.R, w32 + w_off(d, d.D), w32 + b_off(d, d.D), at<float4>(act, a.y));
+    // four CTAs of 8 warps per SM, each warp walking rows
+    const unsigned blocks = unsigned(std::min<int64_t>((d.R + 7) / 8, int64_t(4) * rsi_num_sms()));
+    const bf16* hD = at<bf16>(act, a.h[d.D]);
+    const float *whd = w32 + w_off(d, d.D), *bhd = w32 + b_off(d, d.D);
+    float4* yv = at<float4>(act, a.y);
+    if (d.W <= 256)
+        head_fwd_kernel<1><<<blocks, 256, 0, s>>>(hD, d.W, d.R, whd, bhd, yv);
+    else if (d.W == 512)
+        head_fwd_kernel<2><<<blocks, 256, 0, s>>>(hD, d.W, d.R, whd, bhd, yv);
+    else
+        head_fwd_kernel<4><<<blocks, 256, 0, s>>>(hD, d.W, d.R, whd, bhd, yv);
     RSI_CHECK_LAUNCH("head_fwd_kernel");
     return RSI_OK;
 }
