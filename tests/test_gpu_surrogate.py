@@ -517,3 +517,12 @@ def test_surrogate_gate_serves_accurate_fields_faster_than_rsi():
     assert np.median(errs[256:][served]) <= 1e-2
     assert errs[256:][served].max() <= 3e-2
     assert nn_fields_s >= 20 * rsi_fields_s, (nn_fields_s, rsi_fields_s)
+    # the gate's images: the network's where it serves, the RSI path's (other
+    # QMC point sets, so within the QMC noise) where it does not; a strict
+    # threshold sends some queries back
+    q = params[ntr + 256:ntr + 288]
+    strict = surrogate.Surrogate(net, params[ntr:ntr + 256], errs[:256], threshold=float(np.median(est)))
+    img, est_q, fall = strict.infer(q)
+    assert 0 < len(fall) < len(q)
+    got = surrogate.rel_errors(img, imgs[ntr + 256:ntr + 288]).cpu().numpy()
+    assert np.all(got[fall] <= 2e-2) and np.median(got) <= 1e-2
