@@ -541,7 +541,8 @@ int rsi_nn_forward(const rsi_nn_net *net, const void *w16, const float *w32, voi
 /* Backward pass after rsi_nn_forward and rsi_nn_rows with targets: gradients
  * of loss = sum over rows and outputs of (y - t)^2 / (4 rows) into grad (f32,
  * flat, every parameter overwritten); *loss_dev (device f32) receives the
- * loss.                                                                     */
+ * loss.  The backward's GEMMs read their operands transposed in place and so
+ * run on the tcgen05 engine whatever net->engine says.                      */
 int rsi_nn_backward(const rsi_nn_net *net, const void *w16, const float *w32, void *act, size_t act_bytes,
                     float *grad, float *loss_dev, void *stream);
 /* One Adam step on every parameter (flat buffers) with the schedule in
