@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--c5-piston-log2", type=int, default=16, help="c5: log2 QMC points on the piston")
     ap.add_argument("--c5-iface-log2", type=int, default=18, help="c5: log2 QMC points on the interface")
     ap.add_argument("--lr", type=float, default=1e-3, help="c5: peak learning rate")
+    ap.add_argument("--c5-train-tilt-max", type=float, default=13.0,
+                    help="c5: train on fields with |tilt| below this (degrees; the gate serves the rest by RSI)")
     ap.add_argument("--gemm-shape", default="1024,32768,512",
                     help="--case gemm: M,N,K (default: the surrogate's output layer at batch 1024)")
     ap.add_argument("--engine", choices=["tcgen05", "mma_sync"], default="tcgen05", help="c5: GEMM engine")
@@ -1219,7 +1221,11 @@ def run_surrogate_c5(args):
     tr, ho = slice(0, n - n_hold), slice(n - n_hold, n)
     net = surrogate.CoordNet(n_freq=args.c5_freq, width=args.c5_width, depth=args.c5_depth, rows=args.c5_rows,
                              engine=args.engine)
-    tset = surrogate.TrainingSet(net, params[tr], imgs[tr])
+    # train on the tilts the network can serve: near and past the critical
+    # angle the refracted beam grazes the interface, those fields cost most of
+    # the loss and the gate sends them to the RSI path anyway
+    keep = np.nonzero(np.degrees(np.abs(params[tr][:, 1])) < args.c5_train_tilt_max)[0]
+    tset = surrogate.TrainingSet(net, params[tr][keep], imgs[tr][torch.tensor(keep, device="cuda")])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     losses = surrogate.train(net, tset, steps=args.c5_steps, lr=args.lr)
@@ -1288,6 +1294,7 @@ def run_surrogate_c5(args):
                                    "refracted-beam frame -> Fourier features -> hidden SiLU layers -> re, im, "
                                    "log rms), BF16 weights, FP32 accumulation",
                        "fields": n, "held_out": int(len(errs)), "steps": args.c5_steps, "rows_per_step": net.rows,
+                       "trained_on": f"{len(keep)} of the {n - n_hold} training fields, |tilt| < {args.c5_train_tilt_max:g} deg",
                        "n_freq": net.n_freq, "width": net.width, "depth": net.depth,
                        "rsi_points": [n_p, n_i]},
             "rsi_generation_s": gen_s, "rsi_fields_per_s": rsi_fields_s,
