@@ -1241,9 +1241,11 @@ def run_surrogate_c5(args):
     f_mhz = hp[:, 3] / 1e6
     # the gate: the k-nearest held-out error estimate, leave-one-out over the
     # held-out set (each query's own error excluded from its estimate)
-    sur = surrogate.Surrogate(net, hp, errs)
-    est = np.array([surrogate.Surrogate(net, np.delete(hp, i, 0), np.delete(errs, i)).error_estimate(hp[i:i + 1])[0]
-                    for i in range(len(hp))]) if len(hp) <= 4096 else sur.error_estimate(hp)
+    tmax = math.radians(args.c5_train_tilt_max)
+    sur = surrogate.Surrogate(net, hp, errs, tilt_max=tmax)
+    est = np.array([surrogate.Surrogate(net, np.delete(hp, i, 0), np.delete(errs, i), tilt_max=tmax)
+                    .error_estimate(hp[i:i + 1])[0] for i in range(len(hp))]) if len(hp) <= 4096 \
+        else sur.error_estimate(hp)
     served = est <= 1e-2
     # inference rate: batches of the network's whole-field chunk size
     per = net.rows // surrogate.NPIX
@@ -1284,11 +1286,15 @@ def run_surrogate_c5(args):
     peaks = measured_peaks()
     tf = flops / (gemm_ms * 1e-3) / 1e12
     gemm_bytes = 2.0 * (R * Wd + Wd * Wd) + 4.0 * R * Wd + 2.0 * R * Wd
-    med = lambda m: float(np.median(errs[m])) if m.any() else None
+    # JSON-safe statistics: outside its training tilts the network extrapolates
+    # without bound (the gate never serves those queries)
+    fin = lambda v: float(v) if np.isfinite(v) else None
+    med = lambda m: fin(np.median(errs[m])) if m.any() else None
+    trained = np.degrees(tilt) < args.c5_train_tilt_max
     # the error left after the best complex scale per field (the shape)
     pr, rf = pred.reshape(len(errs), -1), imgs[ho].reshape(len(errs), -1)
     alpha = (pr.conj() * rf).sum(1) / (pr.conj() * pr).sum(1)
-    shape_errs = surrogate.rel_errors(alpha[:, None] * pr, rf).cpu().numpy()
+    shape_errs = surrogate.rel_errors(alpha[:, None] * pr, rf).cpu().numpy()[trained]
     tdeg = np.degrees(tilt)
     line = {"config": {"workload": "c5 learned surrogate: coordinate network per pixel (9 row inputs in the "
                                    "refracted-beam frame -> Fourier features -> hidden SiLU layers -> re, im, "
@@ -1299,10 +1305,14 @@ def run_surrogate_c5(args):
                        "rsi_points": [n_p, n_i]},
             "rsi_generation_s": gen_s, "rsi_fields_per_s": rsi_fields_s,
             "train_s": train_s, "final_train_loss": losses[-1], "train_loss_curve": losses, "lr": args.lr,
-            "held_out_rel_l2": {"median": float(np.median(errs)), "mean": float(errs.mean()),
-                                "p90": float(np.quantile(errs, 0.9)), "max": float(errs.max())},
+            "held_out_rel_l2": {"median": fin(np.median(errs)), "p90": fin(np.quantile(errs, 0.9)),
+                                "within_training_tilts": {"fields": int(trained.sum()),
+                                                          "median": med(trained),
+                                                          "mean": fin(errs[trained].mean()),
+                                                          "p90": fin(np.quantile(errs[trained], 0.9)),
+                                                          "max": fin(errs[trained].max())}},
             "held_out_median_pre_critical": med(pre), "held_out_median_post_critical": med(post),
-            "held_out_shape_only_median": float(np.median(shape_errs)),
+            "held_out_shape_only_median_within_training_tilts": fin(np.median(shape_errs)),
             "held_out_median_by_tilt_deg": {f"{a}-{b}": med((tdeg >= a) & (tdeg < b))
                                             for a, b in ((0, 5), (5, 10), (10, 13), (13, 14.5), (14.5, 15))},
             "held_out_median_by_frequency": {f"{lo}-{lo + 2}MHz": med((f_mhz >= lo) & (f_mhz < lo + 2))

@@ -289,8 +289,11 @@ def rel_errors(pred, ref):
 class Surrogate:
     """Trained network + held-out error table for the fallback gate."""
 
-    def __init__(self, net: CoordNet, held_params, held_err, threshold=1e-2, k=8):
-        self.net, self.threshold, self.k = net, threshold, k
+    def __init__(self, net: CoordNet, held_params, held_err, threshold=1e-2, k=8, tilt_max=None):
+        """tilt_max (radians): the largest |tilt| the network was trained on;
+        queries beyond it always go to the RSI path (the network extrapolates
+        there, its log-RMS output without bound)."""
+        self.net, self.threshold, self.k, self.tilt_max = net, threshold, k, tilt_max
         self.held_u = self._norm(held_params)
         self.held_err = np.asarray(held_err, np.float64)
 
@@ -306,7 +309,10 @@ class Surrogate:
         h = self.held_u[:, 1:]
         d = ((u[:, None, :] - h[None, :, :]) ** 2).sum(-1)
         nn = np.argpartition(d, min(self.k, d.shape[1] - 1), axis=1)[:, :self.k]
-        return self.held_err[nn].mean(axis=1)
+        est = self.held_err[nn].mean(axis=1)
+        if self.tilt_max is not None:
+            est[np.abs(np.asarray(params, np.float64)[:, 1]) >= self.tilt_max] = np.inf
+        return est
 
     def infer(self, params, device="cuda"):
         """Images for params: the network where the error estimate is within
