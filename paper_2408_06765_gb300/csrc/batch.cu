@@ -122,8 +122,20 @@ __global__ void batch_prep_kernel(const BPrep* __restrict__ preps, const BPrepTi
                         p.tile_bytes, t.tile, red, packed != 0);
 }
 
+// Resident CTAs per SM asked of the compiler for the persistent stage kernels:
+// the packed RSI stage (variant 3) keeps its accumulators for two targets in
+// registers at 2 CTAs per SM, as the single-stage kernel does, where 3 spill;
+// RSI_BATCH_RSI_MIN_BLOCKS overrides it.
+#ifndef RSI_BATCH_RSI_MIN_BLOCKS
+#define RSI_BATCH_RSI_MIN_BLOCKS RSI_FP32_PACKED_RSI_MIN_BLOCKS
+#endif
+template <int KIND, int TPT, int VAR>
+constexpr int batch_min_blocks() {
+    return TPT != 2 ? 2 : (KIND == RSI_STAGE_RSI && VAR == 3) ? RSI_BATCH_RSI_MIN_BLOCKS : RSI_FP32_MIN_BLOCKS;
+}
+
 template <int KIND, int NORM, int TPT, int VAR>
-__global__ void __launch_bounds__(kThreads, TPT == 2 ? RSI_FP32_MIN_BLOCKS : 2)
+__global__ void __launch_bounds__(kThreads, batch_min_blocks<KIND, TPT, VAR>())
     batch_stage_kernel(const BStageInst* __restrict__ insts, const BItem* __restrict__ items, int64_t n_items,
                        TwoPiSplit tp, size_t max_tile_bytes, unsigned long long* counter, int* status) {
     extern __shared__ __align__(128) uint8_t smem[];
