@@ -36,11 +36,13 @@ if ROOT not in sys.path:
 # 16-byte records per source shared by the thread's 2 targets).
 OPS = {
     # FP32-pipe warp instructions, MUFU operations and shared loads per pair of
-    # the default kernel (two sources per packed f32x2 instruction): RSI 22
-    # packed per two pairs plus one scalar scaling of the sincos argument per
-    # pair; piston 14 packed per two pairs plus the same scaling
-    "rsi": {"fp32": 12, "mufu": 3, "lds": 1.0, "fma_pipe": 23},
-    "piston": {"fp32": 8, "mufu": 3, "lds": 1.0, "fma_pipe": 15},
+    # the default kernel (two sources per packed f32x2 instruction): RSI 18
+    # packed per two pairs (10 for r - R and the phase, 4 for the obliquity
+    # and the factors g, g/r of the polar amplitude, 4 accumulations) plus one
+    # scalar scaling of the sincos argument per pair; piston 13 packed per two
+    # pairs plus the same scaling
+    "rsi": {"fp32": 10, "mufu": 3, "lds": 1.0, "fma_pipe": 19},
+    "piston": {"fp32": 7.5, "mufu": 3, "lds": 1.0, "fma_pipe": 14},
     # ray-tracing pair (Sec. 2.2), two transducer points per f32x2
     # instruction: linear prediction of the crossing from the tile's reference
     # ray, 2 Newton steps (16 packed FP32 and 3 MUFU per point each), ~110
@@ -258,13 +260,13 @@ def multi_ops(kind: str, nf: int) -> dict:
     on shared points, two sources per packed f32x2 instruction, one target per
     thread): the shared geometry once per source pair, phase, sincos and
     epilogue per frequency, plus one scalar scaling of each sincos argument;
-    the packed record of a source pair (2 + 2 nf float4 for RSI, 4 for the
-    piston) is read once per target."""
-    if kind == "rsi":  # per source pair: shared 14 packed, per f 9 packed
-        return {"fp32": 14.0 / (2 * nf) + 4.5 + 1.0, "mufu": 2.0 + 1.0 / nf, "lds": (2.0 + 2 * nf) / (2.0 * nf),
-                "fma_pipe": 14.0 / nf + 9.0 + 1.0}
-    return {"fp32": 11.0 / (2 * nf) + 1.5 + 1.0, "mufu": 2.0 + 1.0 / nf, "lds": 4.0 / (2.0 * nf),
-            "fma_pipe": 11.0 / nf + 3.0 + 1.0}
+    of the packed record of a source pair, 2 + nf float4 (RSI: geometry and
+    the polar amplitudes) or 4 (piston) are read once per target."""
+    if kind == "rsi":  # per source pair: shared 14 packed, per f 7 packed
+        return {"fp32": 14.0 / (2 * nf) + 3.5 + 1.0, "mufu": 2.0 + 1.0 / nf, "lds": (2.0 + nf) / (2.0 * nf),
+                "fma_pipe": 14.0 / nf + 7.0 + 1.0}
+    return {"fp32": 10.0 / (2 * nf) + 1.5 + 1.0, "mufu": 2.0 + 1.0 / nf, "lds": 4.0 / (2.0 * nf),
+            "fma_pipe": 10.0 / nf + 3.0 + 1.0}
 
 
 def alu_roofline(kind: str, n_sm: int, clock_hz: float, ops: dict | None = None):

@@ -123,11 +123,11 @@ __global__ void batch_prep_kernel(const BPrep* __restrict__ preps, const BPrepTi
 }
 
 // Resident CTAs per SM asked of the compiler for the persistent stage kernels:
-// the packed RSI stage (variant 3) keeps its accumulators for two targets in
-// registers at 2 CTAs per SM, as the single-stage kernel does, where 3 spill;
+// the packed RSI stage (variant 3) keeps its accumulators for two targets and
+// the work-item state in registers at 2 CTAs per SM, where 3 spill;
 // RSI_BATCH_RSI_MIN_BLOCKS overrides it.
 #ifndef RSI_BATCH_RSI_MIN_BLOCKS
-#define RSI_BATCH_RSI_MIN_BLOCKS RSI_FP32_PACKED_RSI_MIN_BLOCKS
+#define RSI_BATCH_RSI_MIN_BLOCKS 2
 #endif
 template <int KIND, int TPT, int VAR>
 constexpr int batch_min_blocks() {

@@ -32,9 +32,11 @@
 #ifndef RSI_FP32_UNROLL
 #define RSI_FP32_UNROLL 2  // unrolling of the loop over a tile's sources
 #endif
-// the packed RSI kernel (variant 3) measured best with its own settings
+// the packed RSI kernel (variant 3) measured best with its own settings: 3
+// resident CTAs (80 registers, no spills; 1453 Gpair/s on the 2^18 x 256^2
+// stage against 1400 at 2 CTAs)
 #ifndef RSI_FP32_PACKED_RSI_MIN_BLOCKS
-#define RSI_FP32_PACKED_RSI_MIN_BLOCKS 2
+#define RSI_FP32_PACKED_RSI_MIN_BLOCKS 3
 #endif
 #ifndef RSI_FP32_PACKED_RSI_UNROLL
 #define RSI_FP32_PACKED_RSI_UNROLL 2
@@ -183,17 +185,22 @@ __device__ __forceinline__ void pair_far(const TgtRef& t, const float4& a, const
 // sm_100-family GPUs.  Tiles are written pair-interleaved (field f of source
 // 2i+L at float (2i)*rec_f + 2f + L) with signs and scales chosen so that no
 // per-pair negation is needed:
-//   f0 px, f1 py, f2 -pz, f3 |p|^2 / 2,
-//   RSI f4 -B.re, f5 -B.im, f6 C.re, f7 C.im      PISTON f4 A, f5..f7 0,
-//   [f8 nx, f9 ny, f10 nz, f11 -n.p]
+//   f0 px, f1 py, f2 -pz, f3 |p|^2 / 2, then
+//   PISTON f4 A, f5..f7 0
+//   RSI    f4 beta, f5 m (B = m e^{i beta}, beta = arg sigma), f6 -m pz, f7 0
+//          [f8..f10 m n, f11 -m n.p  for per-point normals]
 // The distance update is the Newton variant with the factor 1/2 folded in
-// exactly: th = t/2 = |p|^2/2 - D.p, r^2 = R^2 + 2 th, e/2 = th - (r0^2 - R^2)/2,
-// r - R = (r0 - R) + (e/2) / r0.  The RSI epilogue keeps four accumulators
-// (h vr c, h vi s, h vr s, h vi c) so that the complex product needs no
-// negation; they are combined once per tile.
+// exactly: th = t/2 = |p|^2/2 - D.p, r^2 = R^2 + 2 th, and
+// r - R = (r0 - R) + (th - (r0 - R)(r0 + R)/2) / r0, the last product and sum
+// one fused multiply-add.  The RSI term B (ik - 1/r) (n.(Q-P)/r^2) e^{i u}
+// is taken in polar form: with g = m n.(Q-P) / r^2 (the normal carries m),
+//   B (ik - 1/r) e^{iu} n.(Q-P)/r^2 = g (-1/r + ik) e^{i (k (r - R) + beta)} e^{i tau},
+// so each pair adds to four accumulators (g/r cos, g sin, g/r sin, g cos) and
+// the factor k and the target's reference phase e^{i tau} are applied once
+// per tile.
 // ---------------------------------------------------------------------------
 struct TgtRef2 {
-    float2 mx, my, mz, R2, nR, pR, tau, Dx, Dy, Dz;
+    float2 mx, my, mz, R2, nR, nRh, tau, Dx, Dy, Dz;
 };
 __device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
     TgtRef2 r;
@@ -202,7 +209,7 @@ __device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
     r.mz = make_float2(t.Dz, t.Dz);    // pz is stored negated
     r.R2 = make_float2(t.R2, t.R2);
     r.nR = make_float2(-t.R, -t.R);
-    r.pR = make_float2(t.R, t.R);
+    r.nRh = make_float2(-0.5f * t.R, -0.5f * t.R);
     r.tau = make_float2(t.tau, t.tau);
     r.Dx = make_float2(t.Dx, t.Dx);
     r.Dy = make_float2(t.Dy, t.Dy);
@@ -211,7 +218,9 @@ __device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
 }
 
 // two sources (v0 = px, py; v1 = -pz, |p|^2/2; v2, v3 amplitudes; n0, n1
-// normals) onto one target reference, far path
+// scaled normals) onto one target reference, far path.  PISTON: ar1 += A/r
+// cos, ai1 += A/r sin of k (r - R) + tau.  RSI: the four polar accumulators of
+// k (r - R) + beta (the caller applies k and e^{i tau}).
 template <int KIND, int NORM>
 __device__ __forceinline__ void pair_far2(const TgtRef2& t, const float4& v0, const float4& v1, const float4& v2,
                                           const float4& v3, const float4& n0, const float4& n1, float2 k,
@@ -224,45 +233,69 @@ __device__ __forceinline__ void pair_far2(const TgtRef2& t, const float4& v0, co
     ir.x = rsqrt_approx(r2.x);
     ir.y = rsqrt_approx(r2.y);
     const float2 r0 = __fmul2_rn(r2, ir);
-    const float2 am = __fadd2_rn(r0, t.nR);                                   // r0 - R, exact
-    const float2 q = __fmul2_rn(am, __fadd2_rn(r0, t.pR));                    // r0^2 - R^2
-    const float2 eh = __ffma2_rn(q, make_float2(-0.5f, -0.5f), th);           // (r^2 - r0^2)/2
-    const float2 dr = __ffma2_rn(eh, ir, am);                                 // r - R
-    const float2 u = __ffma2_rn(k, dr, t.tau);
+    const float2 am = __fadd2_rn(r0, t.nR);                                  // r0 - R, exact
+    const float2 hs = __ffma2_rn(r0, make_float2(-0.5f, -0.5f), t.nRh);      // -(r0 + R)/2
+    const float2 eh = __ffma2_rn(am, hs, th);                                // (r^2 - r0^2)/2
+    const float2 dr = __ffma2_rn(eh, ir, am);                                // r - R
     float2 sn, cs;
-    __sincosf(u.x, &sn.x, &cs.x);
-    __sincosf(u.y, &sn.y, &cs.y);
     if (KIND == RSI_STAGE_PISTON) {
+        const float2 u = __ffma2_rn(k, dr, t.tau);
+        __sincosf(u.x, &sn.x, &cs.x);
+        __sincosf(u.y, &sn.y, &cs.y);
         const float2 amp = __fmul2_rn(make_float2(v2.x, v2.y), ir);
         ar1 = __ffma2_rn(amp, cs, ar1);
         ai1 = __ffma2_rn(amp, sn, ai1);
     } else {
-        float2 nd;  // n . (Q - P)
+        const float2 u = __ffma2_rn(k, dr, make_float2(v2.x, v2.y));  // k (r - R) + beta
+        __sincosf(u.x, &sn.x, &cs.x);
+        __sincosf(u.y, &sn.y, &cs.y);
+        float2 nd;  // m n . (Q - P)
         if (NORM == RSI_NORMALS_Z)
-            nd = __fadd2_rn(t.Dz, pzn);
+            nd = __ffma2_rn(make_float2(v2.z, v2.w), t.Dz, make_float2(v3.x, v3.y));
         else
             nd = __ffma2_rn(make_float2(n0.x, n0.y), t.Dx,
                             __ffma2_rn(make_float2(n0.z, n0.w), t.Dy,
                                        __ffma2_rn(make_float2(n1.x, n1.y), t.Dz, make_float2(n1.z, n1.w))));
-        const float2 h = __fmul2_rn(nd, __fmul2_rn(ir, ir));                          // cos(theta) / r
-        const float2 vr = __ffma2_rn(ir, make_float2(v2.x, v2.y), make_float2(v3.x, v3.y));  // C.re - B.re / r
-        const float2 vi = __ffma2_rn(ir, make_float2(v2.z, v2.w), make_float2(v3.z, v3.w));  // C.im - B.im / r
-        const float2 hv = __fmul2_rn(h, vr), hw = __fmul2_rn(h, vi);
-        ar1 = __ffma2_rn(hv, cs, ar1);
-        ar2 = __ffma2_rn(hw, sn, ar2);
-        ai1 = __ffma2_rn(hv, sn, ai1);
-        ai2 = __ffma2_rn(hw, cs, ai2);
+        const float2 g = __fmul2_rn(nd, __fmul2_rn(ir, ir));  // m cos(theta) / r
+        const float2 gr = __fmul2_rn(g, ir);
+        ar1 = __ffma2_rn(gr, cs, ar1);
+        ar2 = __ffma2_rn(g, sn, ar2);
+        ai1 = __ffma2_rn(gr, sn, ai1);
+        ai2 = __ffma2_rn(g, cs, ai2);
     }
 }
 
-// one source of a packed tile, unpacked into the scalar record format
+// one source of a packed tile, unpacked for the scalar near path: a = (px,
+// py, pz, |p|^2); PISTON b = (A, 0, 0, 0); RSI b = (beta, m, 0, 0) and n the
+// normal scaled by m (m (0, 0, 1) for flat sources)
 template <int KIND>
 __device__ __forceinline__ void unpack_source(const float* tile_rec, int rec_f, int i, float4& a, float4& b,
                                               float4& n) {
     const float* q = tile_rec + (i >> 1) * 2 * rec_f + (i & 1);
     a = make_float4(q[0], q[2], -q[4], 2.0f * q[6]);
-    b = KIND == RSI_STAGE_RSI ? make_float4(-q[8], -q[10], q[12], q[14]) : make_float4(q[8], 0.f, 0.f, 0.f);
-    n = rec_f == 12 ? make_float4(q[16], q[18], q[20], -q[22]) : make_float4(0.f, 0.f, 1.f, 0.f);
+    b = KIND == RSI_STAGE_RSI ? make_float4(q[8], q[10], 0.f, 0.f) : make_float4(q[8], 0.f, 0.f, 0.f);
+    n = rec_f == 12 ? make_float4(q[16], q[18], q[20], -q[22]) : make_float4(0.f, 0.f, q[10], 0.f);
+}
+
+// near path of the packed RSI records: one source (a, polar b, scaled n)
+// onto one target reference, added directly to the target's sums
+__device__ __forceinline__ void pair_near_polar(const TgtRef& t, const float4& a, const float4& b, const float4& nr,
+                                                float k, float& acc_r, float& acc_i) {
+    float dx = t.Dx - a.x, dy = t.Dy - a.y, dz = t.Dz - a.z;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float tt = fmaf(t.mx, a.x, fmaf(t.my, a.y, fmaf(t.mz, a.z, a.w)));  // r^2 - R^2
+    float ir = rsqrt_approx(r2);
+    ir = r2 > 1e-24f ? ir : 0.0f;  // pairs closer than 1e-12 m contribute nothing
+    float r0 = r2 * ir;
+    float am = t.R - r0;
+    float e = fmaf(am, t.R + r0, tt);  // r^2 - r0^2
+    float dr = fmaf(e, 0.5f * ir, -am);
+    float nd = fmaf(nr.x, dx, fmaf(nr.y, dy, nr.z * dz));  // m n . (Q - P)
+    float s, c;
+    __sincosf(fmaf(k, dr, t.tau + b.x), &s, &c);  // tau + beta first: |tau + beta| <= 2 pi
+    float g = nd * (ir * ir);
+    acc_r = fmaf(-g, fmaf(ir, c, k * s), acc_r);  // g (-c/r - k s)
+    acc_i = fmaf(g, fmaf(-ir, s, k * c), acc_i);  // g (-s/r + k c)
 }
 
 // One CTA's share of a stage: targets j0 .. j0 + TPT*kThreads - 1 against
@@ -357,8 +390,18 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
                 }
 #pragma unroll
                 for (int q = 0; q < TPT; ++q) {
-                    ar[q] = (a1[q].x + a1[q].y) - (a2[q].x + a2[q].y);
-                    ai[q] = (b1[q].x + b1[q].y) + (b2[q].x + b2[q].y);
+                    if (KIND == RSI_STAGE_PISTON) {
+                        ar[q] = a1[q].x + a1[q].y;
+                        ai[q] = b1[q].x + b1[q].y;
+                    } else {
+                        // (-sum g/r cos - k sum g sin) + i (-sum g/r sin + k sum g cos), times e^{i tau}
+                        const float sr = fmaf(-k, a2[q].x + a2[q].y, -(a1[q].x + a1[q].y));
+                        const float si = fmaf(k, b2[q].x + b2[q].y, -(b1[q].x + b1[q].y));
+                        float st, ct;
+                        __sincosf(ref[q].tau, &st, &ct);
+                        ar[q] = fmaf(ct, sr, -st * si);
+                        ai[q] = fmaf(st, sr, ct * si);
+                    }
                 }
             } else {
                 const float* tf = reinterpret_cast<const float*>(rec);
@@ -367,7 +410,12 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
                     float4 ra, rb, rn;
                     unpack_source<KIND>(tf, rec_f, i, ra, rb, rn);
 #pragma unroll
-                    for (int q = 0; q < TPT; ++q) pair_near<KIND, NORM, 2>(ref[q], ra, rb, rn, k, ar[q], ai[q]);
+                    for (int q = 0; q < TPT; ++q) {
+                        if (KIND == RSI_STAGE_PISTON)
+                            pair_near<KIND, NORM, 2>(ref[q], ra, rb, rn, k, ar[q], ai[q]);
+                        else
+                            pair_near_polar(ref[q], ra, rb, rn, k, ar[q], ai[q]);
+                    }
                 }
             }
         } else if (__all_sync(0xffffffffu, far_lane)) {
@@ -490,6 +538,7 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t 
     float px = 4.0f, py = 4.0f, pz = 4.0f, radius2 = 0.0f;
     float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
     float nx = 0.f, ny = 0.f, nz = 1.f;
+    float beta = 0.f, mag = 0.f;  // packed RSI records: B = mag e^{i beta}
     if (valid) {
         float h, l;
         df_diff(src.xh[i], src.xl[i], ch[0], cl[0], h, l);
@@ -508,6 +557,11 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t 
             r1 = float(bi);
             r2 = float(-k * bi);
             r3 = float(k * br);
+            // B = mag e^{i beta} with beta = arg sigma and the signs of the
+            // amplitude scale and the weight in mag, so that reversed normals
+            // (a negated scale) negate every term exactly
+            beta = float(atan2(sg.y, sg.x));
+            mag = float(amp_scale * src.w[i] * hypot(sg.x, sg.y));
             nx = float(src.nx[i]);
             ny = float(src.ny[i]);
             nz = float(src.nz[i]);
@@ -534,15 +588,15 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t 
         rec[1 * fs] = py;
         rec[2 * fs] = -pz;
         rec[3 * fs] = 0.5f * fmaf(px, px, fmaf(py, py, pz * pz));
-        rec[4 * fs] = rsi ? -r0 : r0;
-        rec[5 * fs] = rsi ? -r1 : 0.0f;
-        rec[6 * fs] = rsi ? r2 : 0.0f;
-        rec[7 * fs] = rsi ? r3 : 0.0f;
+        rec[4 * fs] = rsi ? beta : r0;
+        rec[5 * fs] = rsi ? mag : 0.0f;
+        rec[6 * fs] = rsi ? -mag * pz : 0.0f;
+        rec[7 * fs] = 0.0f;
         if (rec_f == 12) {
-            rec[8 * fs] = nx;
-            rec[9 * fs] = ny;
-            rec[10 * fs] = nz;
-            rec[11 * fs] = -fmaf(nx, px, fmaf(ny, py, nz * pz));  // -n . p
+            rec[8 * fs] = mag * nx;
+            rec[9 * fs] = mag * ny;
+            rec[10 * fs] = mag * nz;
+            rec[11 * fs] = -mag * fmaf(nx, px, fmaf(ny, py, nz * pz));  // -m n . p
         }
     }
     double rad = block_reduce(double(radius2), true, red);

@@ -44,12 +44,14 @@ struct MultiArgs {
 //   PISTON  [A, 0, 0, 0]                   (A = -v0 w / 2 pi, frequency independent)
 //   RSI     nf x [B.re, B.im, C.re, C.im]  (B = -w sigma_f / 2 pi, C = i k_f B)
 //           [+ (nx, ny, nz, n.p)]
-template <int KIND, int NORM, int NF>
+// The packed form keeps each RSI amplitude in polar form, nf x [beta_f, m_f]
+// padded to whole float4s (see MRef2).
+template <int KIND, int NORM, int NF, int PK>
 constexpr int mrec_f4() {
-    return KIND == RSI_STAGE_PISTON ? 2 : 1 + NF + (NORM == RSI_NORMALS_POINTS ? 1 : 0);
+    return KIND == RSI_STAGE_PISTON ? 2 : 1 + (PK ? (NF + 1) / 2 : NF) + (NORM == RSI_NORMALS_POINTS ? 1 : 0);
 }
-__host__ __device__ inline int mrec_f4_rt(int kind, int normals, int nf) {
-    return kind == RSI_STAGE_PISTON ? 2 : 1 + nf + (normals == RSI_NORMALS_POINTS ? 1 : 0);
+__host__ __device__ inline int mrec_f4_rt(int kind, int normals, int nf, bool packed) {
+    return kind == RSI_STAGE_PISTON ? 2 : 1 + (packed ? (nf + 1) / 2 : nf) + (normals == RSI_NORMALS_POINTS ? 1 : 0);
 }
 
 struct MRef {
@@ -131,6 +133,26 @@ __device__ __forceinline__ void mterms(const MRef& t, const float4* r, float dr,
     }
 }
 
+// the same with the packed form's polar amplitudes r[1 + f] = (beta_f, m_f, 0, 0)
+template <int KIND, int NORM, int NF>
+__device__ __forceinline__ void mterms_polar(const MRef& t, const float4* r, float dr, float ir, float nd,
+                                             const float* kv, float (&ar)[NF], float (&ai)[NF]) {
+    if (KIND == RSI_STAGE_PISTON) {
+        mterms<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
+    } else {
+        const float h = nd * (ir * ir);  // cos(theta) / r
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            const float4 b = r[1 + f];
+            float s, c;
+            __sincosf(fmaf(kv[f], dr, t.tau[f] + b.x), &s, &c);  // tau + beta first: |tau + beta| <= 2 pi
+            const float g = h * b.y;
+            ar[f] = fmaf(-g, fmaf(ir, c, kv[f] * s), ar[f]);  // g (-c/r - k s)
+            ai[f] = fmaf(g, fmaf(-ir, s, kv[f] * c), ai[f]);  // g (-s/r + k c)
+        }
+    }
+}
+
 // far path: R > 2 (tile radius)
 template <int KIND, int NORM, int NF>
 __device__ __forceinline__ void mpair_far(const MRef& t, const float4* r, const float* kv, float (&ar)[NF],
@@ -155,8 +177,9 @@ __device__ __forceinline__ void mpair_far(const MRef& t, const float4* r, const 
     mterms<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
 }
 
-// near path: r^2 from the FP32 offsets; pairs closer than 1e-12 m contribute nothing
-template <int KIND, int NORM, int NF>
+// near path: r^2 from the FP32 offsets; pairs closer than 1e-12 m contribute
+// nothing.  PK: records unpacked from the packed form (polar amplitudes).
+template <int KIND, int NORM, int NF, int PK>
 __device__ __forceinline__ void mpair_near(const MRef& t, const float4* r, const float* kv, float (&ar)[NF],
                                            float (&ai)[NF]) {
     const float4 a = r[0];
@@ -178,18 +201,26 @@ __device__ __forceinline__ void mpair_near(const MRef& t, const float4* r, const
             nd = fmaf(n.x, dx, fmaf(n.y, dy, n.z * dz));
         }
     }
-    mterms<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
+    if (PK)
+        mterms_polar<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
+    else
+        mterms<KIND, NORM, NF>(t, r, dr, ir, nd, kv, ar, ai);
 }
 
 // ---------------------------------------------------------------------------
 // Packed form: two sources per f32x2 instruction, records pair-interleaved
 // with the signs and the factor 1/2 of the single-frequency packed kernel
 // (field f of source 2i+L at float (2i) rf + 2f + L):
-//   [px, py, -pz, |p|^2/2], then RSI nf x [-B.re, -B.im, C.re, C.im] or
-//   PISTON [A, 0, 0, 0], then [nx, ny, nz, -n.p] for per-point normals.
+//   [px, py, -pz, |p|^2/2], then RSI nf x [beta_f, m_f] (B_f = m_f e^{i beta_f})
+//   (padded to a whole float4) or PISTON [A, 0, 0, 0], then [nx, ny, nz,
+//   -n.p] for per-point normals.
+// With h = n.(Q-P)/r^2 formed once per pair, frequency f adds
+//   B_f (ik_f - 1/r) h e^{i u_f} = m_f h (-1/r + ik_f) e^{i (k_f (r - R) + beta_f)} e^{i tau_f}
+// to four accumulators (m_f h/r cos, m_f h sin, m_f h/r sin, m_f h cos); the
+// factor k_f and e^{i tau_f} are applied once per tile.
 // ---------------------------------------------------------------------------
 struct MRef2 {
-    float2 mx, my, mz, R2, nR, pR, Dx, Dy, Dz;
+    float2 mx, my, mz, R2, nR, nRh, Dx, Dy, Dz;
     float2 tau[kMaxNF];
 };
 template <int NF>
@@ -200,7 +231,7 @@ __device__ __forceinline__ MRef2 packed_mref(const MRef& t) {
     r.mz = make_float2(t.Dz, t.Dz);
     r.R2 = make_float2(t.R2, t.R2);
     r.nR = make_float2(-t.R, -t.R);
-    r.pR = make_float2(t.R, t.R);
+    r.nRh = make_float2(-0.5f * t.R, -0.5f * t.R);
     r.Dx = make_float2(t.Dx, t.Dx);
     r.Dy = make_float2(t.Dy, t.Dy);
     r.Dz = make_float2(t.Dz, t.Dz);
@@ -210,8 +241,9 @@ __device__ __forceinline__ MRef2 packed_mref(const MRef& t) {
 }
 
 // two sources (records pr[0..RF4*2-1], packed) onto one target, far path;
-// acc[f] = (sum h vr c, sum h vi s, sum h vr s, sum h vi c) for RSI or
-// (sum A c / r, -, sum A s / r, -) for the piston
+// acc[f] = (sum m h/r c, sum m h s, sum m h/r s, sum m h c) of k_f (r - R) +
+// beta_f for RSI, or (sum A c / r, -, sum A s / r, -) of k_f (r - R) + tau_f
+// for the piston
 template <int KIND, int NORM, int NF>
 __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, const float2* kv,
                                            float2 (&acc)[NF][4]) {
@@ -224,9 +256,9 @@ __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, con
     ir.x = rsqrt_approx(r2.x);
     ir.y = rsqrt_approx(r2.y);
     const float2 r0 = __fmul2_rn(r2, ir);
-    const float2 am = __fadd2_rn(r0, t.nR);
-    const float2 q = __fmul2_rn(am, __fadd2_rn(r0, t.pR));
-    const float2 eh = __ffma2_rn(q, make_float2(-0.5f, -0.5f), th);
+    const float2 am = __fadd2_rn(r0, t.nR);                              // r0 - R, exact
+    const float2 hs = __ffma2_rn(r0, make_float2(-0.5f, -0.5f), t.nRh);  // -(r0 + R)/2
+    const float2 eh = __ffma2_rn(am, hs, th);                            // (r^2 - r0^2)/2
     const float2 dr = __ffma2_rn(eh, ir, am);
     if (KIND == RSI_STAGE_PISTON) {
         const float4 va = pr[2];
@@ -245,34 +277,36 @@ __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, con
         if (NORM == RSI_NORMALS_Z) {
             nd = __fadd2_rn(t.Dz, pzn);
         } else {
-            const float4 n0 = pr[2 + 2 * NF], n1 = pr[3 + 2 * NF];
+            constexpr int nb = 2 + 2 * ((NF + 1) / 2);  // first normal float4 of the pair
+            const float4 n0 = pr[nb], n1 = pr[nb + 1];
             nd = __ffma2_rn(make_float2(n0.x, n0.y), t.Dx,
                             __ffma2_rn(make_float2(n0.z, n0.w), t.Dy,
                                        __ffma2_rn(make_float2(n1.x, n1.y), t.Dz, make_float2(n1.z, n1.w))));
         }
-        const float2 h = __fmul2_rn(nd, __fmul2_rn(ir, ir));
+        const float2 h = __fmul2_rn(nd, __fmul2_rn(ir, ir));  // cos(theta) / r
+        const float2 hr = __fmul2_rn(h, ir);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const float4 b0 = pr[2 + 2 * f], b1 = pr[3 + 2 * f];
-            const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
+            const float4 b = pr[2 + f];  // (beta_f, m_f) of both sources
+            const float2 u = __ffma2_rn(kv[f], dr, make_float2(b.x, b.y));
             float2 sn, cs;
             __sincosf(u.x, &sn.x, &cs.x);
             __sincosf(u.y, &sn.y, &cs.y);
-            const float2 vr = __ffma2_rn(ir, make_float2(b0.x, b0.y), make_float2(b1.x, b1.y));
-            const float2 vi = __ffma2_rn(ir, make_float2(b0.z, b0.w), make_float2(b1.z, b1.w));
-            const float2 hv = __fmul2_rn(h, vr), hw = __fmul2_rn(h, vi);
-            acc[f][0] = __ffma2_rn(hv, cs, acc[f][0]);
-            acc[f][1] = __ffma2_rn(hw, sn, acc[f][1]);
-            acc[f][2] = __ffma2_rn(hv, sn, acc[f][2]);
-            acc[f][3] = __ffma2_rn(hw, cs, acc[f][3]);
+            const float2 m = make_float2(b.z, b.w);
+            const float2 g = __fmul2_rn(h, m), gr = __fmul2_rn(hr, m);
+            acc[f][0] = __ffma2_rn(gr, cs, acc[f][0]);
+            acc[f][1] = __ffma2_rn(g, sn, acc[f][1]);
+            acc[f][2] = __ffma2_rn(gr, sn, acc[f][2]);
+            acc[f][3] = __ffma2_rn(g, cs, acc[f][3]);
         }
     }
 }
 
 // one source of a packed tile, unpacked into the scalar record format
+// (r[0 .. mrec_f4<KIND, NORM, NF, 0>() - 1], amplitudes in polar form)
 template <int KIND, int NORM, int NF>
 __device__ __forceinline__ void munpack(const float* tile_rec, int i, float4* r) {
-    constexpr int rf = 4 * mrec_f4<KIND, NORM, NF>();
+    constexpr int rf = 4 * mrec_f4<KIND, NORM, NF, 1>();
     const float* q = tile_rec + (i >> 1) * 2 * rf + (i & 1);
     r[0] = make_float4(q[0], q[2], -q[4], 2.0f * q[6]);
     if (KIND == RSI_STAGE_PISTON) {
@@ -280,11 +314,11 @@ __device__ __forceinline__ void munpack(const float* tile_rec, int i, float4* r)
     } else {
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const float* b = q + 8 + 8 * f;
-            r[1 + f] = make_float4(-b[0], -b[2], b[4], b[6]);
+            const float* b = q + 8 + 4 * f;  // fields 4 + 2f (beta_f), 5 + 2f (m_f)
+            r[1 + f] = make_float4(b[0], b[2], 0.f, 0.f);
         }
         if (NORM == RSI_NORMALS_POINTS) {
-            const float* n = q + 8 + 8 * NF;
+            const float* n = q + 2 * (4 + 4 * ((NF + 1) / 2));
             r[1 + NF] = make_float4(n[0], n[2], n[4], -n[6]);
         }
     }
@@ -296,7 +330,8 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RSI_PIPE_STAGES * a.tile_bytes);
     init_barriers(bars);
-    constexpr int RF4 = mrec_f4<KIND, NORM, NF>();
+    constexpr int RF4 = mrec_f4<KIND, NORM, NF, PK>();  // float4 per record in the tiles
+    constexpr int URF4 = mrec_f4<KIND, NORM, NF, 0>();  // float4 per record in the scalar format
     constexpr int TPT = PK ? 1 : kMTpt;
     const int tid = threadIdx.x;
     // one-dimensional grid, the splits of a target block adjacent: they run
@@ -370,36 +405,46 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
                 }
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
-                    ar[q][f] = (acc[f][0].x + acc[f][0].y) - (acc[f][1].x + acc[f][1].y);
-                    ai[q][f] = (acc[f][2].x + acc[f][2].y) + (acc[f][3].x + acc[f][3].y);
+                    if (KIND == RSI_STAGE_PISTON) {
+                        ar[q][f] = acc[f][0].x + acc[f][0].y;
+                        ai[q][f] = acc[f][2].x + acc[f][2].y;
+                    } else {
+                        // (-sum m h/r c - k sum m h s) + i (-sum m h/r s + k sum m h c), times e^{i tau}
+                        const float sr = fmaf(-kv[f], acc[f][1].x + acc[f][1].y, -(acc[f][0].x + acc[f][0].y));
+                        const float si = fmaf(kv[f], acc[f][3].x + acc[f][3].y, -(acc[f][2].x + acc[f][2].y));
+                        float st, ct;
+                        __sincosf(ref[q].tau[f], &st, &ct);
+                        ar[q][f] = fmaf(ct, sr, -st * si);
+                        ai[q][f] = fmaf(st, sr, ct * si);
+                    }
                 }
             }
         } else if (PK) {
             const float* tf = reinterpret_cast<const float*>(rec);
 #pragma unroll 1
             for (int i = 0; i < a.S; ++i) {
-                float4 r[RF4];
+                float4 r[URF4];  // unpacked: 1 + NF (+ 1) float4, polar amplitudes
                 munpack<KIND, NORM, NF>(tf, i, r);
 #pragma unroll
-                for (int q = 0; q < TPT; ++q) mpair_near<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
+                for (int q = 0; q < TPT; ++q) mpair_near<KIND, NORM, NF, PK>(ref[q], r, kv, ar[q], ai[q]);
             }
         } else if (__all_sync(0xffffffffu, far_lane)) {
 #pragma unroll 1
-            for (int i = 0; i < a.S; ++i) {
-                float4 r[RF4];
+            for (int i = 0; i < a.S; ++i) {  // scalar records (PK = 0 only)
+                float4 r[URF4];
 #pragma unroll
-                for (int m = 0; m < RF4; ++m) r[m] = rec[i * RF4 + m];
+                for (int m = 0; m < URF4; ++m) r[m] = rec[i * URF4 + m];
 #pragma unroll
                 for (int q = 0; q < TPT; ++q) mpair_far<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
             }
         } else {
 #pragma unroll 1
             for (int i = 0; i < a.S; ++i) {
-                float4 r[RF4];
+                float4 r[URF4];
 #pragma unroll
-                for (int m = 0; m < RF4; ++m) r[m] = rec[i * RF4 + m];
+                for (int m = 0; m < URF4; ++m) r[m] = rec[i * URF4 + m];
 #pragma unroll
-                for (int q = 0; q < TPT; ++q) mpair_near<KIND, NORM, NF>(ref[q], r, kv, ar[q], ai[q]);
+                for (int q = 0; q < TPT; ++q) mpair_near<KIND, NORM, NF, 0>(ref[q], r, kv, ar[q], ai[q]);
             }
         }
 #pragma unroll
@@ -514,7 +559,7 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
         ch[d] = __double2float_rn(c[d]);
         cl[d] = __double2float_rn(c[d] - double(ch[d]));
     }
-    const int rf = 4 * mrec_f4_rt(kind, normals, nf);
+    const int rf = 4 * mrec_f4_rt(kind, normals, nf, a.packed != 0);
     // field fi of this source: rec[fi * fs] (packed: pair-interleaved, see MRef2)
     const bool pk = a.packed != 0;
     const int fs = pk ? 2 : 1;
@@ -538,6 +583,21 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
     if (kind == RSI_STAGE_PISTON) {
         rec[4 * fs] = valid ? float(amp_scale * src.w[i]) : 0.0f;
         rec[5 * fs] = rec[6 * fs] = rec[7 * fs] = 0.0f;
+    } else if (pk) {  // polar amplitudes (beta_f, m_f), padded to a whole float4
+        const int nfp = 2 * ((nf + 1) / 2);
+        for (int f = 0; f < nfp; ++f) {
+            float* b = rec + (4 + 2 * f) * fs;
+            // B_f = m_f e^{i beta_f}, beta_f = arg sigma_f, the signs of the
+            // scale and the weight in m_f (reversed normals negate exactly)
+            double2 sgm = make_double2(0.0, 0.0);
+            double wa = 0.0;
+            if (valid && f < nf) {
+                sgm = sigma[size_t(f) * size_t(n_src) + size_t(i)];
+                wa = amp_scale * src.w[i];
+            }
+            b[0 * fs] = float(atan2(sgm.y, sgm.x));
+            b[1 * fs] = float(wa * hypot(sgm.x, sgm.y));
+        }
     } else {
         for (int f = 0; f < nf; ++f) {
             float* b = rec + (4 + 4 * f) * fs;
@@ -545,16 +605,18 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
                 const double k = double(a.kh[f]) + double(a.kl[f]);
                 const double2 sgm = sigma[size_t(f) * size_t(n_src) + size_t(i)];
                 const double br = amp_scale * src.w[i] * sgm.x, bi = amp_scale * src.w[i] * sgm.y;
-                b[0 * fs] = sg * float(br);
-                b[1 * fs] = sg * float(bi);
+                b[0 * fs] = float(br);
+                b[1 * fs] = float(bi);
                 b[2 * fs] = float(-k * bi);
                 b[3 * fs] = float(k * br);
             } else {
                 b[0 * fs] = b[1 * fs] = b[2 * fs] = b[3 * fs] = 0.0f;
             }
         }
+    }
+    if (kind != RSI_STAGE_PISTON) {
         if (normals == RSI_NORMALS_POINTS) {
-            float* n = rec + (4 + 4 * nf) * fs;
+            float* n = rec + (rf - 4) * fs;
             const float nx = valid ? float(src.nx[i]) : 0.0f, ny = valid ? float(src.ny[i]) : 0.0f,
                         nz = valid ? float(src.nz[i]) : 1.0f;
             n[0 * fs] = nx;
@@ -653,14 +715,14 @@ int mplan(const rsi_stage& st, int nf, const double* ks, int64_t n_src, int64_t 
         while (p.S > 32 && p.S > cap) p.S >>= 1;
     }
     p.n_tiles = int((n_src + p.S - 1) / p.S);
-    p.tile_bytes = RSI_TILE_HDR_BYTES + size_t(p.S) * 16 * size_t(mrec_f4_rt(st.kind, normals, nf));
+    if (st.variant != 0 && st.variant != 2 && st.variant != 3)
+        return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi: variant must be 0, 2 or 3");
+    a.packed = st.variant != 2;  // 3 (and 0): two sources per f32x2 instruction; 2: scalar
+    p.tile_bytes = RSI_TILE_HDR_BYTES + size_t(p.S) * 16 * size_t(mrec_f4_rt(st.kind, normals, nf, a.packed != 0));
     p.tiles_bytes = align256(size_t(p.n_tiles) * p.tile_bytes);
     a.kind = st.kind;
     a.normals = normals;
     a.nf = nf;
-    if (st.variant != 0 && st.variant != 2 && st.variant != 3)
-        return rsi_fail(RSI_E_INVAL, "rsi_propagate_stage_multi: variant must be 0, 2 or 3");
-    a.packed = st.variant != 2;  // 3 (and 0): two sources per f32x2 instruction; 2: scalar
     a.S = p.S;
     a.n_tiles = p.n_tiles;
     a.n_tgt = n_tgt;
