@@ -218,25 +218,19 @@ __device__ __forceinline__ TgtRef2 packed_reference(const TgtRef& t) {
 }
 
 // two sources (v0 = px, py; v1 = -pz, |p|^2/2; v2, v3 amplitudes; n0, n1
-// scaled normals) onto one target reference, far path.  PISTON: ar1 += A/r
-// cos, ai1 += A/r sin of k (r - R) + tau.  RSI: the four polar accumulators of
-// k (r - R) + beta (the caller applies k and e^{i tau}).
+// scaled normals) onto one target reference, once th = (r^2 - R^2)/2, r^2 and
+// 1/r are known.  PISTON: ar1 += A/r cos, ai1 += A/r sin of k (r - R) + tau.
+// RSI: the four polar accumulators of k (r - R) + beta (the caller applies k
+// and e^{i tau}).
 template <int KIND, int NORM>
-__device__ __forceinline__ void pair_far2(const TgtRef2& t, const float4& v0, const float4& v1, const float4& v2,
-                                          const float4& v3, const float4& n0, const float4& n1, float2 k,
-                                          float2& ar1, float2& ar2, float2& ai1, float2& ai2) {
-    const float2 px = make_float2(v0.x, v0.y), py = make_float2(v0.z, v0.w);
-    const float2 pzn = make_float2(v1.x, v1.y), pwh = make_float2(v1.z, v1.w);
-    const float2 th = __ffma2_rn(t.mx, px, __ffma2_rn(t.my, py, __ffma2_rn(t.mz, pzn, pwh)));  // (r^2 - R^2)/2
-    const float2 r2 = __ffma2_rn(th, make_float2(2.0f, 2.0f), t.R2);
-    float2 ir;
-    ir.x = rsqrt_approx(r2.x);
-    ir.y = rsqrt_approx(r2.y);
+__device__ __forceinline__ void pair_terms2(const TgtRef2& t, float2 th, float2 r2, float2 ir, const float4& v1,
+                                            const float4& v2, const float4& v3, const float4& n0, const float4& n1,
+                                            float2 k, float2& ar1, float2& ar2, float2& ai1, float2& ai2) {
     const float2 r0 = __fmul2_rn(r2, ir);
-    const float2 am = __fadd2_rn(r0, t.nR);                                  // r0 - R, exact
-    const float2 hs = __ffma2_rn(r0, make_float2(-0.5f, -0.5f), t.nRh);      // -(r0 + R)/2
-    const float2 eh = __ffma2_rn(am, hs, th);                                // (r^2 - r0^2)/2
-    const float2 dr = __ffma2_rn(eh, ir, am);                                // r - R
+    const float2 am = __fadd2_rn(r0, t.nR);                              // r0 - R (exact on the far path)
+    const float2 hs = __ffma2_rn(r0, make_float2(-0.5f, -0.5f), t.nRh);  // -(r0 + R)/2
+    const float2 eh = __ffma2_rn(am, hs, th);                            // (r^2 - r0^2)/2
+    const float2 dr = __ffma2_rn(eh, ir, am);                            // r - R
     float2 sn, cs;
     if (KIND == RSI_STAGE_PISTON) {
         const float2 u = __ffma2_rn(k, dr, t.tau);
@@ -265,37 +259,47 @@ __device__ __forceinline__ void pair_far2(const TgtRef2& t, const float4& v0, co
     }
 }
 
-// one source of a packed tile, unpacked for the scalar near path: a = (px,
-// py, pz, |p|^2); PISTON b = (A, 0, 0, 0); RSI b = (beta, m, 0, 0) and n the
-// normal scaled by m (m (0, 0, 1) for flat sources)
-template <int KIND>
-__device__ __forceinline__ void unpack_source(const float* tile_rec, int rec_f, int i, float4& a, float4& b,
-                                              float4& n) {
-    const float* q = tile_rec + (i >> 1) * 2 * rec_f + (i & 1);
-    a = make_float4(q[0], q[2], -q[4], 2.0f * q[6]);
-    b = KIND == RSI_STAGE_RSI ? make_float4(q[8], q[10], 0.f, 0.f) : make_float4(q[8], 0.f, 0.f, 0.f);
-    n = rec_f == 12 ? make_float4(q[16], q[18], q[20], -q[22]) : make_float4(0.f, 0.f, q[10], 0.f);
+// two sources onto one target reference.  Far path (R > 2 tile radii, so
+// r / R lies in (1/2, 3/2)): r^2 = R^2 + 2 th.  Near path: r^2 from the
+// offsets Q - P, and pairs closer than 1e-12 m contribute nothing.
+template <int KIND, int NORM, bool NEAR>
+__device__ __forceinline__ void pair2(const TgtRef2& t, const float4& v0, const float4& v1, const float4& v2,
+                                      const float4& v3, const float4& n0, const float4& n1, float2 k, float2& ar1,
+                                      float2& ar2, float2& ai1, float2& ai2) {
+    const float2 px = make_float2(v0.x, v0.y), py = make_float2(v0.z, v0.w);
+    const float2 pzn = make_float2(v1.x, v1.y), pwh = make_float2(v1.z, v1.w);
+    const float2 th = __ffma2_rn(t.mx, px, __ffma2_rn(t.my, py, __ffma2_rn(t.mz, pzn, pwh)));  // (r^2 - R^2)/2
+    float2 r2, ir;
+    if (NEAR) {
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+        const float2 dx = __ffma2_rn(px, m1, t.Dx), dy = __ffma2_rn(py, m1, t.Dy), dz = __fadd2_rn(t.Dz, pzn);
+        r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        ir.x = r2.x > 1e-24f ? rsqrt_approx(r2.x) : 0.0f;
+        ir.y = r2.y > 1e-24f ? rsqrt_approx(r2.y) : 0.0f;
+    } else {
+        r2 = __ffma2_rn(th, make_float2(2.0f, 2.0f), t.R2);
+        ir.x = rsqrt_approx(r2.x);
+        ir.y = rsqrt_approx(r2.y);
+    }
+    pair_terms2<KIND, NORM>(t, th, r2, ir, v1, v2, v3, n0, n1, k, ar1, ar2, ai1, ai2);
 }
 
-// near path of the packed RSI records: one source (a, polar b, scaled n)
-// onto one target reference, added directly to the target's sums
-__device__ __forceinline__ void pair_near_polar(const TgtRef& t, const float4& a, const float4& b, const float4& nr,
-                                                float k, float& acc_r, float& acc_i) {
-    float dx = t.Dx - a.x, dy = t.Dy - a.y, dz = t.Dz - a.z;
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float tt = fmaf(t.mx, a.x, fmaf(t.my, a.y, fmaf(t.mz, a.z, a.w)));  // r^2 - R^2
-    float ir = rsqrt_approx(r2);
-    ir = r2 > 1e-24f ? ir : 0.0f;  // pairs closer than 1e-12 m contribute nothing
-    float r0 = r2 * ir;
-    float am = t.R - r0;
-    float e = fmaf(am, t.R + r0, tt);  // r^2 - r0^2
-    float dr = fmaf(e, 0.5f * ir, -am);
-    float nd = fmaf(nr.x, dx, fmaf(nr.y, dy, nr.z * dz));  // m n . (Q - P)
-    float s, c;
-    __sincosf(fmaf(k, dr, t.tau + b.x), &s, &c);  // tau + beta first: |tau + beta| <= 2 pi
-    float g = nd * (ir * ir);
-    acc_r = fmaf(-g, fmaf(ir, c, k * s), acc_r);  // g (-c/r - k s)
-    acc_i = fmaf(g, fmaf(-ir, s, k * c), acc_i);  // g (-s/r + k c)
+// every source pair of a staged packed tile onto the thread's TPT targets
+template <int KIND, int NORM, int TPT, bool NEAR>
+__device__ __forceinline__ void packed_tile(const float4* rec, int S, const TgtRef2 (&r2)[TPT], float2 k2,
+                                            float2 (&a1)[TPT], float2 (&a2)[TPT], float2 (&b1)[TPT],
+                                            float2 (&b2)[TPT]) {
+    constexpr int rec_f4 = (KIND == RSI_STAGE_RSI && NORM == RSI_NORMALS_POINTS) ? 3 : 2;
+#pragma unroll packed_unroll<KIND>()
+    for (int i = 0; i < S / 2; ++i) {
+        const float4* pr = rec + i * 2 * rec_f4;
+        const float4 v0 = pr[0], v1 = pr[1], v2 = pr[2], v3 = pr[3];
+        const float4 n0 = (rec_f4 == 3) ? pr[4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 n1 = (rec_f4 == 3) ? pr[5] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < TPT; ++q)
+            pair2<KIND, NORM, NEAR>(r2[q], v0, v1, v2, v3, n0, n1, k2, a1[q], a2[q], b1[q], b2[q]);
+    }
 }
 
 // One CTA's share of a stage: targets j0 .. j0 + TPT*kThreads - 1 against
@@ -368,54 +372,31 @@ __device__ __forceinline__ bool run_block(const BlockWork& w, uint8_t* smem, uin
             ai[q] = 0.0f;
         }
         if (VAR == 3) {
-            const int rec_f = rec_f4 * 4;
-            if (__all_sync(0xffffffffu, far_lane)) {
-                TgtRef2 r2[TPT];
-                float2 a1[TPT], a2[TPT], b1[TPT], b2[TPT];
+            TgtRef2 r2[TPT];
+            float2 a1[TPT], a2[TPT], b1[TPT], b2[TPT];
 #pragma unroll
-                for (int q = 0; q < TPT; ++q) {
-                    r2[q] = packed_reference(ref[q]);
-                    a1[q] = a2[q] = b1[q] = b2[q] = make_float2(0.f, 0.f);
-                }
-                const float2 k2 = make_float2(k, k);
-#pragma unroll packed_unroll<KIND>()
-                for (int i = 0; i < w.S / 2; ++i) {
-                    const float4* pr = rec + i * 2 * rec_f4;
-                    const float4 v0 = pr[0], v1 = pr[1], v2 = pr[2], v3 = pr[3];
-                    const float4 n0 = (rec_f4 == 3) ? pr[4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 n1 = (rec_f4 == 3) ? pr[5] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int q = 0; q < TPT; ++q) {
+                r2[q] = packed_reference(ref[q]);
+                a1[q] = a2[q] = b1[q] = b2[q] = make_float2(0.f, 0.f);
+            }
+            const float2 k2 = make_float2(k, k);
+            if (__all_sync(0xffffffffu, far_lane))
+                packed_tile<KIND, NORM, TPT, false>(rec, w.S, r2, k2, a1, a2, b1, b2);
+            else
+                packed_tile<KIND, NORM, TPT, true>(rec, w.S, r2, k2, a1, a2, b1, b2);
 #pragma unroll
-                    for (int q = 0; q < TPT; ++q)
-                        pair_far2<KIND, NORM>(r2[q], v0, v1, v2, v3, n0, n1, k2, a1[q], a2[q], b1[q], b2[q]);
-                }
-#pragma unroll
-                for (int q = 0; q < TPT; ++q) {
-                    if (KIND == RSI_STAGE_PISTON) {
-                        ar[q] = a1[q].x + a1[q].y;
-                        ai[q] = b1[q].x + b1[q].y;
-                    } else {
-                        // (-sum g/r cos - k sum g sin) + i (-sum g/r sin + k sum g cos), times e^{i tau}
-                        const float sr = fmaf(-k, a2[q].x + a2[q].y, -(a1[q].x + a1[q].y));
-                        const float si = fmaf(k, b2[q].x + b2[q].y, -(b1[q].x + b1[q].y));
-                        float st, ct;
-                        __sincosf(ref[q].tau, &st, &ct);
-                        ar[q] = fmaf(ct, sr, -st * si);
-                        ai[q] = fmaf(st, sr, ct * si);
-                    }
-                }
-            } else {
-                const float* tf = reinterpret_cast<const float*>(rec);
-#pragma unroll 1
-                for (int i = 0; i < w.S; ++i) {
-                    float4 ra, rb, rn;
-                    unpack_source<KIND>(tf, rec_f, i, ra, rb, rn);
-#pragma unroll
-                    for (int q = 0; q < TPT; ++q) {
-                        if (KIND == RSI_STAGE_PISTON)
-                            pair_near<KIND, NORM, 2>(ref[q], ra, rb, rn, k, ar[q], ai[q]);
-                        else
-                            pair_near_polar(ref[q], ra, rb, rn, k, ar[q], ai[q]);
-                    }
+            for (int q = 0; q < TPT; ++q) {
+                if (KIND == RSI_STAGE_PISTON) {
+                    ar[q] = a1[q].x + a1[q].y;
+                    ai[q] = b1[q].x + b1[q].y;
+                } else {
+                    // (-sum g/r cos - k sum g sin) + i (-sum g/r sin + k sum g cos), times e^{i tau}
+                    const float sr = fmaf(-k, a2[q].x + a2[q].y, -(a1[q].x + a1[q].y));
+                    const float si = fmaf(k, b2[q].x + b2[q].y, -(b1[q].x + b1[q].y));
+                    float st, ct;
+                    __sincosf(ref[q].tau, &st, &ct);
+                    ar[q] = fmaf(ct, sr, -st * si);
+                    ai[q] = fmaf(st, sr, ct * si);
                 }
             }
         } else if (__all_sync(0xffffffffu, far_lane)) {
