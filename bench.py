@@ -45,11 +45,12 @@ OPS = {
     "piston": {"fp32": 7.5, "mufu": 3, "lds": 1.0, "fma_pipe": 14},
     # ray-tracing pair (Sec. 2.2), two transducer points per f32x2
     # instruction: linear prediction of the crossing from the tile's reference
-    # ray, 2 Newton steps (16 packed FP32 and 3 MUFU per point each), ~110
-    # packed FP32 per two pairs in all plus 6 scalar (the products of the fast
-    # divisions, the sincos scaling), ~14 compares, selects and clamps, 14 MUFU
-    # (the path differences by a Newton step, T12 inside the amplitude's rsqrt)
-    "raytrace": {"fp32": 61, "alu": 14, "mufu": 14, "lds": 2.0, "fma_pipe": 116},
+    # ray, 1 Newton step (15 packed FP32 per two points, 3 MUFU per point) and
+    # its error bound (3 packed), ~97 packed FP32 per two pairs in all plus 5
+    # scalar (the products of the fast divisions, the sincos scaling), ~13
+    # compares, selects and clamps, 11 MUFU (the path differences by a Newton
+    # step, T12 inside the amplitude's rsqrt); safeguarded steps not counted
+    "raytrace": {"fp32": 53.5, "alu": 13, "mufu": 11, "lds": 2.0, "fma_pipe": 102},
 }
 # "fma_pipe": FP32-pipe lane cycles per pair: a packed f32x2 instruction keeps
 # the pipe two cycles (two FMAs per lane), a scalar one cycle.

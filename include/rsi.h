@@ -288,8 +288,9 @@ typedef struct rsi_raytrace {
     int32_t splits;      /* transducer-point splits (>= 1); 0 = auto                */
     int32_t newton;      /* Newton steps per pair for the crossing point after a
                             linear prediction from the tile's reference ray, before
-                            the convergence test (steps then continue, at most 12,
-                            until the crossing moves < 1 nm); 0 = 2              */
+                            the convergence test (safeguarded steps then continue,
+                            at most 12, until the error bound of the last Newton
+                            step, 1.5 max(1/D1, 1/D2) step^2, is < 1 nm); 0 = 1  */
     int32_t reserved;
 } rsi_raytrace;
 

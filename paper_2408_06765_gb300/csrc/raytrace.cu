@@ -25,7 +25,17 @@ constexpr int kRtThreads = 256;
 // Crossing-point convergence: the phase is second order in the crossing
 // error (Fermat), the amplitude first order; 1 nm keeps both below 1e-6 for
 // path legs down to 0.1 mm at 10 MHz in water.
+//
+// The test is on the error left after the last Newton step, not on the step
+// itself: for Snell's residual G(t) = s1 t / D1 - s2 b / D2 (b = rho - t),
+//   G'  = s1 h1^2 / D1^3 + s2 h2^2 / D2^3,
+//   |G''| <= 3 s1 h1^2 t / D1^5 + 3 s2 h2^2 b / D2^5 <= 3 G' max(1/D1, 1/D2),
+// so a Newton step of length q from t leaves |t' - t*| <~ |G''| q^2 / (2 G')
+// <= 1.5 max(1/D1, 1/D2) q^2.  In FP32 the step itself never settles below
+// the rounding of G (a few nm on 50 mm legs), so a test on |q| would send
+// most rays into the safeguarded loop for nothing.
 constexpr float kCrossTol = 1e-9f;
+constexpr float kCrossCurv = 1.5f;
 constexpr int kCrossExtra = 12;
 
 struct RtArgs {
@@ -80,14 +90,16 @@ __device__ __forceinline__ void df_sqrt(float sh, float sl, float& rh, float& rl
 }
 
 // Snell's residual of a crossing at horizontal distance t from the source
-// foot (b = rho - t beyond it): G = s1 sin a1 - s2 sin a2, and its slope
+// foot (b = rho - t beyond it): G = s1 sin a1 - s2 sin a2, its slope
 // dG = s1 h1^2 / D1^3 + s2 h2^2 / D2^3 (h1q = h1^2, s1h = s1 h1^2, s2h = s2 h2^2)
+// and m = max(1/D1, 1/D2), the curvature bound of the convergence test
 __device__ __forceinline__ void snell_residual(float t, float b, float h1q, float h2q, float s1, float s2, float s1h,
-                                               float s2h, float& G, float& dG) {
+                                               float s2h, float& G, float& dG, float& m) {
     const float r1 = rsqrt_ap(fmaf(t, t, h1q));
     const float r2 = rsqrt_ap(fmaf(b, b, h2q));
     G = fmaf(s1 * t, r1, -(s2 * b) * r2);
     dG = fmaf(s1h, r1 * r1 * r1, s2h * (r2 * r2 * r2));
+    m = fmaxf(r1, r2);
 }
 
 __device__ __forceinline__ RayRef ray_reference(float qxh, float qxl, float qyh, float qyl, float qzh, float qzl,
@@ -118,8 +130,8 @@ __device__ __forceinline__ RayRef ray_reference(float qxh, float qxl, float qyh,
     const float h1q = h1h * h1h, h2q = h2h * h2h;
 #pragma unroll 1
     for (int it = 0; it < 24; ++it) {
-        float G, dG;
-        snell_residual(t, rh - t, h1q, h2q, a.s1, a.s2, a.s1 * h1q, a.s2 * h2q, G, dG);
+        float G, dG, m;
+        snell_residual(t, rh - t, h1q, h2q, a.s1, a.s2, a.s1 * h1q, a.s2 * h2q, G, dG, m);
         if (G > 0.0f)
             hi = t;
         else
@@ -177,24 +189,26 @@ __device__ __forceinline__ RayRef ray_reference(float qxh, float qxl, float qyh,
     return R;
 }
 
-// safeguarded steps for the crossing offset dt of one pair whose plain Newton
-// steps still move it by `step`: Newton inside a bracket of the monotone
-// residual, bisection otherwise, until the step falls below kCrossTol
+// safeguarded steps for the crossing offset dt of one pair whose Newton
+// steps may still leave more than kCrossTol (est, the bound above): Newton
+// inside a bracket of the monotone residual, bisection otherwise, until a
+// Newton step's bound falls below kCrossTol
 __device__ __forceinline__ float cross_safeguarded(const RayRef& R, const RtArgs& a, float h1q, float h2q, float s1h,
-                                                float bfix, float lo0, float hi0, float dt, float step) {
+                                                float bfix, float lo0, float hi0, float dt, float est) {
     float lo = lo0, hi = hi0;
 #pragma unroll 1
-    for (int it = 0; it < kCrossExtra && fabsf(step) > kCrossTol; ++it) {
-        float G, dG;
-        snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG);
+    for (int it = 0; it < kCrossExtra && est > kCrossTol; ++it) {
+        float G, dG, m;
+        snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG, m);
         if (G > 0.0f)
             hi = dt;
         else
             lo = dt;
-        const float dn = dt - __fdividef(G, dG);
-        const float nt = (dn >= lo && dn <= hi) ? dn : 0.5f * (lo + hi);
-        step = nt - dt;
-        dt = nt;
+        const float q = __fdividef(G, dG);
+        const float dn = dt - q;
+        const bool in = dn >= lo && dn <= hi;
+        est = in ? kCrossCurv * m * (q * q) : INFINITY;
+        dt = in ? dn : 0.5f * (lo + hi);
     }
     return dt;
 }
@@ -230,21 +244,24 @@ __device__ __forceinline__ void ray_pair(const RayRef& R, const float4& rec, flo
     const float lo0 = -R.tc, hi0 = bfix;
     float dt = -fmaf(R.a_r, drho, R.a_h * pz);  // linear prediction from the reference ray
     dt = fminf(fmaxf(dt, lo0), hi0);
-    float step = INFINITY;
-    // plain Newton steps (kept inside the segment) from the prediction
+    float est = INFINITY;
+    // plain Newton steps (kept inside the segment) from the prediction; the
+    // bound uses the unclamped step, which also bounds a clamped one (the
+    // root lies inside the segment)
     const int nw = NW ? NW : a.newton;
 #pragma unroll
     for (int it = 0; it < (NW ? NW : 16); ++it) {
         if (!NW && it >= nw) break;
-        float G, dG;
-        snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG);
-        const float nt = fminf(fmaxf(dt - __fdividef(G, dG), lo0), hi0);
-        step = nt - dt;
-        dt = nt;
+        float G, dG, m;
+        snell_residual(R.tc + dt, bfix - dt, h1q, h2q, a.s1, a.s2, s1h, R.s2h22, G, dG, m);
+        const float q = __fdividef(G, dG);
+        est = kCrossCurv * m * (q * q);
+        dt = fminf(fmaxf(dt - q, lo0), hi0);
     }
-    // then, for the rays still moving by more than kCrossTol (those that graze
-    // the interface near the target converge more slowly), safeguarded steps
-    if (fabsf(step) > kCrossTol) dt = cross_safeguarded(R, a, h1q, h2q, s1h, bfix, lo0, hi0, dt, step);
+    // then, for the rays that may still be off by more than kCrossTol (those
+    // that graze the interface near the target converge more slowly),
+    // safeguarded steps
+    if (est > kCrossTol) dt = cross_safeguarded(R, a, h1q, h2q, s1h, bfix, lo0, hi0, dt, est);
     // e1 = (X - P) - (X_c - c) = (dt u + t_c (u - u_c), -p_z); e2 = -(p_h + e1_h, 0)
     const float e1x = fmaf(dt, ux, R.tc * wx), e1y = fmaf(dt, uy, R.tc * wy), e1z = -pz;
     const float e2x = -(px + e1x), e2y = -(py + e1y);
@@ -317,7 +334,7 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     float2 dt = neg2(__ffma2_rn(f2(R.a_r), drho, __fmul2_rn(f2(R.a_h), pz)));
     dt.x = fminf(fmaxf(dt.x, lo0), bfix.x);
     dt.y = fminf(fmaxf(dt.y, lo0), bfix.y);
-    float2 step = f2(INFINITY);
+    float2 est = f2(INFINITY);
     const int nw = NW ? NW : a.newton;
 #pragma unroll
     for (int it = 0; it < (NW ? NW : 16); ++it) {
@@ -329,13 +346,14 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
         const float2 G = __ffma2_rn(__fmul2_rn(f2(a.s1), t), e1, neg2(__fmul2_rn(__fmul2_rn(f2(a.s2), b), e2)));
         const float2 dG = __ffma2_rn(s1h, __fmul2_rn(__fmul2_rn(e1, e1), e1),
                                      __fmul2_rn(f2(R.s2h22), __fmul2_rn(__fmul2_rn(e2, e2), e2)));
-        const float2 dn = sub2(dt, make_float2(__fdividef(G.x, dG.x), __fdividef(G.y, dG.y)));
-        const float2 nt = make_float2(fminf(fmaxf(dn.x, lo0), bfix.x), fminf(fmaxf(dn.y, lo0), bfix.y));
-        step = sub2(nt, dt);
-        dt = nt;
+        const float2 q = make_float2(__fdividef(G.x, dG.x), __fdividef(G.y, dG.y));
+        const float2 m = make_float2(fmaxf(e1.x, e2.x), fmaxf(e1.y, e2.y));
+        est = __fmul2_rn(__fmul2_rn(f2(kCrossCurv), m), __fmul2_rn(q, q));
+        const float2 dn = sub2(dt, q);
+        dt = make_float2(fminf(fmaxf(dn.x, lo0), bfix.x), fminf(fmaxf(dn.y, lo0), bfix.y));
     }
-    if (fabsf(step.x) > kCrossTol) dt.x = cross_safeguarded(R, a, h1q.x, h2q, s1h.x, bfix.x, lo0, bfix.x, dt.x, step.x);
-    if (fabsf(step.y) > kCrossTol) dt.y = cross_safeguarded(R, a, h1q.y, h2q, s1h.y, bfix.y, lo0, bfix.y, dt.y, step.y);
+    if (est.x > kCrossTol) dt.x = cross_safeguarded(R, a, h1q.x, h2q, s1h.x, bfix.x, lo0, bfix.x, dt.x, est.x);
+    if (est.y > kCrossTol) dt.y = cross_safeguarded(R, a, h1q.y, h2q, s1h.y, bfix.y, lo0, bfix.y, dt.y, est.y);
     const float2 e1x = __ffma2_rn(dt, ux, __fmul2_rn(f2(R.tc), wx));
     const float2 e1y = __ffma2_rn(dt, uy, __fmul2_rn(f2(R.tc), wy));
     const float2 e1z = neg2(pz);
@@ -525,7 +543,7 @@ int rt_plan(const rsi_raytrace& rt, int64_t n_src, int64_t n_tgt, RtPlan& p) {
     if (splits < 0) return rsi_fail(RSI_E_INVAL, "rsi_raytrace_field: splits must be >= 0");
     if (splits == 0) {
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, raytrace_kernel<kTpt, 2>, kRtThreads,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, raytrace_kernel<kTpt, 1>, kRtThreads,
                                                           rt_smem(p.tile_bytes)) != cudaSuccess ||
             occ < 1)
             occ = 1;
@@ -624,7 +642,7 @@ extern "C" int rsi_raytrace_field(const rsi_raytrace* rt, const void* src_points
     a.Tn = float(2.0 * rt->rho1 * rt->c2 / z1);
     a.Td1 = float(rt->rho2 * rt->c2 / z1);
     a.Td2 = 1.0f;
-    a.newton = rt->newton ? rt->newton : 2;
+    a.newton = rt->newton ? rt->newton : 1;
     a.tp = two_pi_split();
     double2* field = reinterpret_cast<double2*>(tgt_field);
     a.out = p.splits > 1 ? reinterpret_cast<double2*>(tiles + p.tiles_bytes) : field;
