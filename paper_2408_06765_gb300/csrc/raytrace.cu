@@ -296,11 +296,13 @@ __device__ __forceinline__ void ray_pair(const RayRef& R, const float4& rec, flo
 #endif
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
-__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __fadd2_rn(x, neg2(y)); }
+// x - y as one packed FMA, y (-1) + x: rounded once, so equal to the
+// subtraction; a packed negation would be an instruction of its own
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, f2(-1.0f), x); }
 
-// ray_pair for two transducer points at once: the same operations in the
-// same order, the additions, products and FMAs two at a time (f32x2), the
+// ray_pair for two transducer points at once: the same quantities, the
+// additions, products and FMAs two at a time (f32x2), every sign folded into
+// a negated per-tile constant or an FMA by -1 (no packed negations), the
 // reciprocal square roots, divisions, clamps and sincos per point, and the
 // safeguarded steps only for a point whose ray has not converged
 template <int NW>
@@ -315,13 +317,13 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     float2 ux = __fmul2_rn(vx, iv), uy = __fmul2_rn(vy, iv);
     if (!okx) ux.x = R.ux, uy.x = R.uy;
     if (!oky) ux.y = R.ux, uy.y = R.uy;
-    const float2 dpp = __ffma2_rn(f2(2.0f * R.dx), px,
-                                  __ffma2_rn(f2(2.0f * R.dy), py, neg2(__ffma2_rn(px, px, __fmul2_rn(py, py)))));
-    const float2 dd = __fadd2_rn(__fadd2_rn(f2(R.rho), rho), f2(1e-30f));
+    // rho_c^2 - rho^2 = 2 d.p_h - |p_h|^2 = px (2 dx - px) + py (2 dy - py)
+    const float2 dpp = __ffma2_rn(px, sub2(f2(2.0f * R.dx), px), __fmul2_rn(py, sub2(f2(2.0f * R.dy), py)));
+    const float2 dd = __fadd2_rn(f2(R.rho + 1e-30f), rho);
     const float2 drho = make_float2(__fdividef(dpp.x, dd.x), __fdividef(dpp.y, dd.y));
     const float2 sw = __fmul2_rn(f2(R.irho), iv);
-    float2 wx = __fmul2_rn(__ffma2_rn(f2(R.dx), drho, __fmul2_rn(neg2(px), f2(R.rho))), sw);
-    float2 wy = __fmul2_rn(__ffma2_rn(f2(R.dy), drho, __fmul2_rn(neg2(py), f2(R.rho))), sw);
+    float2 wx = __fmul2_rn(__ffma2_rn(f2(R.dx), drho, __fmul2_rn(px, f2(-R.rho))), sw);
+    float2 wy = __fmul2_rn(__ffma2_rn(f2(R.dy), drho, __fmul2_rn(py, f2(-R.rho))), sw);
     if (!(R.irho > 0.0f && iv.x > 0.0f)) wx.x = ux.x - R.ux, wy.x = uy.x - R.uy;
     if (!(R.irho > 0.0f && iv.y > 0.0f)) wx.y = ux.y - R.ux, wy.y = uy.y - R.uy;
     const float2 h1 = sub2(f2(R.H1), pz);
@@ -331,7 +333,7 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     const float2 s1h = __fmul2_rn(f2(a.s1), h1q);
     const float2 bfix = sub2(f2(R.bc), drho);
     const float lo0 = -R.tc;
-    float2 dt = neg2(__ffma2_rn(f2(R.a_r), drho, __fmul2_rn(f2(R.a_h), pz)));
+    float2 dt = __ffma2_rn(f2(-R.a_r), drho, __fmul2_rn(f2(-R.a_h), pz));
     dt.x = fminf(fmaxf(dt.x, lo0), bfix.x);
     dt.y = fminf(fmaxf(dt.y, lo0), bfix.y);
     float2 est = f2(INFINITY);
@@ -343,7 +345,7 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
         const float2 q1 = __ffma2_rn(t, t, h1q), q2 = __ffma2_rn(b, b, f2(h2q));
         const float2 e1 = make_float2(rsqrt_ap(q1.x), rsqrt_ap(q1.y));
         const float2 e2 = make_float2(rsqrt_ap(q2.x), rsqrt_ap(q2.y));
-        const float2 G = __ffma2_rn(__fmul2_rn(f2(a.s1), t), e1, neg2(__fmul2_rn(__fmul2_rn(f2(a.s2), b), e2)));
+        const float2 G = __ffma2_rn(__fmul2_rn(f2(a.s1), t), e1, __fmul2_rn(__fmul2_rn(f2(-a.s2), b), e2));
         const float2 dG = __ffma2_rn(s1h, __fmul2_rn(__fmul2_rn(e1, e1), e1),
                                      __fmul2_rn(f2(R.s2h22), __fmul2_rn(__fmul2_rn(e2, e2), e2)));
         const float2 q = make_float2(__fdividef(G.x, dG.x), __fdividef(G.y, dG.y));
@@ -354,23 +356,26 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     }
     if (est.x > kCrossTol) dt.x = cross_safeguarded(R, a, h1q.x, h2q, s1h.x, bfix.x, lo0, bfix.x, dt.x, est.x);
     if (est.y > kCrossTol) dt.y = cross_safeguarded(R, a, h1q.y, h2q, s1h.y, bfix.y, lo0, bfix.y, dt.y, est.y);
+    // e1 = (dt u + t_c w, -p_z) and g = -e2_h = p_h + e1_h; the squares of
+    // -p_z and -g equal those of p_z and g, and the signs of the cross terms
+    // go into the per-tile constants -2 H1 and -2 b_c
     const float2 e1x = __ffma2_rn(dt, ux, __fmul2_rn(f2(R.tc), wx));
     const float2 e1y = __ffma2_rn(dt, uy, __fmul2_rn(f2(R.tc), wy));
-    const float2 e1z = neg2(pz);
-    const float2 e2x = neg2(__fadd2_rn(px, e1x)), e2y = neg2(__fadd2_rn(py, e1y));
+    const float2 gx = __fadd2_rn(px, e1x), gy = __fadd2_rn(py, e1y);
     const float2 t1 = __ffma2_rn(f2(2.0f * R.tc), __ffma2_rn(f2(R.ux), e1x, __fmul2_rn(f2(R.uy), e1y)),
-                                 __ffma2_rn(f2(2.0f * R.H1), e1z,
-                                            __ffma2_rn(e1x, e1x, __ffma2_rn(e1y, e1y, __fmul2_rn(e1z, e1z)))));
-    const float2 t2 = __ffma2_rn(f2(2.0f * R.bc), __ffma2_rn(f2(R.ux), e2x, __fmul2_rn(f2(R.uy), e2y)),
-                                 __ffma2_rn(e2x, e2x, __fmul2_rn(e2y, e2y)));
+                                 __ffma2_rn(f2(-2.0f * R.H1), pz,
+                                            __ffma2_rn(e1x, e1x, __ffma2_rn(e1y, e1y, __fmul2_rn(pz, pz)))));
+    const float2 t2 = __ffma2_rn(f2(-2.0f * R.bc), __ffma2_rn(f2(R.ux), gx, __fmul2_rn(f2(R.uy), gy)),
+                                 __ffma2_rn(gx, gx, __fmul2_rn(gy, gy)));
     const float2 q1 = __ffma2_rn(f2(R.D1), f2(R.D1), t1), q2 = __ffma2_rn(f2(R.D2), f2(R.D2), t2);
     const float2 ir1 = make_float2(rsqrt_ap(q1.x), rsqrt_ap(q1.y)), ir2 = make_float2(rsqrt_ap(q2.x), rsqrt_ap(q2.y));
     const float2 D1 = __fmul2_rn(q1, ir1), D2 = __fmul2_rn(q2, ir2);
-    const float2 s1d = __fadd2_rn(f2(R.D1), D1), s2d = __fadd2_rn(f2(R.D2), D2);
-    // D - Dc by one Newton step, as in ray_pair
-    const float2 am1 = sub2(D1, f2(R.D1)), am2 = sub2(D2, f2(R.D2));
-    const float2 dD1 = __ffma2_rn(__ffma2_rn(neg2(am1), s1d, t1), __fmul2_rn(f2(0.5f), ir1), am1);
-    const float2 dD2 = __ffma2_rn(__ffma2_rn(neg2(am2), s2d, t2), __fmul2_rn(f2(0.5f), ir2), am2);
+    // D - Dc by one Newton step, as in ray_pair: am = D - Dc, and
+    // t - am (D + Dc) = am (-(D + Dc)) + t with -(D + Dc) = D (-1) - Dc
+    const float2 am1 = __fadd2_rn(D1, f2(-R.D1)), am2 = __fadd2_rn(D2, f2(-R.D2));
+    const float2 ns1 = __ffma2_rn(D1, f2(-1.0f), f2(-R.D1)), ns2 = __ffma2_rn(D2, f2(-1.0f), f2(-R.D2));
+    const float2 dD1 = __ffma2_rn(__ffma2_rn(am1, ns1, t1), __fmul2_rn(f2(0.5f), ir1), am1);
+    const float2 dD2 = __ffma2_rn(__ffma2_rn(am2, ns2, t2), __fmul2_rn(f2(0.5f), ir2), am2);
     const float2 u = __ffma2_rn(f2(k1), dD1, __ffma2_rn(f2(k2), dD2, f2(R.tau)));
     const float2 cos1 = __fmul2_rn(h1, ir1), cos2 = __fmul2_rn(f2(h2), ir2);
     const float2 tn = __fmul2_rn(f2(a.Tn), cos1), td = __ffma2_rn(f2(a.Td1), cos1, __fmul2_rn(f2(a.Td2), cos2));

@@ -516,7 +516,12 @@ __device__ __forceinline__ void prep_tile(int kind, int normals, int S, int64_t 
     float* rec = reinterpret_cast<float*>(tiles + size_t(tile) * tile_bytes + RSI_TILE_HDR_BYTES) +
                  (packed ? size_t(threadIdx.x >> 1) * 2 * rec_f + (threadIdx.x & 1) : size_t(threadIdx.x) * rec_f);
     const int fs = packed ? 2 : 1;  // stride between the fields of one source
-    float px = 4.0f, py = 4.0f, pz = 4.0f, radius2 = 0.0f;
+    // padding records (past the last source of the last tile) carry a zero
+    // amplitude and sit metres from the tile centre, so that no target comes
+    // near them; they sit behind the transducer (-z), so that the ray-tracing
+    // kernel, which reads the piston's tiles, solves a proper crossing for
+    // them too and every padding term is a finite value times zero
+    float px = 4.0f, py = 4.0f, pz = -4.0f, radius2 = 0.0f;
     float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
     float nx = 0.f, ny = 0.f, nz = 1.f;
     float beta = 0.f, mag = 0.f;  // packed RSI records: B = mag e^{i beta}
