@@ -256,13 +256,24 @@ def measure_unit_rates(rsi, torch, kinds=("ffma", "rsqrt", "sin")):
 ISSUE_LANES_PER_SM, MUFU_LANES_PER_SM = 128, 16
 
 
-def multi_ops(kind: str, nf: int) -> dict:
+def multi_ops(kind: str, nf: int, harmonic: bool = False) -> dict:
     """Per pair-term counts of the multi-frequency stage kernel (nf frequencies
     on shared points, two sources per packed f32x2 instruction, one target per
     thread): the shared geometry once per source pair, phase, sincos and
     epilogue per frequency, plus one scalar scaling of each sincos argument;
     of the packed record of a source pair, 2 + nf float4 (RSI: geometry and
-    the polar amplitudes) or 4 (piston) are read once per target."""
+    the polar amplitudes) or 4 (piston) are read once per target.  harmonic:
+    three frequencies, the third formed from the first by the double angle
+    (no sincos): RSI 14 packed for it (e^{2iu} 6, the product with the
+    source's constant 4, four accumulations) and the padding float4 read;
+    piston 6 packed (e^{2iu} 4, two accumulations)."""
+    if harmonic:
+        assert nf == 3
+        if kind == "rsi":  # per source pair: shared 14, two frequencies 7 + 2 scalar each, derived 14
+            return {"fp32": (14.0 + 2 * 9.0 + 14.0) / 6, "mufu": 5.0 / 3, "lds": 6.0 / 6,
+                    "fma_pipe": (14.0 + 2 * 8.0 + 14.0) / 3}
+        return {"fp32": (10.0 + 2 * 5.0 + 6.0) / 6, "mufu": 5.0 / 3, "lds": 4.0 / 6,
+                "fma_pipe": (10.0 + 2 * 4.0 + 6.0) / 3}
     if kind == "rsi":  # per source pair: shared 14 packed, per f 7 packed
         return {"fp32": 14.0 / (2 * nf) + 3.5 + 1.0, "mufu": 2.0 + 1.0 / nf, "lds": (2.0 + nf) / (2.0 * nf),
                 "fma_pipe": 14.0 / nf + 7.0 + 1.0}
@@ -545,8 +556,12 @@ def run_ours(args):
     clk_hz = (clk["sm_mhz"] if clk and clk.get("sm_mhz") else
               rates["ffma"] / (ISSUE_LANES_PER_SM * n_sm) / 1e6) * 1e6
     nf = len(cfgs) if multi else 1
-    rsi_ops = multi_ops("rsi", nf) if multi else OPS["rsi"]
-    pis_ops = multi_ops("piston", nf) if multi else OPS["piston"]
+    # does the kernel form one frequency from another by the double angle?
+    harm = multi and nf == 3 and rsi.stage_multi_shared_harmonic(
+        rsi.stage_struct(rsi.STAGE_RSI, "fp32c", 1.0, 1.0),
+        [rsi.wavenumber(c["freq"], c["media"][-1]["c"]) for c in cfgs])
+    rsi_ops = multi_ops("rsi", nf, harm) if multi else OPS["rsi"]
+    pis_ops = multi_ops("piston", nf, harm) if multi else OPS["piston"]
     peak, limiter = alu_roofline("rsi", n_sm, clk_hz, rsi_ops)
     pis_avg = pis_ms * 1e-3 / max(1, pis_n)
     pis_peak, _ = alu_roofline("piston", n_sm, clk_hz, pis_ops)
@@ -554,7 +569,7 @@ def run_ours(args):
             "achieved": achieved / 1e9,
             "peak": peak / 1e9, "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
             "limiter": limiter,
-            "ops_per_pair": rsi_ops,
+            "ops_per_pair": rsi_ops, "harmonic_shared": bool(harm),
             "peak_source": "unit counts (4 issue slots of 32 lanes and 16 MUFU lanes per SM per clock) x "
                            f"{n_sm} SMs x the median SM clock of the timed region "
                            f"({clk_hz / 1e6:.0f} MHz)",

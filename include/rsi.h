@@ -209,13 +209,21 @@ int rsi_propagate_stage(const rsi_stage *st,
  * FP32C only, 2 <= nf <= 4; st->variant 0 or 3: two sources per packed
  * f32x2 instruction, 2: scalar.  Each frequency's result equals a
  * single-frequency rsi_propagate_stage to rounding; other conventions as
- * rsi_propagate_stage.  The workspace size depends on nf and the variant.   */
+ * rsi_propagate_stage.  The workspace size depends on nf and the variant.
+ * Shared harmonic: with nf = 3, the packed variant and one wavenumber twice
+ * another (k_j = 2 k_i to a relative 2^-40; with one sound speed, one
+ * frequency twice another), e^{i k_j (r - R)} is formed from e^{i k_i (r - R)}
+ * by the double angle on pairs away from the tile, two MUFU operations per
+ * pair fewer; the result stays a single-frequency stage to rounding.        */
 size_t rsi_stage_multi_workspace_bytes(const rsi_stage *st, int32_t nf, const double *ks, int64_t n_src,
                                        int64_t n_tgt);
 int rsi_propagate_stage_multi(const rsi_stage *st, int32_t nf, const double *ks,
                               const void *src_points, int64_t n_src, const double *src_sigma,
                               const void *tgt_points, int64_t n_tgt, double *tgt_field,
                               void *workspace, size_t workspace_bytes, void *stream);
+/* 1 if rsi_propagate_stage_multi shares a harmonic for these wavenumbers and
+ * this stage (above), 0 if not, a negative status on invalid input.        */
+int rsi_stage_multi_shared_harmonic(const rsi_stage *st, int32_t nf, const double *ks);
 
 /* The paper has no counterpart to this entry point; it exists for callers
  * that cannot give the library device memory for scratch (a latency-bound

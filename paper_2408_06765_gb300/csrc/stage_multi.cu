@@ -38,6 +38,11 @@ struct MultiArgs {
     double2* field;  // the fields [nf][n_tgt] (the last split of a target block sums into it)
     unsigned* done;  // per target block: splits finished (zeroed before the launch)
     int* status;
+    // frequency f of the kernel is the caller's frequency perm[f]; with harm,
+    // k_{nf-1} = 2 k_0 and the far path takes frequency nf-1 from frequency 0
+    // (double angle) instead of its own sincos
+    int perm[kMaxNF];
+    int harm;
 };
 
 // Tile records (float4 units): [p.x, p.y, p.z, |p|^2], then
@@ -240,11 +245,26 @@ __device__ __forceinline__ MRef2 packed_mref(const MRef& t) {
     return r;
 }
 
+// Harmonic sharing (HM, three frequencies with k_2 = 2 k_0): with
+// E_0 = e^{i u_0} from frequency 0's sincos, e^{2 i u_0} = (c - s)(c + s) + i 2 s c
+// by the double angle (that form keeps the modulus |E_0|^2 at every angle;
+// 2 c^2 - 1 would turn the sincos's modulus error into an angle-dependent one,
+// 1.4e-5 on the coherent piston sum of the 5 and 10 MHz workload), and
+//   piston  u_2 = k_2 (r - R) + tau_2 = 2 u_0 + (tau_2 - 2 tau_0): the sums of
+//           A e^{2 i u_0} / r are turned by e^{i (tau_2 - 2 tau_0)} once per tile;
+//   RSI     m_2 e^{i u_2} = c_2 e^{2 i u_0} with the per-source constant
+//           c_2 = m_2 e^{i (beta_2 - 2 beta_0)}, kept in the record's padding
+//           float4 (the near path still reads beta_2, m_2).
+// That replaces two MUFU operations per pair by a few FP32 ones.  The doubled
+// angle carries twice the sincos's angle error of u_0: on the 2.25, 5 and
+// 10 MHz workload the 10 MHz image is 1.0e-6 from the FP64 oracle (5.5e-7
+// with its own sincos).
+//
 // two sources (records pr[0..RF4*2-1], packed) onto one target, far path;
 // acc[f] = (sum m h/r c, sum m h s, sum m h/r s, sum m h c) of k_f (r - R) +
 // beta_f for RSI, or (sum A c / r, -, sum A s / r, -) of k_f (r - R) + tau_f
-// for the piston
-template <int KIND, int NORM, int NF>
+// for the piston (2 u_0 for the shared frequency)
+template <int KIND, int NORM, int NF, int HM>
 __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, const float2* kv,
                                            float2 (&acc)[NF][4]) {
     const float4 v0 = pr[0], v1 = pr[1];
@@ -260,15 +280,24 @@ __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, con
     const float2 hs = __ffma2_rn(r0, make_float2(-0.5f, -0.5f), t.nRh);  // -(r0 + R)/2
     const float2 eh = __ffma2_rn(am, hs, th);                            // (r^2 - r0^2)/2
     const float2 dr = __ffma2_rn(eh, ir, am);
+    float2 sn0, cs0;  // e^{i u_0}, kept for the shared frequency
     if (KIND == RSI_STAGE_PISTON) {
         const float4 va = pr[2];
         const float2 amp = __fmul2_rn(make_float2(va.x, va.y), ir);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
             float2 sn, cs;
-            __sincosf(u.x, &sn.x, &cs.x);
-            __sincosf(u.y, &sn.y, &cs.y);
+            if (HM && f == NF - 1) {
+                // e^{2 i u_0} = (c - s)(c + s) + i 2 s c
+                const float2 c2 = __fadd2_rn(cs0, cs0);
+                cs = __fmul2_rn(__ffma2_rn(sn0, make_float2(-1.0f, -1.0f), cs0), __fadd2_rn(cs0, sn0));
+                sn = __fmul2_rn(sn0, c2);
+            } else {
+                const float2 u = __ffma2_rn(kv[f], dr, t.tau[f]);
+                __sincosf(u.x, &sn.x, &cs.x);
+                __sincosf(u.y, &sn.y, &cs.y);
+                if (f == 0) sn0 = sn, cs0 = cs;
+            }
             acc[f][0] = __ffma2_rn(amp, cs, acc[f][0]);
             acc[f][2] = __ffma2_rn(amp, sn, acc[f][2]);
         }
@@ -287,11 +316,29 @@ __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, con
         const float2 hr = __fmul2_rn(h, ir);
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
+            if (HM && f == NF - 1) {
+                // (er, ei) = c_2 e^{2 i u_0}, c_2 = (cr, ci) from the padding float4
+                const float4 cc = pr[2 + NF];
+                const float2 cr = make_float2(cc.x, cc.y), ci = make_float2(cc.z, cc.w);
+                const float2 c2 = __fadd2_rn(cs0, cs0);
+                // cos 2 u_0 = (c - s)(c + s): modulus |E_0|^2 whatever the angle
+                const float2 cq = __fmul2_rn(__ffma2_rn(sn0, make_float2(-1.0f, -1.0f), cs0), __fadd2_rn(cs0, sn0));
+                const float2 sq = __fmul2_rn(sn0, c2);                                      // sin 2 u_0
+                const float2 nsq = __fmul2_rn(sn0, __fmul2_rn(cs0, make_float2(-2.0f, -2.0f)));  // -sin 2 u_0
+                const float2 er = __ffma2_rn(cr, cq, __fmul2_rn(ci, nsq));
+                const float2 ei = __ffma2_rn(cr, sq, __fmul2_rn(ci, cq));
+                acc[f][0] = __ffma2_rn(hr, er, acc[f][0]);
+                acc[f][1] = __ffma2_rn(h, ei, acc[f][1]);
+                acc[f][2] = __ffma2_rn(hr, ei, acc[f][2]);
+                acc[f][3] = __ffma2_rn(h, er, acc[f][3]);
+                continue;
+            }
             const float4 b = pr[2 + f];  // (beta_f, m_f) of both sources
             const float2 u = __ffma2_rn(kv[f], dr, make_float2(b.x, b.y));
             float2 sn, cs;
             __sincosf(u.x, &sn.x, &cs.x);
             __sincosf(u.y, &sn.y, &cs.y);
+            if (f == 0) sn0 = sn, cs0 = cs;
             const float2 m = make_float2(b.z, b.w);
             const float2 g = __fmul2_rn(h, m), gr = __fmul2_rn(hr, m);
             acc[f][0] = __ffma2_rn(gr, cs, acc[f][0]);
@@ -324,7 +371,7 @@ __device__ __forceinline__ void munpack(const float* tile_rec, int i, float4* r)
     }
 }
 
-template <int KIND, int NORM, int NF, int PK>
+template <int KIND, int NORM, int NF, int PK, int HM>
 __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED_MIN_BLOCKS) : 2)
     stage_multi_kernel(MultiArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -401,13 +448,20 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
                     float4 pr[2 * RF4];
 #pragma unroll
                     for (int m = 0; m < 2 * RF4; ++m) pr[m] = rec[i * 2 * RF4 + m];
-                    mpair_far2<KIND, NORM, NF>(r2, pr, k2, acc);
+                    mpair_far2<KIND, NORM, NF, HM>(r2, pr, k2, acc);
                 }
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     if (KIND == RSI_STAGE_PISTON) {
                         ar[q][f] = acc[f][0].x + acc[f][0].y;
                         ai[q][f] = acc[f][2].x + acc[f][2].y;
+                        if (HM && f == NF - 1) {  // e^{2 i u_0} -> e^{i u_2}: turn by tau_2 - 2 tau_0
+                            float st, ct;
+                            __sincosf(fmaf(-2.0f, ref[q].tau[0], ref[q].tau[f]), &st, &ct);
+                            const float xr = ar[q][f], xi = ai[q][f];
+                            ar[q][f] = fmaf(ct, xr, -st * xi);
+                            ai[q][f] = fmaf(st, xr, ct * xi);
+                        }
                     } else {
                         // (-sum m h/r c - k sum m h s) + i (-sum m h/r s + k sum m h c), times e^{i tau}
                         const float sr = fmaf(-kv[f], acc[f][1].x + acc[f][1].y, -(acc[f][0].x + acc[f][0].y));
@@ -484,7 +538,8 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
                 const double re = double(hr[q][f]) + double(lr[q][f]);
                 const double im = double(hi[q][f]) + double(li[q][f]);
                 if (a.splits == 1 && (!isfinite(re) || !isfinite(im))) atomicExch(a.status, RSI_DEV_NONFINITE);
-                out[size_t(f) * size_t(a.n_tgt) + size_t(j)] = make_double2(re, im);
+                const int fo = a.splits == 1 ? a.perm[f] : f;  // partial sums stay in kernel order
+                out[size_t(fo) * size_t(a.n_tgt) + size_t(j)] = make_double2(re, im);
             }
     }
     if (a.splits == 1) return;
@@ -517,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED
             }
             const double re = sr + cr, im = si + ci;
             if (!isfinite(re) || !isfinite(im)) atomicExch(a.status, RSI_DEV_NONFINITE);
-            a.field[size_t(f) * size_t(a.n_tgt) + size_t(j)] = make_double2(re, im);
+            a.field[size_t(a.perm[f]) * size_t(a.n_tgt) + size_t(j)] = make_double2(re, im);
         }
     }
     __syncthreads();
@@ -592,8 +647,23 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
             double2 sgm = make_double2(0.0, 0.0);
             double wa = 0.0;
             if (valid && f < nf) {
-                sgm = sigma[size_t(f) * size_t(n_src) + size_t(i)];
+                sgm = sigma[size_t(a.perm[f]) * size_t(n_src) + size_t(i)];
                 wa = amp_scale * src.w[i];
+            }
+            if (a.harm && f == nf) {
+                // the padding slot: c = m_{nf-1} e^{i (beta_{nf-1} - 2 beta_0)} of the shared frequency
+                double cr = 0.0, ci = 0.0;
+                if (valid) {
+                    const double2 s0 = sigma[size_t(a.perm[0]) * size_t(n_src) + size_t(i)];
+                    const double2 s2 = sigma[size_t(a.perm[nf - 1]) * size_t(n_src) + size_t(i)];
+                    const double g = atan2(s2.y, s2.x) - 2.0 * atan2(s0.y, s0.x);
+                    const double m = amp_scale * src.w[i] * hypot(s2.x, s2.y);
+                    cr = m * cos(g);
+                    ci = m * sin(g);
+                }
+                b[0 * fs] = float(cr);
+                b[1 * fs] = float(ci);
+                continue;
             }
             b[0 * fs] = float(atan2(sgm.y, sgm.x));
             b[1 * fs] = float(wa * hypot(sgm.x, sgm.y));
@@ -603,7 +673,7 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
             float* b = rec + (4 + 4 * f) * fs;
             if (valid) {
                 const double k = double(a.kh[f]) + double(a.kl[f]);
-                const double2 sgm = sigma[size_t(f) * size_t(n_src) + size_t(i)];
+                const double2 sgm = sigma[size_t(a.perm[f]) * size_t(n_src) + size_t(i)];
                 const double br = amp_scale * src.w[i] * sgm.x, bi = amp_scale * src.w[i] * sgm.y;
                 b[0 * fs] = float(br);
                 b[1 * fs] = float(bi);
@@ -641,9 +711,9 @@ __global__ void mprep_kernel(int kind, int normals, int nf, int64_t n_src, Point
 
 size_t msmem(size_t tile_bytes) { return RSI_PIPE_STAGES * tile_bytes + RSI_PIPE_STAGES * sizeof(uint64_t); }
 
-template <int KIND, int NORM, int NF, int PK>
+template <int KIND, int NORM, int NF, int PK, int HM = 0>
 int mlaunch(const MultiArgs& a, cudaStream_t s, bool occ, int* occ_out) {
-    auto kern = stage_multi_kernel<KIND, NORM, NF, PK>;
+    auto kern = stage_multi_kernel<KIND, NORM, NF, PK, HM>;
     static RsiCtxOnce attr;
     if (attr.needed()) {
         RSI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024),
@@ -669,7 +739,10 @@ template <int KIND, int NORM, int PK>
 int mdispatch_nf(const MultiArgs& a, cudaStream_t s, bool occ, int* o) {
     switch (a.nf) {
         case 2: return mlaunch<KIND, NORM, 2, PK>(a, s, occ, o);
-        case 3: return mlaunch<KIND, NORM, 3, PK>(a, s, occ, o);
+        case 3:
+            if constexpr (PK == 1)
+                if (a.harm) return mlaunch<KIND, NORM, 3, 1, 1>(a, s, occ, o);
+            return mlaunch<KIND, NORM, 3, PK>(a, s, occ, o);
         default: return mlaunch<KIND, NORM, 4, PK>(a, s, occ, o);
     }
 }
@@ -727,8 +800,22 @@ int mplan(const rsi_stage& st, int nf, const double* ks, int64_t n_src, int64_t 
     a.n_tiles = p.n_tiles;
     a.n_tgt = n_tgt;
     a.tile_bytes = p.tile_bytes;
+    // frequency order in the kernel: the caller's, or with a shared harmonic
+    // (three frequencies, packed, k_j = 2 k_i to 2^-40) i first and j last
+    for (int f = 0; f < kMaxNF; ++f) a.perm[f] = f < nf ? f : 0;
+    a.harm = 0;
+    if (nf == 3 && a.packed) {
+        for (int i = 0; i < nf && !a.harm; ++i)
+            for (int j = 0; j < nf && !a.harm; ++j)
+                if (i != j && fabs(ks[j] - 2.0 * ks[i]) <= 0x1p-40 * ks[j]) {
+                    a.harm = 1;
+                    a.perm[0] = i;
+                    a.perm[1] = 3 - i - j;
+                    a.perm[2] = j;
+                }
+    }
     for (int f = 0; f < kMaxNF; ++f) {
-        const double k = f < nf ? ks[f] : ks[0];
+        const double k = f < nf ? ks[a.perm[f]] : ks[0];
         a.kh[f] = float(k);
         a.kl[f] = float(k - double(a.kh[f]));
     }
@@ -827,4 +914,13 @@ extern "C" int rsi_propagate_stage_multi(const rsi_stage* st, int32_t nf, const 
     if (rc != RSI_OK) return rc;
     timing_end(tsc, st->kind, double(nf) * double(n_src) * double(n_tgt), s);
     return RSI_OK;
+}
+
+extern "C" int rsi_stage_multi_shared_harmonic(const rsi_stage* st, int32_t nf, const double* ks) {
+    if (!st || !ks) return rsi_fail(RSI_E_INVAL, "rsi_stage_multi_shared_harmonic: null argument");
+    MPlan p;
+    MultiArgs a = {};
+    const int rc = mplan(*st, nf, ks, 1 << 12, 1 << 12, p, a);
+    if (rc != RSI_OK) return rc;
+    return a.harm;
 }

@@ -45,7 +45,7 @@ SYMBOLS = ["rsi_version", "rsi_last_error", "rsi_sync_status", "rsi_points_bytes
            "rsi_interface_transmit",
            "rsi_interface_reflect", "rsi_field_image", "rsi_field_image_sum", "rsi_launch_count",
            "rsi_raytrace_workspace_bytes", "rsi_raytrace_field", "rsi_stage_multi_workspace_bytes",
-           "rsi_propagate_stage_multi", "rsi_timing_enable", "rsi_timing_read",
+           "rsi_propagate_stage_multi", "rsi_stage_multi_shared_harmonic", "rsi_timing_enable", "rsi_timing_read",
            "rsi_ubench", "rsi_autotune_stage", "rsi_batch_create", "rsi_batch_run",
            "rsi_batch_destroy", "rsi_nn_features", "rsi_nn_gemm", "rsi_nn_transpose", "rsi_nn_loss",
            "rsi_nn_colsum", "rsi_nn_adam", "rsi_nn_adam_dev", "rsi_nn_cast_bf16", "rsi_nn_carrier", "rsi_nn_gemm_carrier", "rsi_nn_carrier_coeffs",
@@ -144,6 +144,7 @@ def load(path: str | None = None):
         L.rsi_interface_reflect.argtypes = [ctypes.POINTER(Interface), vp, i64, vp, vp, vp]
         L.rsi_stage_multi_workspace_bytes.restype = sz
         L.rsi_stage_multi_workspace_bytes.argtypes = [ctypes.POINTER(Stage), i32, vp, i64, i64]
+        L.rsi_stage_multi_shared_harmonic.argtypes = [ctypes.POINTER(Stage), i32, vp]
         L.rsi_propagate_stage_multi.argtypes = [ctypes.POINTER(Stage), i32, vp, vp, i64, vp, vp, i64, vp, vp, sz,
                                                 vp]
         L.rsi_raytrace_workspace_bytes.restype = sz
@@ -344,6 +345,16 @@ def propagate_stage_multi(st: Stage, ks, src: Points, sigma, tgt: Points, out=No
     _check(L.rsi_propagate_stage_multi(ctypes.byref(st), nf, kd, src.ptr(), src.n, _ptr(sigma), tgt.ptr(), tgt.n,
                                        _ptr(out), _ptr(ws), nb, _stream(stream)), "rsi_propagate_stage_multi")
     return out
+
+
+def stage_multi_shared_harmonic(st: Stage, ks) -> bool:
+    """Whether rsi_propagate_stage_multi forms one of these frequencies from
+    another by the double angle (rsi_stage_multi_shared_harmonic)."""
+    kd = (ctypes.c_double * len(ks))(*[float(k) for k in ks])
+    rc = int(load().rsi_stage_multi_shared_harmonic(ctypes.byref(st), len(ks), kd))
+    if rc < 0:
+        _check(rc, "rsi_stage_multi_shared_harmonic")
+    return rc == 1
 
 
 def interface_struct(m_in: dict, m_out: dict, snell_C: float, mode: str = "global") -> Interface:

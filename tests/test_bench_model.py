@@ -43,6 +43,24 @@ def test_multi_frequency_counts():
         assert bench.multi_ops("rsi", nf)["mufu"] < bench.OPS["rsi"]["mufu"]
 
 
+def test_shared_harmonic_counts_move_the_rsi_bound_to_the_fp32_pipe():
+    """Three frequencies with one formed from another by the double angle: 5
+    MUFU per pair (rsqrt and two sincos) against 44 FP32-pipe lane cycles for
+    RSI, so the FP32 pipe binds at 128 / 44 pairs per SM clock, 2.91 pairs per
+    clock where the plain three-frequency kernel's MUFU allowed 2.29; the
+    piston stays MUFU-bound at 16 / 5."""
+    ops = bench.multi_ops("rsi", 3, harmonic=True)
+    assert ops["mufu"] * 3 == pytest.approx(5.0)
+    assert ops["fma_pipe"] * 3 == pytest.approx(44.0)
+    peak, limiter = bench.alu_roofline("rsi", SM, CLK, ops)
+    assert limiter == "fma"
+    assert peak == pytest.approx(128 * SM * CLK / ops["fma_pipe"])
+    plain, _ = bench.alu_roofline("rsi", SM, CLK, bench.multi_ops("rsi", 3))
+    assert peak / plain == pytest.approx((128 / 44) / (16 / 7), rel=1e-9)
+    pk, plim = bench.alu_roofline("piston", SM, CLK, bench.multi_ops("piston", 3, harmonic=True))
+    assert plim == "mufu" and pk == pytest.approx(16 * SM * CLK * 3 / 5)
+
+
 def test_ray_tracing_counts_include_compares_and_bind_on_the_fp32_pipe():
     """The packed ray-tracing pair with one Newton step: 11 MUFU against 102
     FP32-pipe lane cycles (the path differences by a Newton step and T12

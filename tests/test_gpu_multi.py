@@ -73,6 +73,46 @@ def test_multi_matches_single_stages_and_oracle(nf, case, shape):
         assert_close(got[f], want, 1e-4, f"frequency {f}")
 
 
+@pytest.mark.parametrize("case", ["piston", "rsi_flat", "rsi_curved"])
+@pytest.mark.parametrize("shape", [{}, {"tile": 32, "splits": 3}])
+def test_shared_harmonic_matches_single_stages_and_oracle(case, shape):
+    """Three frequencies of which one is twice another (6.2 = 2 x 3.1 MHz,
+    given first, its base last, so the kernel reorders them): the far path
+    forms the 6.2 MHz term from the 3.1 MHz one by the double angle, and every
+    frequency still equals its single-frequency stage and the oracle."""
+    freqs = [6.2e6, 1.7e6, 3.1e6]
+    if case == "piston":
+        src = rsi.make_qmc_points({"kind": "disk", "centre": (0.0, 0.0, 0.0), "tilt": 0.12, "a": 5e-3}, 0, 0, 3001)
+        tgt = rsi.make_qmc_points({"kind": "rect", "centre": (0.0, 0.0, 0.03), "wx": 0.03, "wy": 0.03}, 0, 1, 1999)
+        c, sig, kind, normals = 1480.0, None, rsi.STAGE_PISTON, rsi.NORMALS_Z
+    else:
+        curved = case == "rsi_curved"
+        surf = {"kind": "cyl", "centre": (0.0, 0.0, 0.02), "wx": 0.03, "wy": 0.03, "R": 0.05} if curved else \
+            {"kind": "rect", "centre": (0.0, 0.0, 0.02), "wx": 0.03, "wy": 0.03}
+        src = rsi.make_qmc_points(surf, 0, 2, 4099)
+        tgt = rsi.grid_points({"x0": -0.01, "x1": 0.012, "nx": 41, "z0": 0.021, "z1": 0.04, "nz": 33, "y": 0.0})
+        rng = np.random.default_rng(7)
+        sig = torch.tensor(rng.normal(size=(3, src.n)) + 1j * rng.normal(size=(3, src.n)),
+                           dtype=torch.complex128, device="cuda")
+        c, kind = 5900.0, rsi.STAGE_RSI
+        normals = rsi.NORMALS_POINTS if curved else rsi.NORMALS_Z
+    ks = [2 * math.pi * f / c for f in freqs]
+    st = rsi.stage_struct(kind, "fp32c", ks[0], 1.0, normals, **shape)
+    assert rsi.stage_multi_shared_harmonic(st, ks)
+    assert not rsi.stage_multi_shared_harmonic(st, [ks[0] * (1 + 1e-9)] + ks[1:])
+    assert not rsi.stage_multi_shared_harmonic(rsi.stage_struct(kind, "fp32c", ks[0], 1.0, normals, variant=2), ks)
+    got = rsi.propagate_stage_multi(st, ks, src, sig, tgt).cpu().numpy()
+    rsi.sync_status()
+    hs = host(src)
+    tq = {k: v for k, v in host(tgt).items() if k in ("x", "y", "z")}
+    for f, k in enumerate(ks):
+        one = rsi.stage_struct(kind, "fp32c", k, 1.0, normals, **dict(shape, variant=3))
+        single = rsi.propagate_stage(one, src, None if sig is None else sig[f].contiguous(), tgt).cpu().numpy()
+        assert rel(got[f], single) < 2e-5, f
+        want = oracle.piston_field(hs, tq, k) if sig is None else oracle.rsi_field(hs, sig[f].cpu().numpy(), tq, k)
+        assert_close(got[f], want, 1e-4, f"frequency {f}")
+
+
 def test_reversed_normals_and_rejections():
     src = rsi.make_qmc_points({"kind": "rect", "centre": (0.0, 0.0, 0.02), "wx": 0.02, "wy": 0.02}, 0, 3, 2000)
     tgt = rsi.grid_points({"x0": -0.01, "x1": 0.01, "nx": 16, "z0": 0.0, "z1": 0.015, "nz": 16, "y": 0.0})
