@@ -324,7 +324,7 @@ __device__ __forceinline__ void mpair_far2(const MRef2& t, const float4* pr, con
                 // cos 2 u_0 = (c - s)(c + s): modulus |E_0|^2 whatever the angle
                 const float2 cq = __fmul2_rn(__ffma2_rn(sn0, make_float2(-1.0f, -1.0f), cs0), __fadd2_rn(cs0, sn0));
                 const float2 sq = __fmul2_rn(sn0, c2);                                      // sin 2 u_0
-                const float2 nsq = __fmul2_rn(sn0, __fmul2_rn(cs0, make_float2(-2.0f, -2.0f)));  // -sin 2 u_0
+                const float2 nsq = __fmul2_rn(sq, make_float2(-1.0f, -1.0f));  // -sin 2 u_0, exact
                 const float2 er = __ffma2_rn(cr, cq, __fmul2_rn(ci, nsq));
                 const float2 ei = __ffma2_rn(cr, sq, __fmul2_rn(ci, cq));
                 acc[f][0] = __ffma2_rn(hr, er, acc[f][0]);
@@ -371,8 +371,14 @@ __device__ __forceinline__ void munpack(const float* tile_rec, int i, float4* r)
     }
 }
 
+// the shared-harmonic form keeps 4 (64 registers, 8 bytes spilled outside the
+// pair loop): 2110 Gpair-terms/s on the three-frequency RSI stage, 3 CTAs
+// (77 registers, no spill) 2051
+#ifndef RSI_MULTI_HARM_MIN_BLOCKS
+#define RSI_MULTI_HARM_MIN_BLOCKS RSI_MULTI_PACKED_MIN_BLOCKS
+#endif
 template <int KIND, int NORM, int NF, int PK, int HM>
-__global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : RSI_MULTI_PACKED_MIN_BLOCKS) : 2)
+__global__ void __launch_bounds__(kThreads, PK ? (NF >= 4 ? 3 : HM ? RSI_MULTI_HARM_MIN_BLOCKS : RSI_MULTI_PACKED_MIN_BLOCKS) : 2)
     stage_multi_kernel(MultiArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RSI_PIPE_STAGES * a.tile_bytes);
