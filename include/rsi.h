@@ -173,7 +173,7 @@ typedef struct rsi_stage {
     double v0;         /* PISTON: normal velocity amplitude (m/s)               */
     int32_t normals;   /* RSI: enum rsi_normals                                  */
     int32_t tile;      /* sources per shared-memory tile (64, 128, 256); 0 = auto */
-    int32_t tpt;       /* targets per thread (FP32C: 2 or 4; FP64: 1); 0 = auto   */
+    int32_t tpt;       /* targets per thread (FP32C: 1, 2 or 4; FP64: 1); 0 = auto */
     int32_t splits;    /* source splits (>= 1); 0 = auto                          */
     int32_t variant;   /* FP32C distance update: 0 = auto, 1 = reciprocal, 2 = Newton,
                           3 = Newton on two sources per packed f32x2 instruction */
@@ -373,7 +373,8 @@ typedef struct rsi_batch_plan rsi_batch_plan; /* opaque, host memory */
 /* Plans a batch (host work only, nothing enqueued): per-instance tile sizes
  * by the accuracy rule, work items of about 2^22 pairs sorted largest first,
  * and the workspace layout.  shape: NULL or an FP32C rsi_stage whose tile
- * (upper bound), tpt and variant fields override the defaults.  Returns the
+ * (upper bound, default 256), tpt (1, 2 or 4, default 1) and variant
+ * (default 3) fields override the defaults.  Returns the
  * workspace size and the number of complex64 image elements (the instances'
  * nx*nz, concatenated in instance order).                                  */
 int rsi_batch_create(const rsi_batch_instance *inst, int32_t n_inst, uint64_t seed,

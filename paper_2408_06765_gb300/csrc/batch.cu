@@ -131,7 +131,10 @@ __global__ void batch_prep_kernel(const BPrep* __restrict__ preps, const BPrepTi
 #endif
 template <int KIND, int TPT, int VAR>
 constexpr int batch_min_blocks() {
-    return TPT != 2 ? 2 : (KIND == RSI_STAGE_RSI && VAR == 3) ? RSI_BATCH_RSI_MIN_BLOCKS : RSI_FP32_MIN_BLOCKS;
+    return TPT == 1   ? RSI_FP32_TPT1_MIN_BLOCKS
+           : TPT != 2 ? 2
+           : (KIND == RSI_STAGE_RSI && VAR == 3) ? RSI_BATCH_RSI_MIN_BLOCKS
+                                                  : RSI_FP32_MIN_BLOCKS;
 }
 
 template <int KIND, int NORM, int TPT, int VAR>
@@ -225,9 +228,13 @@ void append_segments(std::vector<BSeg>& segs, int32_t set, int64_t n) {
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
+// one target per thread by default: the persistent stage kernels then hold
+// their work-item state in 64 registers at 4 resident CTAs per SM (two
+// targets per thread: 126 registers, 2 CTAs); 1433 against 1395 Gpair/s on
+// the first 256 instances of the 64 x 32 scan
 struct rsi_batch_plan {
     int n_inst = 0;
-    int S_max = 256, tpt = 2, variant = 3, normals2 = RSI_NORMALS_Z;
+    int S_max = 256, tpt = 1, variant = 3, normals2 = RSI_NORMALS_Z;
     size_t ws_bytes = 0, img_elems = 0, max_tile1 = 0, max_tile2 = 0;
     std::vector<uint8_t> blob;  // device tables, uploaded to workspace offset 0
     // table offsets (bytes) in the blob / workspace
@@ -472,6 +479,13 @@ int launch_batch_stage(const rsi_batch_plan& P, uint8_t* ws, size_t o_st, size_t
 template <int KIND, int NORM>
 int launch_batch_stage_v(const rsi_batch_plan& P, uint8_t* ws, size_t o_st, size_t o_it, int64_t n_items,
                          size_t max_tile, unsigned long long* ctr, int* status, cudaStream_t s) {
+    if (P.tpt == 1) {
+        if (P.variant == 1)
+            return launch_batch_stage<KIND, NORM, 1, 1>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
+        if (P.variant == 3)
+            return launch_batch_stage<KIND, NORM, 1, 3>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
+        return launch_batch_stage<KIND, NORM, 1, 2>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
+    }
     if (P.tpt == 4) {
         if (P.variant == 1)
             return launch_batch_stage<KIND, NORM, 4, 1>(P, ws, o_st, o_it, n_items, max_tile, ctr, status, s);
@@ -560,7 +574,7 @@ extern "C" int rsi_batch_create(const rsi_batch_instance* inst, int32_t n_inst, 
         if (shape->variant) P->variant = shape->variant;
     }
     if (!(P->S_max == 32 || P->S_max == 64 || P->S_max == 128 || P->S_max == 256 || P->S_max == 512) ||
-        (P->tpt != 2 && P->tpt != 4) || (P->variant < 1 || P->variant > 3)) {
+        (P->tpt != 1 && P->tpt != 2 && P->tpt != 4) || (P->variant < 1 || P->variant > 3)) {
         delete P;
         return rsi_fail(RSI_E_INVAL, "rsi_batch_create: bad tile / targets per thread / variant");
     }

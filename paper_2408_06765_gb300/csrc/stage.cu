@@ -151,7 +151,8 @@ int make_plan(const rsi_stage& st, int64_t n_src, int64_t n_tgt, Plan& p, int ma
         // 2 targets per thread keeps 80 registers and 3 CTAs (24 warps) per SM;
         // it measured faster than 4 at every tile size
         p.tpt = st.tpt ? st.tpt : 2;
-        if (p.tpt != 2 && p.tpt != 4) return rsi_fail(RSI_E_INVAL, "FP32C targets per thread must be 2 or 4");
+        if (p.tpt != 1 && p.tpt != 2 && p.tpt != 4)
+            return rsi_fail(RSI_E_INVAL, "FP32C targets per thread must be 1, 2 or 4");
         p.variant = st.variant ? st.variant : 3;  // packed source pairs: ~10% faster than 2 on every shape
         if (p.variant < 1 || p.variant > 3) return rsi_fail(RSI_E_INVAL, "variant must be 1, 2 or 3");
     } else {
@@ -355,7 +356,7 @@ extern "C" int rsi_autotune_stage(const rsi_stage* st, const void* src_points, i
     float best_ms = 1e30f;
     rsi_stage win = base;
     for (int S = 32; S <= cap; S <<= 1)
-        for (int tpt : {2, 4})
+        for (int tpt : {1, 2, 4})
             for (int var : {1, 2, 3}) {
                 rsi_stage c = base;
                 c.tile = S;

@@ -69,6 +69,11 @@ int occupancy_t(const StageArgs& a) {
 
 template <int KIND, int NORM>
 int dispatch_tv(const StageArgs& a, cudaStream_t s, bool occ) {
+    if (a.tpt == 1) {
+        if (a.variant == 3) return occ ? occupancy_t<KIND, NORM, 1, 3>(a) : launch_t<KIND, NORM, 1, 3>(a, s);
+        if (a.variant == 2) return occ ? occupancy_t<KIND, NORM, 1, 2>(a) : launch_t<KIND, NORM, 1, 2>(a, s);
+        return occ ? occupancy_t<KIND, NORM, 1, 1>(a) : launch_t<KIND, NORM, 1, 1>(a, s);
+    }
     if (a.tpt == 4) {
         if (a.variant == 3) return occ ? occupancy_t<KIND, NORM, 4, 3>(a) : launch_t<KIND, NORM, 4, 3>(a, s);
         if (a.variant == 2) return occ ? occupancy_t<KIND, NORM, 4, 2>(a) : launch_t<KIND, NORM, 4, 2>(a, s);

@@ -47,9 +47,16 @@ namespace rsi_fp32 {
 constexpr int kThreads = 256;
 constexpr int kUnroll = RSI_FP32_UNROLL;
 // resident CTAs asked of the compiler, and the unrolling of the packed loop
+// one target per thread: 4 resident CTAs (64 registers)
+#ifndef RSI_FP32_TPT1_MIN_BLOCKS
+#define RSI_FP32_TPT1_MIN_BLOCKS 4
+#endif
 template <int KIND, int TPT, int VAR>
 constexpr int min_blocks() {
-    return TPT != 2 ? 2 : (KIND == RSI_STAGE_RSI && VAR == 3) ? RSI_FP32_PACKED_RSI_MIN_BLOCKS : RSI_FP32_MIN_BLOCKS;
+    return TPT == 1   ? RSI_FP32_TPT1_MIN_BLOCKS
+           : TPT != 2 ? 2
+           : (KIND == RSI_STAGE_RSI && VAR == 3) ? RSI_FP32_PACKED_RSI_MIN_BLOCKS
+                                                  : RSI_FP32_MIN_BLOCKS;
 }
 template <int KIND>
 constexpr int packed_unroll() {

@@ -47,10 +47,13 @@ def uneven_batch(curved=False):
     return cfgs
 
 
+@pytest.mark.parametrize("tpt", [0, 2])
 @pytest.mark.parametrize("curved", [False, True])
-def test_batch_matches_plain_path_and_oracle(curved):
+def test_batch_matches_plain_path_and_oracle(curved, tpt):
+    # tpt 0: the default shape (one target per thread); 2: two per thread
     cfgs = uneven_batch(curved)
-    b = rsi.Batch(cfgs, seed=cfgs[0]["seed"])
+    shape = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", 1.0, 1.0, tpt=tpt, variant=3) if tpt else None
+    b = rsi.Batch(cfgs, seed=cfgs[0]["seed"], shape=shape)
     try:
         b.run()
         torch.cuda.synchronize()
@@ -80,7 +83,7 @@ def test_autotuned_shape_is_valid_and_agrees():
     sig = torch.ones(it["n"], dtype=torch.complex128, device="cuda")
     st = rsi.stage_struct(rsi.STAGE_RSI, "fp32c", 2 * math.pi * 5e6 / 5900.0, normals=rsi.NORMALS_Z)
     best = rsi.autotune_stage(st, src, sig, tgt)
-    assert best.tile in (32, 64, 128) and best.tpt in (2, 4) and best.variant in (1, 2, 3)
+    assert best.tile in (32, 64, 128) and best.tpt in (1, 2, 4) and best.variant in (1, 2, 3)
     ref = rsi.propagate_stage(st, src, sig, tgt)
     tuned = rsi.propagate_stage(best, src, sig, tgt)
     rsi.sync_status()

@@ -175,6 +175,9 @@ def test_multilayer_reduced_counts(curved):
     {"tile": 32, "tpt": 2, "splits": 1, "variant": 3},
     {"tile": 256, "tpt": 4, "splits": 0, "variant": 3},
     {"tile": 128, "tpt": 2, "splits": 5, "variant": 3},
+    {"tile": 64, "tpt": 1, "splits": 2, "variant": 3},
+    {"tile": 256, "tpt": 1, "splits": 0, "variant": 1},
+    {"tile": 32, "tpt": 1, "splits": 1, "variant": 2},
 ])
 def test_launch_shapes_agree(opts):
     cfg = W.small_ragged("fp32c", freq=7.5e6)
