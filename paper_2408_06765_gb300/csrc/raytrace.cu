@@ -306,9 +306,8 @@ __device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y
 // reciprocal square roots, divisions, clamps and sincos per point, and the
 // safeguarded steps only for a point whose ray has not converged
 template <int NW>
-__device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, float A0, const float4& r1, float A1,
+__device__ __forceinline__ void ray_pair2(const RayRef& R, float2 px, float2 py, float2 pzn, float2 A,
                                           const RtArgs& a, float k1, float k2, float2& acc_r, float2& acc_i) {
-    const float2 px = make_float2(r0.x, r1.x), py = make_float2(r0.y, r1.y), pz = make_float2(r0.z, r1.z);
     const float2 vx = sub2(f2(R.dx), px), vy = sub2(f2(R.dy), py);
     const float2 v2 = __ffma2_rn(vx, vx, __fmul2_rn(vy, vy));
     const bool okx = v2.x > 1e-24f, oky = v2.y > 1e-24f;
@@ -326,14 +325,14 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     float2 wy = __fmul2_rn(__ffma2_rn(f2(R.dy), drho, __fmul2_rn(py, f2(-R.rho))), sw);
     if (!(R.irho > 0.0f && iv.x > 0.0f)) wx.x = ux.x - R.ux, wy.x = uy.x - R.uy;
     if (!(R.irho > 0.0f && iv.y > 0.0f)) wx.y = ux.y - R.ux, wy.y = uy.y - R.uy;
-    const float2 h1 = sub2(f2(R.H1), pz);
+    const float2 h1 = __fadd2_rn(f2(R.H1), pzn);  // pzn = -p_z
     const float h2 = R.H2;
     const float2 h1q = __fmul2_rn(h1, h1);
     const float h2q = h2 * h2;
     const float2 s1h = __fmul2_rn(f2(a.s1), h1q);
     const float2 bfix = sub2(f2(R.bc), drho);
     const float lo0 = -R.tc;
-    float2 dt = __ffma2_rn(f2(-R.a_r), drho, __fmul2_rn(f2(-R.a_h), pz));
+    float2 dt = __ffma2_rn(f2(-R.a_r), drho, __fmul2_rn(f2(R.a_h), pzn));
     dt.x = fminf(fmaxf(dt.x, lo0), bfix.x);
     dt.y = fminf(fmaxf(dt.y, lo0), bfix.y);
     float2 est = f2(INFINITY);
@@ -363,8 +362,8 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     const float2 e1y = __ffma2_rn(dt, uy, __fmul2_rn(f2(R.tc), wy));
     const float2 gx = __fadd2_rn(px, e1x), gy = __fadd2_rn(py, e1y);
     const float2 t1 = __ffma2_rn(f2(2.0f * R.tc), __ffma2_rn(f2(R.ux), e1x, __fmul2_rn(f2(R.uy), e1y)),
-                                 __ffma2_rn(f2(-2.0f * R.H1), pz,
-                                            __ffma2_rn(e1x, e1x, __ffma2_rn(e1y, e1y, __fmul2_rn(pz, pz)))));
+                                 __ffma2_rn(f2(2.0f * R.H1), pzn,
+                                            __ffma2_rn(e1x, e1x, __ffma2_rn(e1y, e1y, __fmul2_rn(pzn, pzn)))));
     const float2 t2 = __ffma2_rn(f2(-2.0f * R.bc), __ffma2_rn(f2(R.ux), gx, __fmul2_rn(f2(R.uy), gy)),
                                  __ffma2_rn(gx, gx, __fmul2_rn(gy, gy)));
     const float2 q1 = __ffma2_rn(f2(R.D1), f2(R.D1), t1), q2 = __ffma2_rn(f2(R.D2), f2(R.D2), t2);
@@ -383,7 +382,7 @@ __device__ __forceinline__ void ray_pair2(const RayRef& R, const float4& r0, flo
     const float2 cc = __fmul2_rn(__fmul2_rn(__fmul2_rn(f2(a.c21), cos1), cos1), f2(R.ih22));
     const float2 den = __fmul2_rn(__ffma2_rn(cc, __fmul2_rn(D2, q2), D1), __ffma2_rn(f2(a.c21), D2, D1));
     const float2 dt2 = __fmul2_rn(den, __fmul2_rn(td, td));
-    const float2 amp = __fmul2_rn(__fmul2_rn(make_float2(A0, A1), tn), make_float2(rsqrt_ap(dt2.x), rsqrt_ap(dt2.y)));
+    const float2 amp = __fmul2_rn(__fmul2_rn(A, tn), make_float2(rsqrt_ap(dt2.x), rsqrt_ap(dt2.y)));
     float2 sn, cs;
     __sincosf(u.x, &sn.x, &cs.x);
     __sincosf(u.y, &sn.y, &cs.y);
@@ -449,16 +448,18 @@ __global__ void __launch_bounds__(kRtThreads, RSI_RT_MIN_BLOCKS) raytrace_kernel
             ar[q] = ai[q] = 0.0f;
         }
 #if RSI_RT_PACKED
-        {  // tiles hold an even number of points (32 .. 256)
+        {  // tiles hold an even number of points (32 .. 256), pair-interleaved:
+           // per point pair (px, px', py, py'), (-pz, -pz', ...), (A, A', 0, 0), 0
             float2 pr[TPT], pi[TPT];
 #pragma unroll
             for (int q = 0; q < TPT; ++q) pr[q] = pi[q] = f2(0.0f);
 #pragma unroll 1
             for (int i = 0; i < a.S; i += 2) {
-                const float4 r0 = rec[2 * i], r1 = rec[2 * i + 2];
-                const float A0 = rec[2 * i + 1].x, A1 = rec[2 * i + 3].x;
+                const float4 v0 = rec[2 * i], v1 = rec[2 * i + 1], v2 = rec[2 * i + 2];
+                const float2 px = make_float2(v0.x, v0.y), py = make_float2(v0.z, v0.w);
+                const float2 pzn = make_float2(v1.x, v1.y), A = make_float2(v2.x, v2.y);
 #pragma unroll
-                for (int q = 0; q < TPT; ++q) ray_pair2<NW>(ref[q], r0, A0, r1, A1, a, k1, k2, pr[q], pi[q]);
+                for (int q = 0; q < TPT; ++q) ray_pair2<NW>(ref[q], px, py, pzn, A, a, k1, k2, pr[q], pi[q]);
             }
 #pragma unroll
             for (int q = 0; q < TPT; ++q) {
@@ -625,7 +626,7 @@ extern "C" int rsi_raytrace_field(const rsi_raytrace* rt, const void* src_points
     st.precision = RSI_PREC_FP32C;
     st.k = rt->k1;
     st.v0 = rt->v0;
-    rc = launch_prep_fp32(st, src, n_src, nullptr, p.S, tiles, p.tile_bytes, p.n_tiles, s);
+    rc = launch_prep_fp32(st, src, n_src, nullptr, p.S, tiles, p.tile_bytes, p.n_tiles, s, RSI_RT_PACKED != 0);
     if (rc != RSI_OK) return rc;
 
     RtArgs a = {};
