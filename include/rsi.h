@@ -214,7 +214,9 @@ int rsi_propagate_stage(const rsi_stage *st,
  * another (k_j = 2 k_i to a relative 2^-40; with one sound speed, one
  * frequency twice another), e^{i k_j (r - R)} is formed from e^{i k_i (r - R)}
  * by the double angle on pairs away from the tile, two MUFU operations per
- * pair fewer; the result stays a single-frequency stage to rounding.        */
+ * pair fewer.  The doubled angle carries twice the sincos's angle error: on
+ * 2.25, 5 and 10 MHz the 10 MHz image is 9.7e-7 from the FP64 oracle (5.5e-7
+ * with its own sincos), far inside the FP32C tolerance.                    */
 size_t rsi_stage_multi_workspace_bytes(const rsi_stage *st, int32_t nf, const double *ks, int64_t n_src,
                                        int64_t n_tgt);
 int rsi_propagate_stage_multi(const rsi_stage *st, int32_t nf, const double *ks,
